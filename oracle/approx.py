@@ -1,0 +1,215 @@
+"""FP64 oracle for the paper's moment approximation (test infrastructure only).
+
+The steps follow Methods ("Partition function", "Probability of any sample",
+"Moments calculation", "Approximation method"), extended to uniform loss by
+the covariance form.  For a click pattern S with n modes:
+
+1. Sectors (Methods, "Partition function"): for every sub-ensemble Z of S the
+   generating function  Z_Z(t) = det(I - t O_Z)^{-1/2} = sum_k c_k[Z] t^k  has
+   c_k[Z] det(sigma_Q)^{-1/2} = P(k photons in Z, vacuum on every other
+   detector).  The paper's Fourier sum over nu is the coefficient extraction
+   of this series; here the coefficients are computed exactly from the
+   eigenvalues lambda of O_Z:  log Z_Z(t) = 1/2 sum_p (sum_i lambda_i^p) t^p / p,
+   then the series exponential.
+2. Moments (Methods, "Moments calculation"): in the sub-ensemble of S, let v
+   be the number of detectors of S left in vacuum.  The minors with w
+   detectors removed give the factorial moments of v in every sector,
+        D_w^(k) = sum_{W subset S, |W| = w} c_k[S \\ W] = sum_v C(v, w) q_k(v),
+   for w = 0..j; raw moments follow with Stirling numbers of the second kind.
+3. Inverse moment problem (Methods, "Approximation method"): in each sector
+   q_k(v) ~ exp(-f(v)) with f a polynomial of degree j whose moments 0..j
+   match; solved as the convex maximum-entropy dual by damped Newton.
+4. The all-clicked point v = 0 of every sector is summed:
+        P(S) ~ det(sigma_Q)^{-1/2} sum_k exp(-f_k(0)).
+
+Readings where the paper is silent (each listed in the design notes):
+* the fit variable is v = n - c (same polynomial family as the click count c);
+* sector k >= 1 lives on v in [max(0, n-k), n-1]; sectors k < n add nothing;
+* the polynomial degree is min(j, |support| - 1), so the fit is exact when
+  the support has at most j + 1 points;
+* x = v / n is the variable inside the Newton solve (conditioning only);
+* the sector sum stops at K_max, the first K whose partial sum of c_k[S]
+  reaches (1 - 1e-14) det(I - O_S)^{-1/2};
+* a sector whose mass D_0^(k) is below eps_sector times the largest sector
+  mass is rounding noise (e.g. the odd sectors of a lossless state, which are
+  exactly zero) and contributes nothing.
+"""
+from __future__ import annotations
+
+import math
+from itertools import combinations
+
+import numpy as np
+
+TAIL_EPS = 1e-14
+EPS_SECTOR = 1e-12
+
+
+def sub_rows(modes, M):
+    """Row indices (x of each mode, then p of each mode) of a mode set in xp order."""
+    modes = list(modes)
+    return modes + [m + M for m in modes]
+
+
+def series_coeffs(Osub: np.ndarray, K: int) -> np.ndarray:
+    """c_0..c_K of det(I - t Osub)^{-1/2} (Osub real symmetric)."""
+    c = np.zeros(K + 1)
+    c[0] = 1.0
+    if Osub.size == 0:
+        return c
+    lam = np.linalg.eigvalsh(Osub)
+    a = np.zeros(K + 1)
+    pw = np.ones_like(lam)
+    for p in range(1, K + 1):
+        pw = pw * lam
+        a[p] = 0.5 * pw.sum() / p
+    for k in range(1, K + 1):
+        p = np.arange(1, k + 1)
+        c[k] = np.dot(p * a[1:k + 1], c[k - p]) / k
+    return c
+
+
+def choose_kmax(O: np.ndarray, M: int, modes) -> int:
+    """Smallest K with sum_{k<=K} c_k[S] >= (1 - TAIL_EPS) det(I - O_S)^{-1/2}."""
+    rows = sub_rows(modes, M)
+    Os = O[np.ix_(rows, rows)]
+    if Os.size == 0:
+        return 0
+    total = np.linalg.det(np.eye(len(rows)) - Os) ** -0.5
+    K = 64
+    while True:
+        c = series_coeffs(Os, K)
+        cs = np.cumsum(c)
+        hit = np.nonzero(cs >= (1.0 - TAIL_EPS) * total)[0]
+        if hit.size:
+            return int(hit[0])
+        if K > 1 << 16:
+            raise RuntimeError("sector series does not converge")
+        K *= 2
+
+
+def factorial_moment_tables(O: np.ndarray, M: int, modes, j: int, K: int) -> np.ndarray:
+    """D[w, k] = sum over groups W of S with |W| = w of c_k[S \\ W], w = 0..j."""
+    modes = list(modes)
+    n = len(modes)
+    D = np.zeros((j + 1, K + 1))
+    for w in range(min(j, n) + 1):
+        for W in combinations(range(n), w):
+            keep = [modes[a] for a in range(n) if a not in W]
+            rows = sub_rows(keep, M)
+            D[w] += series_coeffs(O[np.ix_(rows, rows)], K)
+    return D
+
+
+def stirling2(i: int, w: int) -> int:
+    if i == w:
+        return 1
+    if w == 0 or w > i:
+        return 0
+    return w * stirling2(i - 1, w) + stirling2(i - 1, w - 1)
+
+
+def raw_moments(Dk: np.ndarray, j: int) -> np.ndarray:
+    """mu_i = sum_v v^i q(v) = sum_w S(i, w) w! D_w, i = 0..j."""
+    return np.array([sum(stirling2(i, w) * math.factorial(w) * Dk[w] for w in range(i + 1))
+                     for i in range(j + 1)])
+
+
+def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter: int = 200):
+    """Coefficients a of q(x) = exp(-sum_i a_i x^i) on the support points x with
+    sum_x x^i q(x) = m_i (i = 0..J, m_0 = 1).  Returns (a, converged)."""
+    J = m.size - 1
+    X = np.vander(support, J + 1, increasing=True)            # X[s, i] = x_s^i
+    a = np.zeros(J + 1)
+    a[0] = math.log(support.size)
+
+    def phi(a):
+        return np.exp(-X @ a).sum() + a @ m
+
+    f = phi(a)
+    for it in range(max_iter):
+        q = np.exp(-X @ a)
+        g = m - X.T @ q
+        if np.max(np.abs(g)) <= tol:
+            return a, True
+        H = (X * q[:, None]).T @ X
+        try:
+            step = np.linalg.solve(H, g)
+        except np.linalg.LinAlgError:
+            return a, False
+        # gradient of phi is g; Newton direction -step; Armijo backtracking.
+        # Near the optimum the decrease of phi is below its rounding, so a step
+        # that halves the gradient is accepted as well.
+        t = 1.0
+        gmax = np.max(np.abs(g))
+        while True:
+            an = a - t * step
+            fn = phi(an)
+            if np.isfinite(fn) and fn <= f - 1e-4 * t * (g @ step):
+                break
+            if np.isfinite(fn) and fn <= f + 1e-14 * abs(f) and \
+                    np.max(np.abs(m - X.T @ np.exp(-X @ an))) <= 0.5 * gmax:
+                break
+            t *= 0.5
+            if t < 1e-12:
+                return a, False
+        a, f = an, fn
+    q = np.exp(-X @ a)
+    return a, bool(np.max(np.abs(m - X.T @ q)) <= 1e3 * tol)
+
+
+def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int):
+    """Estimate of q_k(v = 0) from the factorial moments D_0..D_j of sector k.
+
+    Returns (value, flag) with flag 0 = fitted at order j' = min(j, |V|-1),
+    1 = fell back to a lower order, 2 = no fit possible (value 0)."""
+    if k < n or Dk[0] <= 0.0:
+        return 0.0, 0
+    if n == 0:
+        return Dk[0], 0
+    v = np.arange(max(0, n - k), n, dtype=np.float64)          # v = n is empty for k >= 1
+    Jmax = min(j, v.size - 1)
+    mu = raw_moments(Dk, Jmax)
+    x = v / n
+    for J in range(Jmax, -1, -1):
+        mnorm = np.array([mu[i] / n ** i for i in range(J + 1)]) / mu[0]
+        a, ok = maxent_fit(x, mnorm)
+        if ok:
+            return mu[0] * math.exp(-a[0]), 0 if J == Jmax else 1
+    return 0.0, 2
+
+
+def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
+                   K: int | None = None, eps_sector: float = EPS_SECTOR):
+    """log P(S) by the order-j approximation.  Returns (logP, info dict)."""
+    modes = list(modes)
+    n = len(modes)
+    if K is None:
+        K = choose_kmax(O, M, modes)
+    D = factorial_moment_tables(O, M, modes, j, K)
+    total, flags = 0.0, 0
+    parts = np.zeros(K + 1)
+    floor = eps_sector * D[0].max()
+    for k in range(K + 1):
+        if D[0, k] < floor:
+            continue
+        val, fl = sector_last_point(D[:, k], n, k, j)
+        parts[k] = val
+        total += val
+        flags = max(flags, fl)
+    logP = -0.5 * logdet_sigmaQ + (math.log(total) if total > 0 else -math.inf)
+    return logP, dict(K=K, D=D, parts=parts, flag=flags)
+
+
+def exact_sector_last_points(O: np.ndarray, M: int, modes, K: int) -> np.ndarray:
+    """Exact q_k(v = 0) = sum_{Z subset S} (-1)^{n-|Z|} c_k[Z], by inclusion-exclusion
+    inside each sector (small n only)."""
+    modes = list(modes)
+    n = len(modes)
+    out = np.zeros(K + 1)
+    for z in range(1 << n):
+        Z = [modes[a] for a in range(n) if z >> a & 1]
+        rows = sub_rows(Z, M)
+        sgn = -1.0 if (n - len(Z)) & 1 else 1.0
+        out += sgn * series_coeffs(O[np.ix_(rows, rows)], K)
+    return out
