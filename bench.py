@@ -1,0 +1,320 @@
+"""Benchmark: exact click-pattern probabilities on one GB300 (or N, one rank each).
+
+One step = the whole exact path on one batch: state build (sigma, O, log det
+sigma_Q from U, r, eta) plus the signed subset sweep for every click pattern of
+the batch.  Default workload: 24 modes, 12 squeezed inputs r ~ U[0.6, 1.2],
+eta = 0.5, Haar U, 1024 patterns with n ~ U{12..20} clicks (2.4e8 subsets),
+FP32-determinant / compensated-sum split.  Metric: subset log-dets per second
+(whole job), plus patterns per second and the error against the FP64 oracle.
+
+    python bench.py [--gpus N --steps K --warmup W --precision fp32|fp64]
+    python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gbs_inputs as g  # noqa: E402
+
+METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
+UNIT = "subset logdets/s"
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
+
+
+def schur_flops(n: int) -> float:
+    """Algorithmic flops of the include/exclude Schur recursion over n modes:
+    every internal node at depth k includes its next mode with r = n-1-k modes
+    left: pivot det 3, rsqrt 1, inverse 4, tau 1, W = B Q 12 r, rank-2 update
+    4 r (2r + 1); plus one add per leaf."""
+    tot = float(1 << n)
+    for k in range(n):
+        r = n - 1 - k
+        tot += (1 << k) * (8 * r * r + 16 * r + 9)
+    return tot
+
+
+def workload(name: str, rank: int, world: int):
+    c = g.CONFIGS[name]
+    U, r = c.unitary(), c.squeezing()
+    # weak scaling: rank k evaluates its own batch (pattern counters k*n_pat ...)
+    allp = g.gen_patterns(c.seed, c.M, c.n_lo, c.n_hi, c.n_pat * world) if world > 1 else c.patterns()
+    pats = allp[rank * c.n_pat:(rank + 1) * c.n_pat]
+    n = np.array([len(g.pattern_modes(p)) for p in pats])
+    return c, U, r, pats, n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(U, r, eta, pats, n, budget_s: float = 12.0):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample of
+    the workload's patterns (in order, until the time budget is used)."""
+    import oracle
+    st = oracle.build_state(U, r, eta)
+    t0 = time.perf_counter()
+    done, subsets, logp = 0, 0, []
+    while done < len(pats) and time.perf_counter() - t0 < budget_s:
+        chunk = pats[done:done + 16]
+        res = oracle.prob_exact(st, chunk)
+        logp.append(res["logP"])
+        subsets += int(sum(1 << int(k) for k in n[done:done + len(chunk)]))
+        done += len(chunk)
+    el = time.perf_counter() - t0
+    return dict(value=subsets / el, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+                sample="first %d of %d patterns (%d subsets) in %.1f s" % (done, len(pats), subsets, el),
+                patterns=done, logP=np.concatenate(logp) if logp else np.zeros(0))
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    c, U, r, pats, n = workload(args.workload, 0, 1)
+    import oracle
+    st = oracle.build_state(U, r, c.eta)
+    per_step = 4                                   # patterns per step, rotating through the batch
+    def step(i):
+        sel = [(i * per_step + j) % len(pats) for j in range(per_step)]
+        oracle.prob_exact(st, pats[sel])
+        return int(sum(1 << int(n[s]) for s in sel))
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    subsets = sum(step(args.warmup + i) for i in range(args.steps))
+    el = time.perf_counter() - t0
+    val = subsets / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": c.name, "M": c.M, "n_pat_per_step": per_step,
+                                            "clicks": [c.n_lo, c.n_hi], "eta": c.eta},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "%d patterns per step, rotating through the %d-pattern batch"
+                                       % (per_step, len(pats))},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2106_01445_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2106_01445_gb300.api import Context, patterns_tensor, _complex_interleaved
+
+    c, U, r, pats, n = workload(args.workload, rank, world)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context(local, stream)
+    ctx.reserve(len(pats), int(n.max()))
+    Ud = _complex_interleaved(U, dev)
+    rd = torch.as_tensor(r, device=dev)
+    pd = patterns_tensor(pats, dev)
+    M = c.M
+    O = torch.empty((2 * M, 2 * M), dtype=torch.float64, device=dev)
+    logdet = torch.empty(1, dtype=torch.float64, device=dev)
+    sst = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {k: torch.empty(len(pats), dtype=torch.float64, device=dev) for k in ("logP", "kappa", "err_bound")}
+    out["status"] = torch.empty(len(pats), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(prec):
+        ctx.build_state_into(Ud, rd, c.eta, O, logdet, sst)
+        ctx.prob(O, logdet, pd, order=0, precision=prec, out=out)
+
+    subsets = float(sum(2.0 ** k for k in n))
+    flops = float(sum(schur_flops(int(k)) for k in n))
+    prec = args.precision
+
+    def timed(prec, K, W, clocks=None):
+        for _ in range(W):
+            step(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ctx.timing(True)
+        ctx.timing_read(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        torch.cuda.synchronize()
+        for i in range(K):
+            ev[i][0].record(stream)
+            step(prec)
+            ev[i][1].record(stream)
+            flush.fill_(float(i))           # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        ms = sum(a.elapsed_time(bb) for a, bb in ev)
+        sweep_ms, launches = ctx.timing_read(reset=True)
+        ctx.timing(False)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms, sweep_ms, launches, ck
+
+    clocks = ClockSampler(local)
+    ms, sweep_ms, launches, ck = timed(prec, args.steps, args.warmup, clocks)
+    # the other precision, for the FP32-vs-FP64 comparison (shorter)
+    other = "fp64" if prec == "fp32" else "fp32"
+    ms_o, sweep_o, launches_o, _ = timed(other, max(3, args.steps // 10), 2)
+
+    # correctness of this exact launch shape against the oracle (untimed)
+    step(prec)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    value = subsets * world * args.steps / (ms * 1e-3)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": c.name, "M": c.M, "squeezed": c.K, "r": [c.r_lo, c.r_hi], "eta": c.eta,
+                       "interferometer": c.interferometer, "n_pat": len(pats), "clicks": [c.n_lo, c.n_hi],
+                       "subsets_per_step": subsets, "precision": prec,
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "patterns_per_s": len(pats) * world * args.steps / (ms * 1e-3),
+            "gpu_launches": 4 * args.steps}
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel (the subset sweep): plain FP32/FP64 pipe, no tensor cores
+    props = torch.cuda.get_device_properties(dev)
+    smax = (ck or {}).get("sm_max_mhz") or 2070.0
+    lanes = 128 if prec == "fp32" else None
+    fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6
+    meas = {"fp32": ctx.peak_flops("fp32"), "fp64": ctx.peak_flops("fp64")}
+    peak = fp32_peak if prec == "fp32" else meas["fp64"]
+    achieved = flops / (sweep_ms / max(launches, 1) * 1e-3)
+    line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "sweep_kernel<%s>" % ("float" if prec == "fp32" else "double"),
+                        "kernel_ms": sweep_ms / max(launches, 1), "flops_per_launch": flops,
+                        "peak_basis": ("SMs x 128 FP32 lanes x 2 x max SM clock" if prec == "fp32"
+                                       else "measured FP64 FMA loop"),
+                        "fma_loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
+    line["other_precision"] = {"precision": other, "value": subsets * world * max(3, args.steps // 10) / (ms_o * 1e-3),
+                               "ms_per_step": ms_o / max(3, args.steps // 10),
+                               "kernel_ms": sweep_o / max(launches_o, 1)}
+    line["clocks"] = ck
+    # end to end through the public host-buffer entry point (copies inside the region)
+    K2 = max(3, min(args.steps, 50))
+    for _ in range(2):
+        ctx.run_host(U, r, c.eta, pats, precision=prec)
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        hres = ctx.run_host(U, r, c.eta, pats, precision=prec)
+    el = time.perf_counter() - t0
+    line["e2e"] = {"value": subsets * K2 / el, "unit": UNIT,
+                   "h2d_bytes_per_step": 16 * M * M + 8 * M + 16 * len(pats),
+                   "d2h_bytes_per_step": len(pats) * (8 + 8 + 8 + 4) + 4}
+    # oracle on the host cores: baseline and the stated error of this run
+    cb = cpu_baseline(U, r, c.eta, pats, n, budget_s=args.cpu_budget)
+    k = cb.pop("patterns")
+    ref = cb.pop("logP")
+    d = np.abs(res["logP"][:k] - ref)
+    line["cpu_baseline"] = cb
+    line["error_vs_oracle"] = {"patterns_checked": int(k), "max_abs_dlogP": float(d.max()) if k else None,
+                               "max_err_bound": float(res["err_bound"][:k].max()) if k else None,
+                               "all_within_bound": bool((d <= np.maximum(res["err_bound"][:k], 1e-10)).all()),
+                               "status_ok": int((res["status"] == 0).sum())}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="m24_exact")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

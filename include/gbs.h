@@ -1,0 +1,135 @@
+/*
+ * gbs.h -- C ABI of libgbs: click-pattern probabilities of a Gaussian boson
+ * sampler with threshold detectors, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Popova & Rubtsov, "Cracking the Quantum Advantage threshold for
+ * Gaussian Boson Sampling" (arXiv 2106.01445).  Section names below refer to
+ * that paper.
+ *
+ * Conventions shared by every entry point
+ *  - M modes, 1 <= M <= 128.  a_out = U a_in: U[i*M + j] is the amplitude from
+ *    input j to output (detector) i.  Complex arrays are interleaved (re, im).
+ *  - Quadratures in xp order (x_1..x_M, p_1..p_M), hbar = 1, vacuum sigma = I/2.
+ *    Every 2M x 2M matrix is row-major FP64.
+ *  - A click pattern is two uint64 words: bit i of word i/64 set <=> detector i
+ *    clicked.
+ *  - Pointers are DEVICE pointers unless the name ends in _host.  The caller
+ *    owns every buffer passed in; the context owns its workspace.
+ *  - Calls are asynchronous on the context's stream unless stated otherwise.
+ *    They return a gbs_status; a non-zero code leaves outputs undefined and
+ *    gbs_last_error() describes it.  Per-pattern problems are reported in the
+ *    per-pattern status array and never fail the batch.
+ *  - No entry point aborts, traps or waits without a bound.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbs_ctx gbs_ctx;
+
+typedef enum {
+    GBS_OK = 0,
+    GBS_E_INVALID = 1,     /* bad argument (size, range, pointer, non-unitary U) */
+    GBS_E_CUDA = 2,        /* a CUDA runtime call failed */
+    GBS_E_NOMEM = 3,       /* workspace too small (reserve more) or allocation failed */
+    GBS_E_NONPOSITIVE = 4, /* signed sum T <= its error bound: log P undefined */
+    GBS_E_NOT_SPD = 5,     /* a pivot of an SPD factorisation was not positive */
+    GBS_E_TIMEOUT = 6,     /* a bounded device loop ran out of iterations */
+    GBS_E_FIT = 7          /* approximation: a sector fit fell back to a lower order */
+} gbs_status;
+
+typedef enum {
+    GBS_FP64 = 0,        /* every factorisation and sum in FP64 */
+    GBS_FP32_SPLIT = 1   /* subset factorisations in FP32; signed sum compensated, FP64 result */
+} gbs_precision;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Errors: GBS_E_INVALID,
+ * GBS_E_CUDA. */
+int gbs_create(gbs_ctx **ctx, int device, void *cuda_stream);
+int gbs_destroy(gbs_ctx *ctx);
+int gbs_set_stream(gbs_ctx *ctx, void *cuda_stream);
+/* Last error message of this context (static storage owned by the context). */
+const char *gbs_last_error(const gbs_ctx *ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int gbs_version(void);
+
+/* Pre-size the workspace for up to n_pat patterns of up to n_max clicks so
+ * that later gbs_prob calls within those limits allocate nothing and never
+ * synchronise (needed for CUDA-graph capture).  Synchronous. */
+int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max);
+
+/* ---- state build (Methods, "Model" and "Partition function") ------------
+ * From U (M x M complex, unitary), squeezing r (M, r_j = 0 for vacuum
+ * inputs) and uniform transmission eta in (0, 1]:
+ *   sigma   = eta R sigma_in R^T + (1 - eta) I/2,  R = [[Re U, -Im U], [Im U, Re U]],
+ *   sigma_in = diag(e^{-2r}/2 (x), e^{2r}/2 (p)),
+ *   sigma_Q = sigma + I/2,  O = I - sigma_Q^{-1},  logdet = log det sigma_Q.
+ * sigma may be NULL.  logdet_sigmaQ points to one double on the device.
+ * status_dev: optional device int32 receiving GBS_OK or GBS_E_INVALID (U not
+ * unitary to 1e-10, r < 0 or not finite); if NULL the call synchronises and
+ * returns that status itself. */
+int gbs_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
+                    double *sigma, double *O, double *logdet_sigmaQ, int32_t *status_dev);
+
+/* ---- click-pattern probabilities ---------------------------------------
+ * Methods, "Probability of any sample" and Eq. (p(n)):
+ *   P(S) = det(sigma_Q)^{-1/2} sum_{Z subset S} (-1)^{|S|-|Z|} det(I - O_Z)^{-1/2},
+ * O_Z = rows/columns x and p of the modes in Z.
+ * order 0: the exact sum over all 2^n subsets (n <= 40).
+ * order 2..4: the paper's moment approximation (Methods, "Moments calculation"
+ *   and "Approximation method") from minors removing <= order detectors.
+ * Inputs: O (2M x 2M), logdet_sigmaQ (device, one double), patterns (n_pat x 2
+ * uint64).  Outputs per pattern (each may be NULL except logP):
+ *   logP      natural log of P(S)
+ *   kappa     condition number sum_Z |term| / |T| of the signed sum (order 0)
+ *   err_bound a-posteriori bound on |error of logP| from the arithmetic
+ *   status    gbs_status of this pattern
+ * Without a prior gbs_reserve covering the call, the call may synchronise once
+ * to size its workspace. */
+int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+             const uint64_t *patterns, int n_pat, int order, int precision, double *logP,
+             double *kappa, double *err_bound, int32_t *status);
+
+/* The whole path from HOST buffers: copies U, r and the patterns to the device,
+ * builds the state, evaluates every pattern and copies the per-pattern results
+ * back.  Synchronous.  Any of kappa_host, err_host, status_host may be NULL. */
+int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host, double eta,
+                 const uint64_t *patterns_host, int n_pat, int order, int precision,
+                 double *logP_host, double *kappa_host, double *err_host, int32_t *status_host);
+
+/* ---- synthetic click patterns -------------------------------------------
+ * Pattern i draws uint32 words w_0, w_1, ... from Philox4x32-10 (Salmon et al.,
+ * SC'11) with key (seed mod 2^32, seed / 2^32) and counters (i, block, stream, 0);
+ * n = n_lo + floor(w_0 (n_hi - n_lo + 1) / 2^32); then for k < n:
+ * j = k + floor(w_{k+1} (M - k) / 2^32), swap perm[k], perm[j]; the clicked set is
+ * perm[0..n-1].  out: n_pat x 2 uint64.  Bit-exact with the host generator. */
+int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_lo, int n_hi,
+                     int n_pat, uint64_t *out);
+
+/* ---- measurement helpers -------------------------------------------------
+ * Kernel timing: while enabled, the context records a CUDA event pair on its
+ * stream around every launch of the subset-sweep kernel.  gbs_timing_read
+ * synchronises the stream and returns the summed device time (ms) and launch
+ * count since the last reset (reset != 0 clears them).  At most 4096 launches
+ * are kept between reads; older pairs are folded in as the ring wraps. */
+int gbs_timing_enable(gbs_ctx *ctx, int enable);
+int gbs_timing_read(gbs_ctx *ctx, int reset, double *sweep_ms, long long *sweep_launches);
+
+/*
+ * Peak arithmetic throughput of this GPU's FP32 (kind 0) and FP64 (kind 1) FMA
+ * pipes from a register-resident dependent-FMA loop; result in FLOP/s (one FMA
+ * = 2 FLOP) at the clocks of the run.  Synchronous. */
+int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBS_H */

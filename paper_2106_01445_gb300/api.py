@@ -1,0 +1,156 @@
+"""Python binding of libgbs: argument marshalling between torch/numpy and the C ABI.
+
+Every step of the computation runs in libgbs's CUDA kernels; torch provides
+device memory and the stream only.  Names follow include/gbs.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT
+
+PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, GBS_FP64: GBS_FP64,
+              GBS_FP32_SPLIT: GBS_FP32_SPLIT}
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_f64(x, device) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
+
+
+def _complex_interleaved(U, device) -> torch.Tensor:
+    if isinstance(U, torch.Tensor):
+        U = U.to(device=device, dtype=torch.complex128).contiguous()
+        return torch.view_as_real(U).contiguous()
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    return torch.as_tensor(U.view(np.float64).reshape(U.shape[0], -1), device=device)
+
+
+def patterns_tensor(patterns, device) -> torch.Tensor:
+    """(n, 2) int64 tensor holding the uint64 pattern words bit for bit."""
+    if isinstance(patterns, torch.Tensor):
+        return patterns.to(device=device, dtype=torch.int64).contiguous()
+    a = np.ascontiguousarray(patterns, dtype=np.uint64).reshape(-1, 2)
+    return torch.as_tensor(a.view(np.int64), device=device)
+
+
+class Context:
+    """A libgbs context bound to one CUDA device and one stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        code = self.lib.gbs_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
+        if code:
+            raise GbsError(code, "gbs_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code: int):
+        if code:
+            raise GbsError(code, self.lib.gbs_last_error(self.h).decode())
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self.lib.gbs_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def reserve(self, n_pat: int, n_max: int):
+        self._check(self.lib.gbs_reserve(self.h, n_pat, n_max))
+
+    def build_state(self, U, r, eta: float, want_sigma: bool = False, check: bool = True):
+        """Device O (2M x 2M), log det sigma_Q (1,), sigma (or None), status (1,) int32."""
+        Ud = _complex_interleaved(U, self.device)
+        M = Ud.shape[0]
+        rd = _dev_f64(r, self.device)
+        O = torch.empty((2 * M, 2 * M), dtype=torch.float64, device=self.device)
+        logdet = torch.empty(1, dtype=torch.float64, device=self.device)
+        sigma = torch.empty_like(O) if want_sigma else None
+        status = None if check else torch.zeros(1, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gbs_build_state(self.h, M, _ptr(Ud), _ptr(rd), float(eta), _ptr(sigma),
+                                             _ptr(O), _ptr(logdet), _ptr(status)))
+        return dict(O=O, logdet=logdet, sigma=sigma, status=status)
+
+    def prob(self, O: torch.Tensor, logdet: torch.Tensor, patterns, order: int = 0,
+             precision="fp64", out=None):
+        """log P per pattern (device tensors): dict(logP, kappa, err_bound, status)."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        if out is None:
+            out = dict(logP=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       kappa=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       err_bound=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       status=torch.empty(n_pat, dtype=torch.int32, device=self.device))
+        self._check(self.lib.gbs_prob(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), n_pat, order,
+                                      PRECISIONS[precision], _ptr(out["logP"]), _ptr(out["kappa"]),
+                                      _ptr(out["err_bound"]), _ptr(out["status"])))
+        return out
+
+    def run_host(self, U, r, eta: float, patterns, order: int = 0, precision="fp64", out=None):
+        """The whole path from host (numpy) buffers; returns numpy arrays."""
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        M = U.shape[0]
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        pats = np.ascontiguousarray(patterns, dtype=np.uint64).reshape(-1, 2)
+        n_pat = pats.shape[0]
+        if out is None:
+            out = dict(logP=np.empty(n_pat), kappa=np.empty(n_pat), err_bound=np.empty(n_pat),
+                       status=np.empty(n_pat, dtype=np.int32))
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self._check(self.lib.gbs_run_host(self.h, M, c(U), c(r), float(eta), c(pats), n_pat, order,
+                                          PRECISIONS[precision], c(out["logP"]), c(out["kappa"]),
+                                          c(out["err_bound"]), c(out["status"])))
+        return out
+
+    def gen_patterns(self, seed: int, stream: int, M: int, n_lo: int, n_hi: int, n_pat: int):
+        out = torch.empty((n_pat, 2), dtype=torch.int64, device=self.device)
+        self._check(self.lib.gbs_gen_patterns(self.h, seed, stream, M, n_lo, n_hi, n_pat, _ptr(out)))
+        return out
+
+    def timing(self, enable: bool = True):
+        self._check(self.lib.gbs_timing_enable(self.h, 1 if enable else 0))
+
+    def timing_read(self, reset: bool = True):
+        """(summed device ms, launches) of the sweep kernel since the last reset."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self._check(self.lib.gbs_timing_read(self.h, 1 if reset else 0, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def build_state_into(self, Ud: torch.Tensor, rd: torch.Tensor, eta: float, O: torch.Tensor,
+                         logdet: torch.Tensor, status: torch.Tensor):
+        """State build into preallocated device buffers (U interleaved (M, 2M) f64); no sync."""
+        self._check(self.lib.gbs_build_state(self.h, Ud.shape[0], _ptr(Ud), _ptr(rd), float(eta), None,
+                                             _ptr(O), _ptr(logdet), _ptr(status)))
+
+    def peak_flops(self, kind: str = "fp32") -> float:
+        v = ctypes.c_double()
+        self._check(self.lib.gbs_peak_flops(self.h, 0 if kind == "fp32" else 1, ctypes.byref(v)))
+        return v.value
+
+
+def patterns_numpy(t: torch.Tensor) -> np.ndarray:
+    """(n, 2) uint64 numpy array from a device pattern tensor."""
+    return t.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,258 @@
+// C ABI entry points of libgbs: context, workspace and argument checks.
+// The arithmetic lives in state.cu, gen.cu and sweep.cu.
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gbs_internal.cuh"
+
+int gbs_fail(gbs_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int gbs_ws_ensure(gbs_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return GBS_OK;
+    GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) GBS_CUDA(ctx, cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    size_t want = bytes + bytes / 4 + (1 << 20);
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return gbs_fail(ctx, GBS_E_NOMEM, "cannot allocate %zu bytes of workspace", want);
+    }
+    ctx->ws_bytes = want;
+    return GBS_OK;
+}
+
+static int timing_fold_oldest(gbs_ctx *ctx) {
+    const int R = gbs_ctx::kTimingRing;
+    cudaEvent_t *e = ctx->tev + 2 * (ctx->t_tail % R);
+    GBS_CUDA(ctx, cudaEventSynchronize(e[1]));
+    float ms = 0.f;
+    GBS_CUDA(ctx, cudaEventElapsedTime(&ms, e[0], e[1]));
+    ctx->t_ms += ms;
+    ctx->t_launches += 1;
+    ctx->t_tail += 1;
+    return GBS_OK;
+}
+
+int gbs_timing_begin(gbs_ctx *ctx) {
+    if (!ctx->timing) return GBS_OK;
+    if (ctx->t_head - ctx->t_tail == gbs_ctx::kTimingRing) {
+        int st = timing_fold_oldest(ctx);
+        if (st) return st;
+    }
+    GBS_CUDA(ctx, cudaEventRecord(ctx->tev[2 * (ctx->t_head % gbs_ctx::kTimingRing)], ctx->stream));
+    return GBS_OK;
+}
+
+int gbs_timing_end(gbs_ctx *ctx) {
+    if (!ctx->timing) return GBS_OK;
+    GBS_CUDA(ctx, cudaEventRecord(ctx->tev[2 * (ctx->t_head % gbs_ctx::kTimingRing) + 1], ctx->stream));
+    ctx->t_head += 1;
+    return GBS_OK;
+}
+
+extern "C" {
+
+int gbs_version(void) { return 100; }
+
+int gbs_timing_enable(gbs_ctx *ctx, int enable) {
+    if (!ctx) return GBS_E_INVALID;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (enable && !ctx->tev) {
+        ctx->tev = new cudaEvent_t[2 * gbs_ctx::kTimingRing];
+        for (int i = 0; i < 2 * gbs_ctx::kTimingRing; ++i)
+            GBS_CUDA(ctx, cudaEventCreate(&ctx->tev[i]));
+    }
+    ctx->timing = enable != 0;
+    return GBS_OK;
+}
+
+int gbs_timing_read(gbs_ctx *ctx, int reset, double *sweep_ms, long long *sweep_launches) {
+    if (!ctx) return GBS_E_INVALID;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    while (ctx->tev && ctx->t_tail < ctx->t_head) {
+        int st = timing_fold_oldest(ctx);
+        if (st) return st;
+    }
+    if (sweep_ms) *sweep_ms = ctx->t_ms;
+    if (sweep_launches) *sweep_launches = ctx->t_launches;
+    if (reset) {
+        ctx->t_ms = 0.0;
+        ctx->t_launches = 0;
+    }
+    return GBS_OK;
+}
+
+int gbs_create(gbs_ctx **out, int device, void *cuda_stream) {
+    if (!out) return GBS_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GBS_E_INVALID;
+    }
+    gbs_ctx *ctx = new gbs_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost(&ctx->pinned, 4096) != cudaSuccess ||
+        cudaMalloc(&ctx->dscratch, 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GBS_E_CUDA;
+    }
+    *out = ctx;
+    return GBS_OK;
+}
+
+int gbs_destroy(gbs_ctx *ctx) {
+    if (!ctx) return GBS_E_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->host_io) cudaFree(ctx->host_io);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->dscratch) cudaFree(ctx->dscratch);
+    if (ctx->tev) {
+        for (int i = 0; i < 2 * gbs_ctx::kTimingRing; ++i) cudaEventDestroy(ctx->tev[i]);
+        delete[] ctx->tev;
+    }
+    delete ctx;
+    return GBS_OK;
+}
+
+int gbs_set_stream(gbs_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return GBS_E_INVALID;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return GBS_OK;
+}
+
+const char *gbs_last_error(const gbs_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
+    if (!ctx || n_pat < 0 || n_max < 0 || n_max > 40)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_reserve: bad n_pat %d / n_max %d", n_pat, n_max);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    long long units = 0;
+    for (int prec = 0; prec < 2; ++prec) {
+        long long u = sweep_units_upper_bound(n_pat, n_max, prec);
+        if (u > units) units = u;
+    }
+    int st = gbs_ws_ensure(ctx, sweep_workspace_bytes(n_pat, units));
+    if (st) return st;
+    ctx->reserved = true;
+    ctx->cap_pat = n_pat;
+    ctx->cap_units = units;
+    return GBS_OK;
+}
+
+int gbs_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
+                    double *sigma, double *O, double *logdet_sigmaQ, int32_t *status_dev) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || !U || !r || !O || !logdet_sigmaQ || !(eta > 0.0) || eta > 1.0)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_build_state: bad arguments (M=%d, eta=%g)", M, eta);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_build_state(ctx, M, U, r, eta, sigma, O, logdet_sigmaQ, status_dev);
+}
+
+int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+             const uint64_t *patterns, int n_pat, int order, int precision, double *logP,
+             double *kappa, double *err_bound, int32_t *status) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 0 || !O || !logdet_sigmaQ || (n_pat && (!patterns || !logP)))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: bad arguments (M=%d, n_pat=%d)", M, n_pat);
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: unknown precision %d", precision);
+    if (n_pat == 0) return GBS_OK;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (order == 0)
+        return sweep_exact(ctx, M, O, logdet_sigmaQ, patterns, n_pat, precision, logP, kappa,
+                           err_bound, status);
+    return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: order %d is not available", order);
+}
+
+int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host, double eta,
+                 const uint64_t *patterns_host, int n_pat, int order, int precision,
+                 double *logP_host, double *kappa_host, double *err_host, int32_t *status_host) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 0 || !U_host || !r_host || (n_pat && (!patterns_host || !logP_host)))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_run_host: bad arguments");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    size_t N = 2 * (size_t)M;
+    // device layout: U | r | O | logdet | status | patterns | logP | kappa | err | pstatus
+    size_t off_U = 0, off_r = off_U + 2 * M * M * 8, off_O = off_r + M * 8,
+           off_ld = off_O + N * N * 8, off_st = off_ld + 8, off_pat = off_st + 8,
+           off_lp = off_pat + (size_t)n_pat * 16, off_k = off_lp + (size_t)n_pat * 8,
+           off_e = off_k + (size_t)n_pat * 8, off_ps = off_e + (size_t)n_pat * 8,
+           total = off_ps + (size_t)n_pat * 4 + 256;
+    if (total > ctx->host_io_bytes) {
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->host_io) GBS_CUDA(ctx, cudaFree(ctx->host_io));
+        ctx->host_io = nullptr;
+        ctx->host_io_bytes = 0;
+        if (cudaMalloc(&ctx->host_io, total) != cudaSuccess) {
+            cudaGetLastError();
+            return gbs_fail(ctx, GBS_E_NOMEM, "gbs_run_host: cannot allocate %zu bytes", total);
+        }
+        ctx->host_io_bytes = total;
+    }
+    char *b = (char *)ctx->host_io;
+    cudaStream_t s = ctx->stream;
+    GBS_CUDA(ctx, cudaMemcpyAsync(b + off_U, U_host, 2 * M * M * 8, cudaMemcpyHostToDevice, s));
+    GBS_CUDA(ctx, cudaMemcpyAsync(b + off_r, r_host, M * 8, cudaMemcpyHostToDevice, s));
+    if (n_pat)
+        GBS_CUDA(ctx, cudaMemcpyAsync(b + off_pat, patterns_host, (size_t)n_pat * 16,
+                                      cudaMemcpyHostToDevice, s));
+    int st = launch_build_state(ctx, M, (double *)(b + off_U), (double *)(b + off_r), eta, nullptr,
+                                (double *)(b + off_O), (double *)(b + off_ld),
+                                (int32_t *)(b + off_st));
+    if (st) return st;
+    st = gbs_prob(ctx, M, (double *)(b + off_O), (double *)(b + off_ld), (uint64_t *)(b + off_pat),
+                  n_pat, order, precision, (double *)(b + off_lp), (double *)(b + off_k),
+                  (double *)(b + off_e), (int32_t *)(b + off_ps));
+    if (st) return st;
+    int32_t state_status = 0;
+    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, b + off_st, 4, cudaMemcpyDeviceToHost, s));
+    if (n_pat) {
+        GBS_CUDA(ctx, cudaMemcpyAsync(logP_host, b + off_lp, n_pat * 8, cudaMemcpyDeviceToHost, s));
+        if (kappa_host)
+            GBS_CUDA(ctx, cudaMemcpyAsync(kappa_host, b + off_k, n_pat * 8, cudaMemcpyDeviceToHost, s));
+        if (err_host)
+            GBS_CUDA(ctx, cudaMemcpyAsync(err_host, b + off_e, n_pat * 8, cudaMemcpyDeviceToHost, s));
+        if (status_host)
+            GBS_CUDA(ctx, cudaMemcpyAsync(status_host, b + off_ps, n_pat * 4, cudaMemcpyDeviceToHost, s));
+    }
+    GBS_CUDA(ctx, cudaStreamSynchronize(s));
+    memcpy(&state_status, ctx->pinned, 4);
+    if (state_status)
+        return gbs_fail(ctx, state_status, "gbs_run_host: state build rejected the inputs");
+    return GBS_OK;
+}
+
+int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_lo, int n_hi,
+                     int n_pat, uint64_t *out) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_lo < 0 || n_hi < n_lo || n_hi > M || n_pat < 0 || (n_pat && !out))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_gen_patterns: bad arguments");
+    if (n_pat == 0) return GBS_OK;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_gen_patterns(ctx, seed, stream, M, n_lo, n_hi, n_pat, out);
+}
+
+int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops) {
+    if (!ctx || !flops || (kind != 0 && kind != 1)) return GBS_E_INVALID;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return peak_flops(ctx, kind, flops);
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal declarations shared by the translation units of libgbs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/gbs.h"
+
+struct gbs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    char err[512] = {0};
+    // device workspace (grown on demand, or pre-sized by gbs_reserve)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool reserved = false;
+    long long cap_units = 0;  // unit partial slots in the workspace
+    int cap_pat = 0;          // patterns covered by the workspace
+    // pinned host scratch for small readbacks, and a small device scratch
+    void *pinned = nullptr;
+    int32_t *dscratch = nullptr;
+    // buffers of gbs_run_host (device copies of the host inputs)
+    void *host_io = nullptr;
+    size_t host_io_bytes = 0;
+    // persistent-grid sizes of the sweep kernels (CTAs per SM), by precision
+    int sweep_blocks_per_sm[2] = {0, 0};
+    // optional event timing of the sweep kernel launches
+    static const int kTimingRing = 4096;
+    bool timing = false;
+    cudaEvent_t *tev = nullptr;   // 2 * kTimingRing events
+    long long t_head = 0, t_tail = 0;
+    double t_ms = 0.0;
+    long long t_launches = 0;
+};
+
+// Bracket one sweep launch with timing events (no-ops unless timing is on).
+int gbs_timing_begin(gbs_ctx *ctx);
+int gbs_timing_end(gbs_ctx *ctx);
+
+// Record an error message on the context and return the code.
+int gbs_fail(gbs_ctx *ctx, int code, const char *fmt, ...);
+
+#define GBS_CUDA(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return gbs_fail((ctx), GBS_E_CUDA, "%s failed: %s (%s:%d)", #call,              \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+// Grow the context workspace to at least `bytes` (synchronises the stream).
+int gbs_ws_ensure(gbs_ctx *ctx, size_t bytes);
+
+// --- launchers implemented in the kernel translation units ---------------
+int launch_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
+                       double *sigma, double *O, double *logdet, int32_t *status_dev);
+int launch_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_lo,
+                        int n_hi, int n_pat, uint64_t *out);
+int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
+                const uint64_t *patterns, int n_pat, int precision, double *logP,
+                double *kappa, double *err_bound, int32_t *status);
+size_t sweep_workspace_bytes(int n_pat, long long units);
+long long sweep_units_upper_bound(int n_pat, int n_max, int precision);
+int peak_flops(gbs_ctx *ctx, int kind, double *flops);

@@ -1,0 +1,625 @@
+// Exact signed subset sweep (Methods, "Probability of any sample", Eq. (p(n))):
+//
+//   T(S) = sum_{Z subset S} (-1)^{|S|-|Z|} det(A_Z)^{-1/2},   A = I - O = sigma_Q^{-1},
+//   log P(S) = -1/2 log det sigma_Q + log T(S).
+//
+// The paper evaluates one determinant per subset ("2^n determinants").  Here the
+// subsets are the leaves of a binary include/exclude tree over the n modes of S
+// and the determinants share their factorisations: at a tree node the Schur
+// complement C of the modes already included is kept; excluding the next mode
+// drops its two rows (a view, no arithmetic), including it multiplies the
+// determinant by det(P) of its 2x2 pivot block and applies the rank-2 update
+// C' = C_rest - B P^{-1} B^T.  That is ~46 flops per subset instead of
+// (2|Z|)^3/3 for a fresh Cholesky.
+//
+// Work decomposition (one persistent launch over every pattern):
+//   unit   = (pattern, include/exclude choice of the first q modes): a CTA gathers
+//            A on the unit's modes, eliminates the included prefix modes, and
+//   expands the next L levels breadth-first in shared memory (2^L nodes), then
+//   every thread runs the last B levels of its node as straight-line code with
+//            the Schur complements in registers.
+// Signed terms are accumulated per thread with the error-free TwoSum (float-float
+// in the FP32 path, double-double in the FP64 path), reduced across the CTA in
+// double with TwoSum, stored per unit, and summed per pattern in unit order.
+#include <stdlib.h>
+
+#include "gbs_internal.cuh"
+
+namespace {
+
+constexpr int kL = 7;                  // breadth-first levels per unit
+constexpr int kThreads = 1 << kL;      // one thread per node after the expansion
+constexpr int kMaxN = 40;              // clicks per pattern on the exact path
+constexpr int kPlanThreads = 1024;
+
+__host__ __device__ constexpr int sym(int d) { return d * (d + 1) / 2; }
+// packed upper-triangle index of (i, j), i <= j, in a d x d symmetric matrix
+__host__ __device__ constexpr int pidx(int d, int i, int j) { return i * d - (i * (i - 1)) / 2 + (j - i); }
+// odd node stride: per-thread node reads hit distinct banks
+__host__ __device__ constexpr int nstride(int d) { return sym(d) | 1; }
+
+template <typename T> struct Prec;
+template <> struct Prec<float> { static constexpr int B = 6; static constexpr int idx = GBS_FP32_SPLIT; };
+template <> struct Prec<double> { static constexpr int B = 4; static constexpr int idx = GBS_FP64; };
+
+template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+
+// ---- shared-memory layout ----------------------------------------------------
+template <typename T> struct Layout {
+    static constexpr int B = Prec<T>::B;
+    static constexpr int R = kL + B;  // modes of a unit's level-0 matrix
+    static constexpr int level_size(int l) { return (1 << l) * nstride(2 * (R - l)); }
+    static constexpr int max_even() {
+        int m = 0;
+        for (int l = 0; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
+        return m;
+    }
+    static constexpr int max_odd() {
+        int m = sym(2 * kMaxN);  // prefix-elimination matrix lives here first
+        for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
+        return m;
+    }
+    static constexpr int dec_entries() {
+        int s = 0;
+        for (int m = 1; m <= R; ++m) s += sym(2 * m);
+        return s;
+    }
+    // byte offsets
+    static constexpr size_t off_X = 0;
+    static constexpr size_t off_Y = off_X + sizeof(T) * max_even();
+    static constexpr size_t off_tauX = off_Y + sizeof(T) * max_odd();
+    static constexpr size_t off_tauY = off_tauX + sizeof(T) * kThreads;
+    static constexpr size_t off_red = off_tauY + sizeof(T) * kThreads;      // 3 doubles per warp
+    static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
+    static constexpr size_t off_pos = off_modes + sizeof(int) * 128;
+    static constexpr size_t off_decoff = off_pos + sizeof(int) * 2 * kMaxN;
+    static constexpr size_t off_dec = off_decoff + sizeof(int) * (R + 2);
+    static constexpr size_t bytes = (off_dec + sizeof(uint16_t) * dec_entries() + 15) / 16 * 16;
+};
+
+// ---- error-free accumulation ----------------------------------------------------
+template <typename T> struct Acc {
+    T hi, lo, abs;
+};
+
+template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
+    T s = a.hi + x;
+    T bp = s - a.hi;
+    a.lo += (a.hi - (s - bp)) + (x - bp);
+    a.hi = s;
+}
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    double bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// ---- register-resident bottom levels ----------------------------------------------
+template <typename T, int MD> struct RegMat {
+    T v[sym(2 * MD)];
+    __device__ __forceinline__ T operator()(int i, int j) const { return v[pidx(2 * MD, i, j)]; }
+};
+template <typename T, int MD> struct SmemMat {
+    const T *p;
+    __device__ __forceinline__ T operator()(int i, int j) const { return p[pidx(2 * MD, i, j)]; }
+};
+
+// Subtree of the node whose matrix is A viewed from mode O on (MD - O modes).
+// NEG: the node's leaves carry a minus sign relative to the subtree root.
+// Levels at depth >= nreal are padding modes (identity block): include only.
+template <typename T, int MD, int O, bool NEG, typename Src>
+__device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, Acc<T> &acc) {
+    constexpr int m = MD - O;
+    constexpr int o = 2 * O;
+    const T p00 = A(o, o), p01 = A(o, o + 1), p11 = A(o + 1, o + 1);
+    const T det = p00 * p11 - p01 * p01;
+    const T rs = rsq<T>(det);
+    const bool real = depth < nreal;
+    if constexpr (m == 1) {
+        // the two leaves: include (+tau rs) and exclude (-tau)
+        const T inc = tau * rs;
+        T comb = real ? inc - tau : inc;
+        acc_add(acc, NEG ? -comb : comb);
+        acc.abs += real ? inc + tau : inc;
+    } else {
+        constexpr int d = 2 * (m - 1);
+        const T inv = rs * rs;
+        const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+        T b0[d], b1[d], w0[d], w1[d];
+#pragma unroll
+        for (int i = 0; i < d; ++i) {
+            b0[i] = A(o, o + 2 + i);
+            b1[i] = A(o + 1, o + 2 + i);
+            w0[i] = q00 * b0[i] + q01 * b1[i];
+            w1[i] = q01 * b0[i] + q11 * b1[i];
+        }
+        RegMat<T, m - 1> C;
+#pragma unroll
+        for (int i = 0; i < d; ++i)
+#pragma unroll
+            for (int j = i; j < d; ++j)
+                C.v[pidx(d, i, j)] = A(o + 2 + i, o + 2 + j) - w0[i] * b0[j] - w1[i] * b1[j];
+        dfs<T, m - 1, 0, NEG>(C, tau * rs, depth + 1, nreal, acc);
+        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc);
+    }
+}
+
+// ---- plan: order patterns by click count, one unit per prefix choice -----------------
+template <typename T> __host__ __device__ inline void unit_shape(int n, int &n_eff, int &L_eff, int &q) {
+    constexpr int B = Prec<T>::B;
+    n_eff = n > B ? n : B;
+    L_eff = n_eff - B < kL ? n_eff - B : kL;
+    q = n_eff - B - L_eff;
+}
+
+struct Plan {
+    unsigned long long *counter;
+    long long *total_units;
+    int *overflow;      // 1: the batch exceeded the workspace and was not evaluated
+    int *perm;          // sorted position -> pattern index
+    int *pat_n;         // clicks of each pattern (-1 invalid)
+    long long *unit_off;  // n_pat + 1, in sorted order
+    int *pflags;        // per sorted position: status bits
+    double *partials;   // 3 per unit
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_t *__restrict__ pats,
+                                                           int n_pat, long long cap_units, Plan pl) {
+    __shared__ int hist[130];
+    __shared__ long long chunk[kPlanThreads];
+    const int t = threadIdx.x;
+    for (int i = t; i < 130; i += kPlanThreads) hist[i] = 0;
+    __syncthreads();
+    const uint64_t mlo = M >= 64 ? ~0ull : ((1ull << M) - 1);
+    const uint64_t mhi = M > 64 ? (M >= 128 ? ~0ull : ((1ull << (M - 64)) - 1)) : 0ull;
+    for (int p = t; p < n_pat; p += kPlanThreads) {
+        uint64_t lo = pats[2 * p], hi = pats[2 * p + 1];
+        int n = __popcll(lo) + __popcll(hi);
+        bool ok = !(lo & ~mlo) && !(hi & ~mhi) && n <= kMaxN;
+        int key = ok ? n : -1;
+        pl.pat_n[p] = key;
+        atomicAdd(&hist[key + 1], 1);
+    }
+    __syncthreads();
+    if (t == 0) {  // bins from the largest n down to the invalid bin
+        int run = 0;
+        for (int b = 129; b >= 0; --b) {
+            int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int p = t; p < n_pat; p += kPlanThreads) {
+        int pos = atomicAdd(&hist[pl.pat_n[p] + 1], 1);
+        pl.perm[pos] = p;
+    }
+    __syncthreads();
+    // unit counts in sorted order, exclusive scan
+    const int per = (n_pat + kPlanThreads - 1) / kPlanThreads;
+    long long s = 0;
+    for (int i = t * per; i < n_pat && i < (t + 1) * per; ++i) {
+        int n = pl.pat_n[pl.perm[i]];
+        int n_eff, L_eff, q;
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q);
+        s += n < 0 ? 0 : (1ll << q);
+    }
+    chunk[t] = s;
+    __syncthreads();
+    for (int off = 1; off < kPlanThreads; off <<= 1) {
+        long long v = t >= off ? chunk[t - off] : 0;
+        __syncthreads();
+        chunk[t] += v;
+        __syncthreads();
+    }
+    long long run = chunk[t] - s;
+    for (int i = t * per; i < n_pat && i < (t + 1) * per; ++i) {
+        pl.unit_off[i] = run;
+        pl.pflags[i] = 0;
+        int n = pl.pat_n[pl.perm[i]];
+        int n_eff, L_eff, q;
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q);
+        run += n < 0 ? 0 : (1ll << q);
+    }
+    if (t == kPlanThreads - 1) {
+        long long total = chunk[t];
+        pl.unit_off[n_pat] = total;
+        bool over = total > cap_units;
+        *pl.total_units = over ? 0 : total;
+        *pl.overflow = over ? 1 : 0;
+        *pl.counter = 0;
+    }
+}
+
+// ---- the sweep ------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__restrict__ O,
+                                                        const uint64_t *__restrict__ pats,
+                                                        int n_pat, Plan pl) {
+    using Lay = Layout<T>;
+    constexpr int B = Prec<T>::B;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *X = (T *)(smem + Lay::off_X);
+    T *Y = (T *)(smem + Lay::off_Y);
+    T *tauX = (T *)(smem + Lay::off_tauX);
+    T *tauY = (T *)(smem + Lay::off_tauY);
+    double *red = (double *)(smem + Lay::off_red);
+    int *modes = (int *)(smem + Lay::off_modes);
+    int *pos = (int *)(smem + Lay::off_pos);
+    int *decoff = (int *)(smem + Lay::off_decoff);
+    uint16_t *dec = (uint16_t *)(smem + Lay::off_dec);
+    __shared__ long long s_unit;
+    __shared__ int s_n, s_k, s_flag;
+    __shared__ double s_tpre;
+
+    const int t = threadIdx.x;
+    const int N2 = 2 * M;
+    // decode tables (i, j) of packed indices for every even dimension 2m <= 2R
+    if (t == 0) {
+        int off = 0;
+        for (int m = 1; m <= Lay::R; ++m) {
+            decoff[m] = off;
+            off += sym(2 * m);
+        }
+    }
+    __syncthreads();
+    for (int m = 1; m <= Lay::R; ++m) {
+        const int d = 2 * m;
+        for (int i = t; i < d; i += kThreads)
+            for (int j = i; j < d; ++j) dec[decoff[m] + pidx(d, i, j)] = (uint16_t)(i | (j << 8));
+    }
+    const long long total = *pl.total_units;
+
+    for (;;) {
+        if (t == 0) s_unit = (long long)atomicAdd(pl.counter, 1ull);
+        __syncthreads();
+        const long long u = s_unit;
+        if (u >= total) break;
+        // sorted pattern position: unit_off[sp] <= u < unit_off[sp + 1]
+        int lo = 0, hi = n_pat;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (pl.unit_off[mid] <= u) lo = mid; else hi = mid;
+        }
+        const int sp = lo;
+        const int p = pl.perm[sp];
+        const long long prefix = u - pl.unit_off[sp];
+        const uint64_t wlo = pats[2 * p], whi = pats[2 * p + 1];
+        if (t == 0) {
+            int n = 0;
+            for (int i = 0; i < M; ++i) {
+                uint64_t w = i < 64 ? wlo : whi;
+                if (w >> (i & 63) & 1ull) modes[n++] = i;
+            }
+            s_n = n;
+            s_flag = 0;
+        }
+        __syncthreads();
+        const int n = s_n;
+        int n_eff, L_eff, q;
+        unit_shape<T>(n, n_eff, L_eff, q);
+        const int r = L_eff + B;
+        // rows of the unit matrix: included prefix modes, then modes q .. n_eff-1
+        if (t == 0) {
+            int k = 0;
+            for (int a = 0; a < q; ++a)
+                if (prefix >> a & 1) pos[k++] = a;
+            for (int a = q; a < n_eff; ++a) pos[k + a - q] = a;
+            s_k = k;
+        }
+        __syncthreads();
+        const int k = s_k;
+        const int D0 = 2 * (k + r);
+        // gather G = (I - O) on those rows into Y (packed), padding modes as identity
+        for (int i = t; i < D0; i += kThreads) {
+            const int a = pos[i >> 1];
+            const int si = a < n ? modes[a] + (i & 1) * M : -1;
+            for (int j = i; j < D0; ++j) {
+                const int b = pos[j >> 1];
+                T v;
+                if (si < 0 || b >= n) {
+                    v = (i == j) ? T(1) : T(0);
+                } else {
+                    const int sj = modes[b] + (j & 1) * M;
+                    v = (T)((i == j ? 1.0 : 0.0) - O[(size_t)si * N2 + sj]);
+                }
+                Y[pidx(D0, i, j)] = v;
+            }
+        }
+        __syncthreads();
+        // eliminate the included prefix modes (2x2 block pivots)
+        double tpre = 1.0;
+        for (int e = 0; e < k; ++e) {
+            const int c0 = 2 * e;
+            const T p00 = Y[pidx(D0, c0, c0)], p01 = Y[pidx(D0, c0, c0 + 1)],
+                    p11 = Y[pidx(D0, c0 + 1, c0 + 1)];
+            const T det = p00 * p11 - p01 * p01;
+            if (!(det > T(0))) s_flag = 1;
+            tpre *= rsqrt((double)det);
+            const T inv = T(1) / det;
+            const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+            for (int i = c0 + 2 + t; i < D0; i += kThreads) {
+                const T bi0 = Y[pidx(D0, c0, i)], bi1 = Y[pidx(D0, c0 + 1, i)];
+                const T wi0 = q00 * bi0 + q01 * bi1, wi1 = q01 * bi0 + q11 * bi1;
+                for (int j = i; j < D0; ++j)
+                    Y[pidx(D0, i, j)] -= wi0 * Y[pidx(D0, c0, j)] + wi1 * Y[pidx(D0, c0 + 1, j)];
+            }
+            __syncthreads();
+        }
+        // level 0 of the expansion: the trailing 2r x 2r block, packed into X
+        {
+            const int d = 2 * r, o = 2 * k;
+            for (int i = t; i < d; i += kThreads)
+                for (int j = i; j < d; ++j) X[pidx(d, i, j)] = Y[pidx(D0, o + i, o + j)];
+            if (t == 0) tauX[0] = T(1);
+        }
+        __syncthreads();
+        // breadth-first expansion of L_eff levels
+        for (int l = 0; l < L_eff; ++l) {
+            const T *src = (l & 1) ? Y : X;
+            T *dst = (l & 1) ? X : Y;
+            const T *tsrc = (l & 1) ? tauY : tauX;
+            T *tdst = (l & 1) ? tauX : tauY;
+            const int d = 2 * (r - l), dc = d - 2;
+            const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
+            const int lg_tpc = kL - (l + 1);
+            const int c = t >> lg_tpc, sub = t & ((1 << lg_tpc) - 1);
+            const int parent = c >> 1;
+            const bool inc = c & 1;
+            const T *P = src + parent * sstr;
+            T *Cd = dst + c * dstr;
+            const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
+            const T det = p00 * p11 - p01 * p01;
+            const T rs = rsq<T>(det);
+            const T inv = rs * rs;
+            const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+            const uint16_t *dd = dec + decoff[dc >> 1];
+            for (int e = sub; e < Ec; e += (1 << lg_tpc)) {
+                const int ij = dd[e];
+                const int i = ij & 0xff, j = ij >> 8;
+                T v = P[pidx(d, i + 2, j + 2)];
+                if (inc) {
+                    const T bi0 = P[pidx(d, 0, i + 2)], bi1 = P[pidx(d, 1, i + 2)];
+                    const T bj0 = P[pidx(d, 0, j + 2)], bj1 = P[pidx(d, 1, j + 2)];
+                    v -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
+                }
+                Cd[e] = v;
+            }
+            if (sub == 0) {
+                tdst[c] = inc ? tsrc[parent] * rs : tsrc[parent];
+                if (!(det > T(0))) s_flag = 1;
+            }
+            __syncthreads();
+        }
+        // register-resident bottom B levels, one node per thread
+        double c_hi = 0.0, c_lo = 0.0, c_abs = 0.0;
+        if (t < (1 << L_eff)) {
+            const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
+            const T tau_node = ((L_eff & 1) ? tauY : tauX)[t];
+            const int nreal = n - (n_eff - B);
+            Acc<T> acc{T(0), T(0), T(0)};
+            SmemMat<T, B> A{node};
+            dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
+            const int excl = (q - k) + (L_eff - __popc(t));
+            const double sgn = (excl & 1) ? -1.0 : 1.0;
+            const double tn = (double)tau_node;
+            c_hi = sgn * tn * (double)acc.hi;
+            c_lo = sgn * tn * (double)acc.lo;
+            c_abs = tn * (double)acc.abs;
+            if (!(acc.abs == acc.abs) || !(tau_node == tau_node)) s_flag = 1;
+        }
+        // deterministic CTA reduction (TwoSum tree)
+        for (int off = 16; off; off >>= 1) {
+            double oh = __shfl_xor_sync(0xffffffffu, c_hi, off);
+            double ol = __shfl_xor_sync(0xffffffffu, c_lo, off);
+            double oa = __shfl_xor_sync(0xffffffffu, c_abs, off);
+            double s, e;
+            two_sum(c_hi, oh, s, e);
+            c_hi = s;
+            c_lo += ol + e;
+            c_abs += oa;
+        }
+        if ((t & 31) == 0) {
+            red[3 * (t >> 5)] = c_hi;
+            red[3 * (t >> 5) + 1] = c_lo;
+            red[3 * (t >> 5) + 2] = c_abs;
+        }
+        if (t == 0) s_tpre = tpre;
+        __syncthreads();
+        if (t == 0) {
+            double h = red[0], l = red[1], a = red[2];
+            for (int w = 1; w < kThreads / 32; ++w) {
+                double s, e;
+                two_sum(h, red[3 * w], s, e);
+                h = s;
+                l += red[3 * w + 1] + e;
+                a += red[3 * w + 2];
+            }
+            const double tp = s_tpre;
+            double *out = pl.partials + 3 * u;
+            out[0] = h * tp;
+            out[1] = l * tp;
+            out[2] = a * tp;
+            if (s_flag || !(tp == tp)) atomicOr(pl.pflags + sp, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- per-pattern result: sum of the pattern's unit partials in unit order -------------
+template <typename T>
+__global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Plan pl,
+                                double *__restrict__ logP, double *__restrict__ kappa,
+                                double *__restrict__ err_bound, int32_t *__restrict__ status) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_pat) return;
+    const int sp = warp;
+    const int p = pl.perm[sp];
+    const int n = pl.pat_n[p];
+    const bool batch_over = *pl.overflow != 0;
+    const long long u0 = pl.unit_off[sp], u1 = pl.unit_off[sp + 1];
+    double h = 0.0, l = 0.0, a = 0.0;
+    if (!batch_over)
+        for (long long u = u0 + lane; u < u1; u += 32) {
+            const double *q = pl.partials + 3 * u;
+            double s, e;
+            two_sum(h, q[0], s, e);
+            h = s;
+            l += q[1] + e;
+            a += q[2];
+        }
+    for (int off = 1; off < 32; off <<= 1) {  // fixed pairing order: deterministic
+        double oh = __shfl_down_sync(0xffffffffu, h, off);
+        double ol = __shfl_down_sync(0xffffffffu, l, off);
+        double oa = __shfl_down_sync(0xffffffffu, a, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            double s, e;
+            two_sum(h, oh, s, e);
+            h = s;
+            l += ol + e;
+            a += oa;
+        }
+    }
+    if (lane) return;
+    const double Tv = h + l;
+    int st = GBS_OK;
+    double lp = nan(""), kap = nan(""), eb = nan("");
+    if (n < 0) {
+        st = GBS_E_INVALID;
+    } else if (batch_over) {
+        st = GBS_E_NOMEM;
+    } else if (pl.pflags[sp] != 0) {
+        st = GBS_E_NOT_SPD;
+    } else {
+        // a-posteriori bound: every term carries a relative error of at most
+        // c (2n + 4) u from its chain of 2x2 pivots; the signed sum amplifies by kappa.
+        const double uu = Prec<T>::idx == GBS_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        kap = a / fabs(Tv);
+        const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * 1.1102230246251565e-16;
+        if (!(Tv > 0.0) || !(rel < 0.5)) {
+            st = GBS_E_NONPOSITIVE;
+        } else {
+            lp = -0.5 * (*logdet) + log(Tv);
+            eb = -log1p(-rel);
+        }
+    }
+    logP[p] = lp;
+    if (kappa) kappa[p] = kap;
+    if (err_bound) err_bound[p] = eb;
+    if (status) status[p] = st;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct WsOffsets {
+    size_t counter, total, overflow, perm, pat_n, unit_off, pflags, partials, end;
+};
+
+WsOffsets ws_offsets(int n_pat, long long units) {
+    WsOffsets o;
+    o.counter = 0;
+    o.total = 8;
+    o.overflow = 16;
+    o.perm = align256(20);
+    o.pat_n = align256(o.perm + 4 * (size_t)n_pat);
+    o.unit_off = align256(o.pat_n + 4 * (size_t)n_pat);
+    o.pflags = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
+    o.partials = align256(o.pflags + 4 * (size_t)n_pat);
+    o.end = o.partials + 24 * (size_t)units;
+    return o;
+}
+
+Plan plan_from(void *ws, int n_pat) {
+    WsOffsets o = ws_offsets(n_pat, 0);
+    char *b = (char *)ws;
+    Plan pl;
+    pl.counter = (unsigned long long *)(b + o.counter);
+    pl.total_units = (long long *)(b + o.total);
+    pl.overflow = (int *)(b + o.overflow);
+    pl.perm = (int *)(b + o.perm);
+    pl.pat_n = (int *)(b + o.pat_n);
+    pl.unit_off = (long long *)(b + o.unit_off);
+    pl.pflags = (int *)(b + o.pflags);
+    pl.partials = (double *)(b + o.partials);
+    return pl;
+}
+
+template <typename T>
+int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
+              int n_pat, double *logP, double *kappa, double *err_bound, int32_t *status) {
+    using Lay = Layout<T>;
+    const int pi = Prec<T>::idx;
+    if (ctx->reserved && n_pat > ctx->cap_pat)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: %d patterns exceed the reservation of %d",
+                        n_pat, ctx->cap_pat);
+    if (ctx->sweep_blocks_per_sm[pi] == 0) {
+        GBS_CUDA(ctx, cudaFuncSetAttribute(sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Lay::bytes));
+        int nb = 0;
+        GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T>, kThreads,
+                                                                    Lay::bytes));
+        if (nb < 1) return gbs_fail(ctx, GBS_E_CUDA, "sweep kernel does not fit on an SM");
+        ctx->sweep_blocks_per_sm[pi] = nb;
+    }
+    long long cap;
+    if (ctx->reserved) {
+        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+    } else {
+        int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, 0).end);
+        if (st) return st;
+        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+    }
+    Plan pl = plan_from(ctx->ws, n_pat);
+    plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    if (!ctx->reserved) {
+        // size the unit partials: one small readback
+        GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.unit_off + n_pat, 8, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        long long need = *(long long *)ctx->pinned;
+        if (need > cap) {
+            int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, need).end);
+            if (st) return st;
+            cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+            pl = plan_from(ctx->ws, n_pat);
+            plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
+            GBS_CUDA(ctx, cudaGetLastError());
+        }
+    }
+    const int grid = ctx->num_sms * ctx->sweep_blocks_per_sm[pi];
+    int st = gbs_timing_begin(ctx);
+    if (st) return st;
+    sweep_kernel<T><<<grid, kThreads, Lay::bytes, ctx->stream>>>(M, O, pats, n_pat, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    st = gbs_timing_end(ctx);
+    if (st) return st;
+    const int fthreads = 256, fblocks = (n_pat * 32 + fthreads - 1) / fthreads;
+    finalize_kernel<T><<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa,
+                                                             err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
+
+}  // namespace
+
+size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_pat, units).end; }
+
+long long sweep_units_upper_bound(int n_pat, int n_max, int precision) {
+    int n_eff, L_eff, q;
+    if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q);
+    else unit_shape<float>(n_max, n_eff, L_eff, q);
+    return (long long)n_pat << q;
+}
+
+int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
+                const uint64_t *patterns, int n_pat, int precision, double *logP, double *kappa,
+                double *err_bound, int32_t *status) {
+    if (precision == GBS_FP64)
+        return run_sweep<double>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+    return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+}

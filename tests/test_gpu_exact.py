@@ -1,0 +1,209 @@
+"""GPU parity of the exact path (state build, pattern generation, signed subset
+sweep) against the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import gbs_inputs as g
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+# |d log P| bounds: FP64 path 1e-10 wherever the a-posteriori bound is below it;
+# otherwise (and in the FP32 split) the library's own err_bound must hold.
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_ok):
+    from paper_2106_01445_gb300 import build
+    build.build()
+    from paper_2106_01445_gb300.api import Context
+    return Context(0)
+
+
+def gpu_state(ctx, U, r, eta):
+    return ctx.build_state(U, r, eta, want_sigma=True)
+
+
+def gpu_prob(ctx, st, pats, precision, order=0):
+    out = ctx.prob(st["O"], st["logdet"], pats, order=order, precision=precision)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def check_against_oracle(res, ref, precision):
+    ok = ref["status"] == 0
+    assert (res["status"][ok] == 0).all(), res["status"][ok]
+    d = np.abs(res["logP"][ok] - ref["logP"][ok])
+    bound = res["err_bound"][ok]
+    if precision == "fp64":
+        assert (d <= np.maximum(TOL64, bound)).all(), (d.max(), bound[d.argmax()])
+        tight = bound <= 1e-11
+        assert (d[tight] <= TOL64).all()
+    else:
+        assert (d <= bound).all(), (d.max(), bound[d.argmax()], res["kappa"][ok][d.argmax()])
+    return d
+
+
+@pytest.mark.parametrize("name,eta", [("m8_all", 1.0), ("m24_exact", 0.5), ("m100_approx", 0.3),
+                                      ("m32_grad", 0.6)])
+def test_state_build_parity(ctx, name, eta):
+    c = g.CONFIGS[name]
+    U, r = c.unitary(), c.squeezing()
+    st = gpu_state(ctx, U, r, eta)
+    ref = oracle.build_state(U, r, eta)
+    assert np.abs(st["O"].cpu().numpy() - ref.O).max() < 1e-13
+    assert np.abs(st["sigma"].cpu().numpy() - ref.sigma).max() < 1e-12 * np.abs(ref.sigma).max()
+    assert abs(st["logdet"].item() - ref.logdet) < 1e-12 * max(1.0, abs(ref.logdet))
+
+
+def test_state_build_rejects_bad_input(ctx):
+    from paper_2106_01445_gb300 import GbsError
+    U = g.haar_unitary(5, 1)
+    with pytest.raises(GbsError):
+        ctx.build_state(1.01 * U, np.full(5, 0.5), 0.5)
+    with pytest.raises(GbsError):
+        ctx.build_state(U, np.array([0.5, -0.1, 0, 0, 0]), 0.5)
+    with pytest.raises(GbsError):
+        ctx.build_state(U, np.full(5, 0.5), 1.5)
+
+
+@pytest.mark.parametrize("M,n_lo,n_hi,n_pat,seed,stream", [
+    (24, 12, 20, 1024, 2, 2), (50, 10, 40, 4096, 3, 2), (100, 40, 90, 3000, 5, 2),
+    (100, 30, 30, 64, 5, 3), (128, 0, 128, 500, 7, 2), (8, 0, 8, 333, 0, 2)])
+def test_gen_patterns_bit_exact(ctx, M, n_lo, n_hi, n_pat, seed, stream):
+    from paper_2106_01445_gb300.api import patterns_numpy
+    dev = patterns_numpy(ctx.gen_patterns(seed, stream, M, n_lo, n_hi, n_pat))
+    host = g.gen_patterns(seed, M, n_lo, n_hi, n_pat, stream=stream)
+    assert np.array_equal(dev, host)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("eta", [1.0, 0.5])
+def test_all_patterns_m8(ctx, precision, eta):
+    c = g.CONFIGS["m8_all"]
+    U, r = c.unitary(), c.squeezing()
+    pats = g.all_patterns(8)
+    res = gpu_prob(ctx, gpu_state(ctx, U, r, eta), pats, precision)
+    ref = oracle.prob_exact(oracle.build_state(U, r, eta), pats)
+    check_against_oracle(res, ref, precision)
+    total = np.exp(res["logP"]).sum()
+    assert abs(total - 1.0) < (1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_uneven_batch_all_sizes(ctx, precision):
+    # one launch over patterns of every size 0..22, ragged, incl. the padding
+    # (n < B), one-unit and multi-unit shapes
+    M = 26
+    U = g.haar_unitary(M, 101)
+    r = g.squeezing(M, 13, 0.6, 1.2, 101)
+    rng = np.random.default_rng(5)
+    modes_list = [sorted(rng.choice(M, size=n, replace=False)) for n in list(range(0, 23)) + [3, 7, 13, 14, 15]]
+    pats = np.stack([g.modes_to_pattern(m) for m in modes_list])
+    st = gpu_state(ctx, U, r, 0.55)
+    res = gpu_prob(ctx, st, pats, precision)
+    ref = oracle.prob_exact(oracle.build_state(U, r, 0.55), pats)
+    check_against_oracle(res, ref, precision)
+    assert abs(res["logP"][0] + 0.5 * st["logdet"].item()) < 1e-14   # empty pattern
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_m24_config_sample(ctx, precision):
+    # the 24-mode workload in the benchmark's launch shape (all 1024 patterns in one
+    # call); the oracle checks a sample spanning every click count
+    c = g.CONFIGS["m24_exact"]
+    U, r = c.unitary(), c.squeezing()
+    pats = c.patterns()
+    res = gpu_prob(ctx, gpu_state(ctx, U, r, c.eta), pats, precision)
+    n = np.array([len(g.pattern_modes(p)) for p in pats])
+    idx = []
+    for k in range(12, 21):
+        w = np.nonzero(n == k)[0]
+        idx += list(w[: (3 if k <= 17 else 1)])
+    idx = np.array(idx)
+    ref = oracle.prob_exact(oracle.build_state(U, r, c.eta), pats[idx])
+    sub = {k: v[idx] for k, v in res.items()}
+    check_against_oracle(sub, ref, precision)
+    assert (res["status"] == 0).all()
+
+
+def test_fp32_and_fp64_agree_full_config(ctx):
+    c = g.CONFIGS["m24_exact"]
+    st = gpu_state(ctx, c.unitary(), c.squeezing(), c.eta)
+    a = gpu_prob(ctx, st, c.patterns(), "fp64")
+    b = gpu_prob(ctx, st, c.patterns(), "fp32")
+    d = np.abs(a["logP"] - b["logP"])
+    assert (d <= b["err_bound"] + a["err_bound"]).all()
+
+
+def test_block_diagonal_factorises_at_n30(ctx):
+    # Property at full size: with a block-diagonal interferometer the click
+    # probability factorises over blocks, each block is exact from the oracle.
+    M, bs = 100, 4
+    U = np.zeros((M, M), dtype=complex)
+    for b in range(M // bs):
+        U[b * bs:(b + 1) * bs, b * bs:(b + 1) * bs] = g.haar_unitary(bs, 200 + b)
+    r = g.squeezing(M, M, 0.4, 0.9, 77)
+    eta = 0.3
+    pats = g.gen_patterns(5, M, 30, 30, 4, stream=g.STREAM_ANCHORS)
+    st = gpu_state(ctx, U, r, eta)
+    for precision in ("fp64", "fp32"):
+        res = gpu_prob(ctx, st, pats, precision)
+        for i, p in enumerate(pats):
+            modes = set(g.pattern_modes(p))
+            lp = 0.0
+            for b in range(M // bs):
+                blk = list(range(b * bs, (b + 1) * bs))
+                sub = oracle.build_state(U[np.ix_(blk, blk)], r[blk], eta)
+                loc = [j for j, m in enumerate(blk) if m in modes]
+                lp += oracle.prob_exact(sub, g.modes_to_pattern(loc)[None])["logP"][0]
+            assert res["status"][i] == 0
+            tol = TOL64 if precision == "fp64" else res["err_bound"][i]
+            assert abs(res["logP"][i] - lp) <= max(tol, res["err_bound"][i]), (precision, i)
+
+
+def test_large_pattern_against_parallel_oracle(ctx):
+    # one 22-click pattern of the 24-mode device, oracle over 4M subsets in parallel
+    c = g.CONFIGS["m24_exact"]
+    U, r = c.unitary(), c.squeezing()
+    modes = [m for m in range(24) if m not in (3, 17)]
+    st = gpu_state(ctx, U, r, c.eta)
+    ref_state = oracle.build_state(U, r, c.eta)
+    T = oracle.subset_sum(ref_state.A, 24, modes, nchunk=256)
+    ref = -0.5 * ref_state.logdet + math.log(T[0] + T[1])
+    for precision in ("fp64", "fp32"):
+        res = gpu_prob(ctx, st, g.modes_to_pattern(modes)[None], precision)
+        tol = max(TOL64, res["err_bound"][0]) if precision == "fp64" else res["err_bound"][0]
+        assert abs(res["logP"][0] - ref) <= tol
+
+
+def test_deterministic(ctx):
+    c = g.CONFIGS["m24_exact"]
+    st = gpu_state(ctx, c.unitary(), c.squeezing(), c.eta)
+    for precision in ("fp64", "fp32"):
+        a = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
+        b = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
+        assert np.array_equal(a, b)
+
+
+def test_invalid_patterns_flagged(ctx):
+    M = 10
+    st = gpu_state(ctx, g.haar_unitary(M, 3), g.squeezing(M, 5, 0.5, 1.0, 3), 0.7)
+    pats = np.array([[1 << 12, 0], [0b1011, 0], [0, 1], [(1 << 41) - 1, 0]], dtype=np.uint64)
+    res = gpu_prob(ctx, st, pats, "fp64")
+    assert res["status"][0] == 1 and res["status"][2] == 1    # detector index >= M
+    assert res["status"][1] == 0
+    assert res["status"][3] == 1                               # beyond M
+
+
+def test_host_entry_point_matches_device_path(ctx):
+    c = g.CONFIGS["m24_exact"]
+    U, r, pats = c.unitary(), c.squeezing(), c.patterns()[:200]
+    dev = gpu_prob(ctx, gpu_state(ctx, U, r, c.eta), pats, "fp32")
+    host = ctx.run_host(U, r, c.eta, pats, precision="fp32")
+    assert np.array_equal(dev["logP"], host["logP"])
+    assert np.array_equal(dev["status"], host["status"])
