@@ -27,8 +27,9 @@
 
 namespace {
 
-constexpr int kL = 7;                  // breadth-first levels per unit
+constexpr int kL = 7;                  // breadth-first levels per sub-unit
 constexpr int kThreads = 1 << kL;      // one thread per node after the expansion
+constexpr int kS = 3;                  // prefix levels a CTA loops over inside one unit
 constexpr int kMaxN = 40;              // clicks per pattern on the exact path
 constexpr int kPlanThreads = 1024;
 
@@ -69,7 +70,9 @@ template <typename T> struct Layout {
     // byte offsets
     static constexpr size_t off_X = 0;
     static constexpr size_t off_Y = off_X + sizeof(T) * max_even();
-    static constexpr size_t off_tauX = off_Y + sizeof(T) * max_odd();
+    static constexpr int ublk() { return sym(2 * (kS + R)); }
+    static constexpr size_t off_U = off_Y + sizeof(T) * max_odd();
+    static constexpr size_t off_tauX = off_U + sizeof(T) * ublk();
     static constexpr size_t off_tauY = off_tauX + sizeof(T) * kThreads;
     static constexpr size_t off_red = off_tauY + sizeof(T) * kThreads;      // 3 doubles per warp
     static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
@@ -148,11 +151,15 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 }
 
 // ---- plan: order patterns by click count, one unit per prefix choice -----------------
-template <typename T> __host__ __device__ inline void unit_shape(int n, int &n_eff, int &L_eff, int &q) {
+// n_eff = clicks padded to >= B; L_eff breadth-first levels; q prefix levels of
+// which the first q - s index units and the last s are looped over in the CTA.
+template <typename T>
+__host__ __device__ inline void unit_shape(int n, int &n_eff, int &L_eff, int &q, int &s) {
     constexpr int B = Prec<T>::B;
     n_eff = n > B ? n : B;
     L_eff = n_eff - B < kL ? n_eff - B : kL;
     q = n_eff - B - L_eff;
+    s = q < kS ? q : kS;
 }
 
 struct Plan {
@@ -204,9 +211,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
     long long s = 0;
     for (int i = t * per; i < n_pat && i < (t + 1) * per; ++i) {
         int n = pl.pat_n[pl.perm[i]];
-        int n_eff, L_eff, q;
-        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q);
-        s += n < 0 ? 0 : (1ll << q);
+        int n_eff, L_eff, q, ss;
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss);
+        s += n < 0 ? 0 : (1ll << (q - ss));
     }
     chunk[t] = s;
     __syncthreads();
@@ -221,9 +228,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
         pl.unit_off[i] = run;
         pl.pflags[i] = 0;
         int n = pl.pat_n[pl.perm[i]];
-        int n_eff, L_eff, q;
-        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q);
-        run += n < 0 ? 0 : (1ll << q);
+        int n_eff, L_eff, q, ss;
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss);
+        run += n < 0 ? 0 : (1ll << (q - ss));
     }
     if (t == kPlanThreads - 1) {
         long long total = chunk[t];
@@ -254,6 +261,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     uint16_t *dec = (uint16_t *)(smem + Lay::off_dec);
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
+    T *Ub = (T *)(smem + Lay::off_U);
     __shared__ double s_tpre;
 
     const int t = threadIdx.x;
@@ -300,41 +308,42 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         }
         __syncthreads();
         const int n = s_n;
-        int n_eff, L_eff, q;
-        unit_shape<T>(n, n_eff, L_eff, q);
-        const int r = L_eff + B;
-        // rows of the unit matrix: included prefix modes, then modes q .. n_eff-1
+        int n_eff, L_eff, q, ss;
+        unit_shape<T>(n, n_eff, L_eff, q, ss);
+        const int r = L_eff + B;           // modes of a sub-unit's level-0 matrix
+        const int qs = q - ss;             // prefix levels fixed by the unit index
+        const int rp = ss + r;             // modes after the unit's prefix elimination
+        // rows of the unit matrix: included prefix modes, then modes qs .. n_eff-1
         if (t == 0) {
             int k = 0;
-            for (int a = 0; a < q; ++a)
+            for (int a = 0; a < qs; ++a)
                 if (prefix >> a & 1) pos[k++] = a;
-            for (int a = q; a < n_eff; ++a) pos[k + a - q] = a;
+            for (int a = qs; a < n_eff; ++a) pos[k + a - qs] = a;
             s_k = k;
         }
         __syncthreads();
         const int k = s_k;
-        const int D0 = 2 * (k + r);
-        // gather G = (I - O) on those rows into Y (packed), padding modes as identity
-        for (int i = t; i < D0; i += kThreads) {
-            const int a = pos[i >> 1];
-            const int si = a < n ? modes[a] + (i & 1) * M : -1;
-            for (int j = i; j < D0; ++j) {
-                const int b = pos[j >> 1];
-                T v;
-                if (si < 0 || b >= n) {
-                    v = (i == j) ? T(1) : T(0);
-                } else {
-                    const int sj = modes[b] + (j & 1) * M;
-                    v = (T)((i == j ? 1.0 : 0.0) - O[(size_t)si * N2 + sj]);
-                }
-                Y[pidx(D0, i, j)] = v;
+        const int D0 = 2 * (k + rp);
+        // gather G = (I - O) on those rows into Y (packed), padding modes as identity;
+        // every thread takes entries of the whole matrix (independent loads in flight)
+        for (int f = t; f < D0 * D0; f += kThreads) {
+            const int i = f / D0, j = f - i * D0;
+            if (j < i) continue;
+            const int a = pos[i >> 1], b = pos[j >> 1];
+            T v;
+            if (a >= n || b >= n) {
+                v = (i == j) ? T(1) : T(0);
+            } else {
+                const int si = modes[a] + (i & 1) * M, sj = modes[b] + (j & 1) * M;
+                v = (T)((i == j ? 1.0 : 0.0) - O[(size_t)si * N2 + sj]);
             }
+            Y[pidx(D0, i, j)] = v;
         }
         __syncthreads();
         // eliminate the included prefix modes (2x2 block pivots)
         double tpre = 1.0;
         for (int e = 0; e < k; ++e) {
-            const int c0 = 2 * e;
+            const int c0 = 2 * e, Dt = D0 - c0 - 2;
             const T p00 = Y[pidx(D0, c0, c0)], p01 = Y[pidx(D0, c0, c0 + 1)],
                     p11 = Y[pidx(D0, c0 + 1, c0 + 1)];
             const T det = p00 * p11 - p01 * p01;
@@ -342,76 +351,137 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             tpre *= rsqrt((double)det);
             const T inv = T(1) / det;
             const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-            for (int i = c0 + 2 + t; i < D0; i += kThreads) {
+            for (int f = t; f < Dt * Dt; f += kThreads) {
+                const int i = c0 + 2 + f / Dt, j = c0 + 2 + f % Dt;
+                if (j < i) continue;
                 const T bi0 = Y[pidx(D0, c0, i)], bi1 = Y[pidx(D0, c0 + 1, i)];
-                const T wi0 = q00 * bi0 + q01 * bi1, wi1 = q01 * bi0 + q11 * bi1;
-                for (int j = i; j < D0; ++j)
-                    Y[pidx(D0, i, j)] -= wi0 * Y[pidx(D0, c0, j)] + wi1 * Y[pidx(D0, c0 + 1, j)];
+                const T bj0 = Y[pidx(D0, c0, j)], bj1 = Y[pidx(D0, c0 + 1, j)];
+                Y[pidx(D0, i, j)] -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
             }
             __syncthreads();
         }
-        // level 0 of the expansion: the trailing 2r x 2r block, packed into X
+        // the unit's trailing 2rp x 2rp block -> Ublk
         {
-            const int d = 2 * r, o = 2 * k;
-            for (int i = t; i < d; i += kThreads)
-                for (int j = i; j < d; ++j) X[pidx(d, i, j)] = Y[pidx(D0, o + i, o + j)];
-            if (t == 0) tauX[0] = T(1);
+            const int d = 2 * rp, o = 2 * k;
+            for (int f = t; f < d * d; f += kThreads) {
+                const int i = f / d, j = f - i * d;
+                if (j >= i) Ub[pidx(d, i, j)] = Y[pidx(D0, o + i, o + j)];
+            }
         }
         __syncthreads();
-        // breadth-first expansion of L_eff levels
-        for (int l = 0; l < L_eff; ++l) {
-            const T *src = (l & 1) ? Y : X;
-            T *dst = (l & 1) ? X : Y;
-            const T *tsrc = (l & 1) ? tauY : tauX;
-            T *tdst = (l & 1) ? tauX : tauY;
-            const int d = 2 * (r - l), dc = d - 2;
-            const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
-            const int lg_tpc = kL - (l + 1);
-            const int c = t >> lg_tpc, sub = t & ((1 << lg_tpc) - 1);
-            const int parent = c >> 1;
-            const bool inc = c & 1;
-            const T *P = src + parent * sstr;
-            T *Cd = dst + c * dstr;
-            const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
-            const T det = p00 * p11 - p01 * p01;
-            const T rs = rsq<T>(det);
-            const T inv = rs * rs;
-            const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-            const uint16_t *dd = dec + decoff[dc >> 1];
-            for (int e = sub; e < Ec; e += (1 << lg_tpc)) {
-                const int ij = dd[e];
-                const int i = ij & 0xff, j = ij >> 8;
-                T v = P[pidx(d, i + 2, j + 2)];
-                if (inc) {
-                    const T bi0 = P[pidx(d, 0, i + 2)], bi1 = P[pidx(d, 1, i + 2)];
-                    const T bj0 = P[pidx(d, 0, j + 2)], bj1 = P[pidx(d, 1, j + 2)];
-                    v -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
+        double u_hi = 0.0, u_lo = 0.0, u_abs = 0.0;
+        for (int sub = 0; sub < (1 << ss); ++sub) {
+            // sub-unit: include the set bits of `sub` among the next ss modes
+            const int kk = __popc(sub);
+            const int Ds = 2 * (kk + r), dU = 2 * rp;
+            // rows: included sub modes (in order), then the last r modes of Ublk
+            for (int f = t; f < Ds * Ds; f += kThreads) {
+                const int i = f / Ds, j = f - i * Ds;
+                if (j < i) continue;
+                int ai = i >> 1, bj = j >> 1;
+                // position of the ai-th row mode inside Ublk
+                int ui, uj;
+                {
+                    int c = 0, m = 0;
+                    ui = -1;
+                    for (; m < ss; ++m)
+                        if (sub >> m & 1) { if (c == ai) { ui = m; break; } ++c; }
+                    if (ui < 0) ui = ss + (ai - kk);
+                    c = 0;
+                    uj = -1;
+                    for (m = 0; m < ss; ++m)
+                        if (sub >> m & 1) { if (c == bj) { uj = m; break; } ++c; }
+                    if (uj < 0) uj = ss + (bj - kk);
                 }
-                Cd[e] = v;
-            }
-            if (sub == 0) {
-                tdst[c] = inc ? tsrc[parent] * rs : tsrc[parent];
-                if (!(det > T(0))) s_flag = 1;
+                Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
             }
             __syncthreads();
+            double tsub = 1.0;
+            for (int e = 0; e < kk; ++e) {
+                const int c0 = 2 * e, Dt = Ds - c0 - 2;
+                const T p00 = Y[pidx(Ds, c0, c0)], p01 = Y[pidx(Ds, c0, c0 + 1)],
+                        p11 = Y[pidx(Ds, c0 + 1, c0 + 1)];
+                const T det = p00 * p11 - p01 * p01;
+                if (!(det > T(0))) s_flag = 1;
+                tsub *= rsqrt((double)det);
+                const T inv = T(1) / det;
+                const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+                for (int f = t; f < Dt * Dt; f += kThreads) {
+                    const int i = c0 + 2 + f / Dt, j = c0 + 2 + f % Dt;
+                    if (j < i) continue;
+                    const T bi0 = Y[pidx(Ds, c0, i)], bi1 = Y[pidx(Ds, c0 + 1, i)];
+                    const T bj0 = Y[pidx(Ds, c0, j)], bj1 = Y[pidx(Ds, c0 + 1, j)];
+                    Y[pidx(Ds, i, j)] -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
+                }
+                __syncthreads();
+            }
+            // level 0 of the expansion: the trailing 2r x 2r block, packed into X
+            {
+                const int d = 2 * r, o = 2 * kk;
+                for (int f = t; f < d * d; f += kThreads) {
+                    const int i = f / d, j = f - i * d;
+                    if (j >= i) X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
+                }
+                if (t == 0) tauX[0] = T(1);
+            }
+            __syncthreads();
+            // breadth-first expansion of L_eff levels
+            for (int l = 0; l < L_eff; ++l) {
+                const T *src = (l & 1) ? Y : X;
+                T *dst = (l & 1) ? X : Y;
+                const T *tsrc = (l & 1) ? tauY : tauX;
+                T *tdst = (l & 1) ? tauX : tauY;
+                const int d = 2 * (r - l), dc = d - 2;
+                const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
+                const int lg_tpc = kL - (l + 1);
+                const int c = t >> lg_tpc, sb = t & ((1 << lg_tpc) - 1);
+                const int parent = c >> 1;
+                const bool inc = c & 1;
+                const T *P = src + parent * sstr;
+                T *Cd = dst + c * dstr;
+                const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
+                const T det = p00 * p11 - p01 * p01;
+                const T rs = rsq<T>(det);
+                const T inv = rs * rs;
+                const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+                const uint16_t *dd = dec + decoff[dc >> 1];
+                for (int e = sb; e < Ec; e += (1 << lg_tpc)) {
+                    const int ij = dd[e];
+                    const int i = ij & 0xff, j = ij >> 8;
+                    T v = P[pidx(d, i + 2, j + 2)];
+                    if (inc) {
+                        const T bi0 = P[pidx(d, 0, i + 2)], bi1 = P[pidx(d, 1, i + 2)];
+                        const T bj0 = P[pidx(d, 0, j + 2)], bj1 = P[pidx(d, 1, j + 2)];
+                        v -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
+                    }
+                    Cd[e] = v;
+                }
+                if (sb == 0) {
+                    tdst[c] = inc ? tsrc[parent] * rs : tsrc[parent];
+                    if (!(det > T(0))) s_flag = 1;
+                }
+                __syncthreads();
+            }
+            // register-resident bottom B levels, one node per thread
+            if (t < (1 << L_eff)) {
+                const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
+                const T tau_node = ((L_eff & 1) ? tauY : tauX)[t];
+                const int nreal = n - (n_eff - B);
+                Acc<T> acc{T(0), T(0), T(0)};
+                SmemMat<T, B> A{node};
+                dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
+                const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
+                const double sc = ((excl & 1) ? -1.0 : 1.0) * (double)tau_node * tsub;
+                double sh, se;
+                two_sum(u_hi, sc * (double)acc.hi, sh, se);
+                u_hi = sh;
+                u_lo += se + sc * (double)acc.lo;
+                u_abs += fabs(sc) * (double)acc.abs;
+                if (!(acc.abs == acc.abs) || !(tau_node == tau_node)) s_flag = 1;
+            }
+            __syncthreads();   // X / Y are rewritten by the next sub-unit
         }
-        // register-resident bottom B levels, one node per thread
-        double c_hi = 0.0, c_lo = 0.0, c_abs = 0.0;
-        if (t < (1 << L_eff)) {
-            const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
-            const T tau_node = ((L_eff & 1) ? tauY : tauX)[t];
-            const int nreal = n - (n_eff - B);
-            Acc<T> acc{T(0), T(0), T(0)};
-            SmemMat<T, B> A{node};
-            dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
-            const int excl = (q - k) + (L_eff - __popc(t));
-            const double sgn = (excl & 1) ? -1.0 : 1.0;
-            const double tn = (double)tau_node;
-            c_hi = sgn * tn * (double)acc.hi;
-            c_lo = sgn * tn * (double)acc.lo;
-            c_abs = tn * (double)acc.abs;
-            if (!(acc.abs == acc.abs) || !(tau_node == tau_node)) s_flag = 1;
-        }
+        double c_hi = u_hi, c_lo = u_lo, c_abs = u_abs;
         // deterministic CTA reduction (TwoSum tree)
         for (int off = 16; off; off >>= 1) {
             double oh = __shfl_xor_sync(0xffffffffu, c_hi, off);
@@ -500,11 +570,11 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
         const double uu = Prec<T>::idx == GBS_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         kap = a / fabs(Tv);
         const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * 1.1102230246251565e-16;
-        if (!(Tv > 0.0) || !(rel < 0.5)) {
+        if (!(Tv > 0.0)) {
             st = GBS_E_NONPOSITIVE;
         } else {
             lp = -0.5 * (*logdet) + log(Tv);
-            eb = -log1p(-rel);
+            eb = rel < 1.0 ? -log1p(-rel) : INFINITY;
         }
     }
     logP[p] = lp;
@@ -610,10 +680,10 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
 size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_pat, units).end; }
 
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision) {
-    int n_eff, L_eff, q;
-    if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q);
-    else unit_shape<float>(n_max, n_eff, L_eff, q);
-    return (long long)n_pat << q;
+    int n_eff, L_eff, q, ss;
+    if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss);
+    else unit_shape<float>(n_max, n_eff, L_eff, q, ss);
+    return (long long)n_pat << (q - ss);
 }
 
 int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
