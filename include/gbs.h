@@ -45,7 +45,9 @@ typedef enum {
 
 typedef enum {
     GBS_FP64 = 0,        /* every factorisation and sum in FP64 */
-    GBS_FP32_SPLIT = 1   /* subset factorisations in FP32; signed sum compensated, FP64 result */
+    GBS_FP32_SPLIT = 1,  /* subset factorisations in FP32; signed sum compensated, FP64 result */
+    GBS_DD = 2           /* double-double (~106-bit) factorisations and sum, on the FP64 pipes:
+                            for patterns whose signed sum cancels beyond FP64 (kappa u64 >~ 1e-10) */
 } gbs_precision;
 
 /* ---- context ------------------------------------------------------------ */

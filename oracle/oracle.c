@@ -20,6 +20,11 @@
  *    submatrix of A on the x and p rows of the modes in Z.
  *  - The signed sum is accumulated with the error-free Sum2 of Ogita, Rump and
  *    Oishi (SIAM J. Sci. Comput. 26, 2005) in subset-mask order 0..2^n-1.
+ *  - For click patterns far below their expected click count the signed sum
+ *    cancels by many orders of magnitude (kappa = sum|term| / |T| up to 1e13 and
+ *    beyond), and FP64 subset determinants leave ~kappa * 1e-16 error.  The
+ *    double-double variants (orc_subset_sum_dd*) compute every Cholesky and
+ *    the sum with ~106-bit arithmetic.
  */
 #include <math.h>
 #include <stdint.h>
@@ -159,6 +164,140 @@ int orc_subset_sum(int M, const double *A, const int *modes, int n, uint64_t z_b
     return status;
 }
 
+/* ---- double-double arithmetic (Dekker 1971; Hida, Li & Bailey 2001) -------
+ * A value is hi + lo with |lo| <= ulp(hi)/2; about 106 significant bits.  Used
+ * for subset determinants whose signed sum cancels beyond FP64 precision. */
+typedef struct {
+    double hi, lo;
+} dd;
+
+static dd dd_two_sum(double a, double b) {
+    dd r;
+    two_sum(a, b, &r.hi, &r.lo);
+    return r;
+}
+static dd dd_quick(double a, double b) { /* requires |a| >= |b| */
+    dd r;
+    r.hi = a + b;
+    r.lo = b - (r.hi - a);
+    return r;
+}
+static dd dd_two_prod(double a, double b) {
+    dd r;
+    r.hi = a * b;
+    r.lo = fma(a, b, -r.hi);
+    return r;
+}
+static dd dd_add(dd a, dd b) {
+    dd s = dd_two_sum(a.hi, b.hi), t = dd_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_quick(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_quick(s.hi, s.lo);
+}
+static dd dd_neg(dd a) {
+    dd r = {-a.hi, -a.lo};
+    return r;
+}
+static dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+static dd dd_mul(dd a, dd b) {
+    dd p = dd_two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return dd_quick(p.hi, p.lo);
+}
+static dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul((dd){q1, 0.0}, b));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul((dd){q2, 0.0}, b));
+    double q3 = r.hi / b.hi;
+    return dd_add(dd_quick(q1, q2), (dd){q3, 0.0});
+}
+static dd dd_sqrt(dd a) { /* one Newton step from the double square root */
+    double x = sqrt(a.hi);
+    dd r = dd_sub(a, dd_two_prod(x, x));
+    return dd_two_sum(x, r.hi / (2.0 * x));
+}
+
+/* cholesky() in double-double; a holds n*n dd values (lower triangle used). */
+static int cholesky_dd(dd *a, int n) {
+    for (int j = 0; j < n; ++j) {
+        dd d = a[j * n + j];
+        for (int k = 0; k < j; ++k) d = dd_sub(d, dd_mul(a[j * n + k], a[j * n + k]));
+        if (!(d.hi > 0.0)) return ORC_NOT_SPD;
+        d = dd_sqrt(d);
+        a[j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            dd s = a[i * n + j];
+            for (int k = 0; k < j; ++k) s = dd_sub(s, dd_mul(a[i * n + k], a[j * n + k]));
+            a[i * n + j] = dd_div(s, d);
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * orc_subset_sum in double-double: every subset Cholesky and the signed sum
+ * carry ~106 bits, so the result keeps its accuracy when the sum cancels by
+ * many orders of magnitude.  A is the FP64 matrix (I - O) (exact inputs).
+ * out: (hi, lo) of T and sum_Z det(A_Z)^{-1/2}.
+ */
+int orc_subset_sum_dd(int M, const double *A, const int *modes, int n, uint64_t z_begin,
+                      uint64_t z_end, double *out) {
+    int N = 2 * M;
+    dd *B = malloc(sizeof(dd) * 4 * (size_t)n * n + 1);
+    int *idx = malloc(sizeof(int) * 2 * (size_t)n + 1);
+    if (!B || !idx) { free(B); free(idx); return ORC_INVALID; }
+    dd sum = {0.0, 0.0};
+    double sabs = 0.0;
+    int status = ORC_OK;
+    for (uint64_t z = z_begin; z < z_end; ++z) {
+        int k = 0;
+        for (int a = 0; a < n; ++a)
+            if (z >> a & 1) { idx[2 * k] = modes[a]; idx[2 * k + 1] = modes[a] + M; ++k; }
+        int d = 2 * k;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) B[i * d + j] = (dd){A[idx[i] * N + idx[j]], 0.0};
+        dd tau = {1.0, 0.0};
+        if (d) {
+            if (cholesky_dd(B, d)) { status = ORC_NOT_SPD; break; }
+            for (int i = 0; i < d; ++i) tau = dd_div(tau, B[i * d + i]);
+        }
+        sum = ((n - k) & 1) ? dd_sub(sum, tau) : dd_add(sum, tau);
+        sabs += tau.hi;
+    }
+    out[0] = sum.hi; out[1] = sum.lo; out[2] = sabs;
+    free(B); free(idx);
+    return status;
+}
+
+/* orc_subset_sum_dd split into mask ranges run in parallel, merged in order. */
+int orc_subset_sum_dd_parallel(int M, const double *A, const int *modes, int n, int nchunk,
+                               int nthreads, double *out) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    uint64_t total = (uint64_t)1 << n;
+    if (nchunk < 1) nchunk = 1;
+    double *part = calloc((size_t)nchunk * 3, sizeof(double));
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int c = 0; c < nchunk; ++c) {
+        uint64_t b = total * (uint64_t)c / (uint64_t)nchunk;
+        uint64_t e = total * (uint64_t)(c + 1) / (uint64_t)nchunk;
+        bad |= orc_subset_sum_dd(M, A, modes, n, b, e, part + 3 * c);
+    }
+    dd sum = {0.0, 0.0};
+    double sabs = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+        sum = dd_add(sum, (dd){part[3 * c], part[3 * c + 1]});
+        sabs += part[3 * c + 2];
+    }
+    out[0] = sum.hi; out[1] = sum.lo; out[2] = sabs;
+    free(part);
+    return bad ? ORC_NOT_SPD : ORC_OK;
+}
+
 static int pattern_modes(uint64_t lo, uint64_t hi, int M, int *modes) {
     int n = 0;
     for (int i = 0; i < M; ++i) {
@@ -177,7 +316,7 @@ static int pattern_modes(uint64_t lo, uint64_t hi, int M, int *modes) {
  */
 int orc_prob_exact(int M, const double *A, double logdet_sigmaQ, const uint64_t *patterns,
                    int n_pat, double *logP, double *T, double *sumabs, int *status,
-                   int nthreads) {
+                   int nthreads, int use_dd) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -187,7 +326,9 @@ int orc_prob_exact(int M, const double *A, double logdet_sigmaQ, const uint64_t 
         int modes[128];
         int n = pattern_modes(patterns[2 * p], patterns[2 * p + 1], M, modes);
         double out[3] = {0, 0, 0};
-        int st = (n > 40) ? ORC_INVALID : orc_subset_sum(M, A, modes, n, 0, (uint64_t)1 << n, out);
+        int st = (n > 40) ? ORC_INVALID
+                 : use_dd ? orc_subset_sum_dd(M, A, modes, n, 0, (uint64_t)1 << n, out)
+                          : orc_subset_sum(M, A, modes, n, 0, (uint64_t)1 << n, out);
         double t = out[0] + out[1];
         if (!st && !(t > 0.0)) st = 4;
         status[p] = st;
@@ -195,7 +336,8 @@ int orc_prob_exact(int M, const double *A, double logdet_sigmaQ, const uint64_t 
         T[2 * p] = out[0];
         T[2 * p + 1] = out[1];
         sumabs[p] = out[2];
-        logP[p] = st ? NAN : -0.5 * logdet_sigmaQ + log(t);
+        /* log(hi + lo) = log(hi) + log1p(lo / hi) keeps the double-double digits */
+        logP[p] = st ? NAN : -0.5 * logdet_sigmaQ + log(out[0]) + log1p(out[1] / out[0]);
     }
     return bad ? 4 : ORC_OK;
 }

@@ -11,10 +11,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD
 
-PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, GBS_FP64: GBS_FP64,
-              GBS_FP32_SPLIT: GBS_FP32_SPLIT}
+PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, GBS_FP64: GBS_FP64,
+              GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD}
 
 
 def _ptr(t) -> ctypes.c_void_p:

@@ -144,7 +144,7 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_reserve: bad n_pat %d / n_max %d", n_pat, n_max);
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     long long units = 0;
-    for (int prec = 0; prec < 2; ++prec) {
+    for (int prec = 0; prec < 3; ++prec) {
         long long u = sweep_units_upper_bound(n_pat, n_max, prec);
         if (u > units) units = u;
     }
@@ -171,7 +171,7 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
     if (!ctx) return GBS_E_INVALID;
     if (M < 1 || M > 128 || n_pat < 0 || !O || !logdet_sigmaQ || (n_pat && (!patterns || !logP)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: bad arguments (M=%d, n_pat=%d)", M, n_pat);
-    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT)
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: unknown precision %d", precision);
     if (n_pat == 0) return GBS_OK;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));

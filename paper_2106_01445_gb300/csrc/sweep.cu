@@ -23,6 +23,7 @@
 // double with TwoSum, stored per unit, and summed per pattern in unit order.
 #include <stdlib.h>
 
+#include "dd.cuh"
 #include "gbs_internal.cuh"
 
 namespace {
@@ -39,13 +40,48 @@ __host__ __device__ constexpr int pidx(int d, int i, int j) { return i * d - (i 
 // odd node stride: per-thread node reads hit distinct banks
 __host__ __device__ constexpr int nstride(int d) { return sym(d) | 1; }
 
+// Per precision: B register-resident levels per thread; Tau, the type of the
+// products of pivot factors above the thread level; u, the unit roundoff.
 template <typename T> struct Prec;
-template <> struct Prec<float> { static constexpr int B = 6; static constexpr int idx = GBS_FP32_SPLIT; };
-template <> struct Prec<double> { static constexpr int B = 4; static constexpr int idx = GBS_FP64; };
+template <> struct Prec<float> {
+    static constexpr int B = 6, idx = GBS_FP32_SPLIT;
+    using Tau = double;
+    static constexpr double u = 5.9604644775390625e-08, u_sum = 1.1102230246251565e-16;
+};
+template <> struct Prec<double> {
+    static constexpr int B = 4, idx = GBS_FP64;
+    using Tau = double;
+    static constexpr double u = 1.1102230246251565e-16, u_sum = 1.1102230246251565e-16;
+};
+template <> struct Prec<dd> {
+    static constexpr int B = 3, idx = GBS_DD;
+    using Tau = dd;
+    static constexpr double u = 1.2325951644078309e-32, u_sum = 1.2325951644078309e-32;
+};
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
+
+// 1/sqrt(det) as a prefix factor, in the Tau type of the precision
+__device__ __forceinline__ double rsq_tau(float x) { return rsqrt((double)x); }
+__device__ __forceinline__ double rsq_tau(double x) { return rsqrt(x); }
+__device__ __forceinline__ dd rsq_tau(dd x) { return dd_rsqrt(x); }
+
+// an entry of A = I - O from its FP64 data (exact in double-double)
+template <typename T> __device__ __forceinline__ T a_entry(double delta, double o) { return (T)(delta - o); }
+template <> __device__ __forceinline__ dd a_entry<dd>(double delta, double o) { return dd_two_sum(delta, -o); }
+
+__device__ __forceinline__ double to_hi(float x) { return x; }
+__device__ __forceinline__ double to_hi(double x) { return x; }
+__device__ __forceinline__ double to_hi(dd x) { return x.hi; }
+__device__ __forceinline__ double to_lo(float) { return 0.0; }
+__device__ __forceinline__ double to_lo(double) { return 0.0; }
+__device__ __forceinline__ double to_lo(dd x) { return x.lo; }
+__device__ __forceinline__ bool is_nan(float x) { return x != x; }
+__device__ __forceinline__ bool is_nan(double x) { return x != x; }
+__device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 
 // ---- shared-memory layout ----------------------------------------------------
 template <typename T> struct Layout {
@@ -83,6 +119,12 @@ template <typename T> struct Layout {
 };
 
 // ---- error-free accumulation ----------------------------------------------------
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    double bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
 template <typename T> struct Acc {
     T hi, lo, abs;
 };
@@ -93,12 +135,37 @@ template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
     a.lo += (a.hi - (s - bp)) + (x - bp);
     a.hi = s;
 }
+// double-double sums need no further compensation
+template <> __device__ __forceinline__ void acc_add<dd>(Acc<dd> &a, dd x) { a.hi += x; }
 
-__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
-    s = a + b;
-    double bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
+// (hi, lo) += sc * (x_hi + x_lo) for one thread's subtree sum
+__device__ __forceinline__ void unit_add(double &h, double &l, double sc, double xh, double xl) {
+    double s, e;
+    two_sum(h, sc * xh, s, e);
+    h = s;
+    l += e + sc * xl;
 }
+__device__ __forceinline__ void unit_add(double &h, double &l, dd sc, double xh, double xl) {
+    dd c = sc * dd(xh, xl);
+    dd u = dd(h, l) + c;
+    h = u.hi;
+    l = u.lo;
+}
+__device__ __forceinline__ double tau_abs(double x) { return fabs(x); }
+__device__ __forceinline__ double tau_abs(dd x) { return fabs(x.hi); }
+// (hi, lo) * prefix factor
+__device__ __forceinline__ void unit_scale(double &h, double &l, double tp) {
+    h *= tp;
+    l *= tp;
+}
+__device__ __forceinline__ void unit_scale(double &h, double &l, dd tp) {
+    dd u = dd(h, l) * tp;
+    h = u.hi;
+    l = u.lo;
+}
+__device__ __forceinline__ double tau_hi(double x) { return x; }
+__device__ __forceinline__ double tau_hi(dd x) { return x.hi; }
+
 
 // ---- register-resident bottom levels ----------------------------------------------
 template <typename T, int MD> struct RegMat {
@@ -262,7 +329,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
     T *Ub = (T *)(smem + Lay::off_U);
-    __shared__ double s_tpre;
+    using Tau = typename Prec<T>::Tau;
+    __shared__ Tau s_tpre;
 
     const int t = threadIdx.x;
     const int N2 = 2 * M;
@@ -335,20 +403,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 v = (i == j) ? T(1) : T(0);
             } else {
                 const int si = modes[a] + (i & 1) * M, sj = modes[b] + (j & 1) * M;
-                v = (T)((i == j ? 1.0 : 0.0) - O[(size_t)si * N2 + sj]);
+                    v = a_entry<T>(i == j ? 1.0 : 0.0, O[(size_t)si * N2 + sj]);
             }
             Y[pidx(D0, i, j)] = v;
         }
         __syncthreads();
         // eliminate the included prefix modes (2x2 block pivots)
-        double tpre = 1.0;
+        Tau tpre = Tau(1.0);
         for (int e = 0; e < k; ++e) {
             const int c0 = 2 * e, Dt = D0 - c0 - 2;
             const T p00 = Y[pidx(D0, c0, c0)], p01 = Y[pidx(D0, c0, c0 + 1)],
                     p11 = Y[pidx(D0, c0 + 1, c0 + 1)];
             const T det = p00 * p11 - p01 * p01;
             if (!(det > T(0))) s_flag = 1;
-            tpre *= rsqrt((double)det);
+            tpre = tpre * rsq_tau(det);
             const T inv = T(1) / det;
             const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
             for (int f = t; f < Dt * Dt; f += kThreads) {
@@ -396,14 +464,14 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
             }
             __syncthreads();
-            double tsub = 1.0;
+            Tau tsub = Tau(1.0);
             for (int e = 0; e < kk; ++e) {
                 const int c0 = 2 * e, Dt = Ds - c0 - 2;
                 const T p00 = Y[pidx(Ds, c0, c0)], p01 = Y[pidx(Ds, c0, c0 + 1)],
                         p11 = Y[pidx(Ds, c0 + 1, c0 + 1)];
                 const T det = p00 * p11 - p01 * p01;
                 if (!(det > T(0))) s_flag = 1;
-                tsub *= rsqrt((double)det);
+                tsub = tsub * rsq_tau(det);
                 const T inv = T(1) / det;
                 const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
                 for (int f = t; f < Dt * Dt; f += kThreads) {
@@ -471,13 +539,10 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 SmemMat<T, B> A{node};
                 dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
                 const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
-                const double sc = ((excl & 1) ? -1.0 : 1.0) * (double)tau_node * tsub;
-                double sh, se;
-                two_sum(u_hi, sc * (double)acc.hi, sh, se);
-                u_hi = sh;
-                u_lo += se + sc * (double)acc.lo;
-                u_abs += fabs(sc) * (double)acc.abs;
-                if (!(acc.abs == acc.abs) || !(tau_node == tau_node)) s_flag = 1;
+                const Tau sc = Tau((excl & 1) ? -1.0 : 1.0) * Tau(tau_node) * tsub;
+                unit_add(u_hi, u_lo, sc, to_hi(acc.hi) , to_lo(acc.hi) + to_hi(acc.lo));
+                u_abs += tau_abs(sc) * to_hi(acc.abs);
+                if (is_nan(acc.abs) || is_nan(tau_node)) s_flag = 1;
             }
             __syncthreads();   // X / Y are rewritten by the next sub-unit
         }
@@ -509,12 +574,13 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 l += red[3 * w + 1] + e;
                 a += red[3 * w + 2];
             }
-            const double tp = s_tpre;
+            const Tau tp = s_tpre;
+            unit_scale(h, l, tp);
             double *out = pl.partials + 3 * u;
-            out[0] = h * tp;
-            out[1] = l * tp;
-            out[2] = a * tp;
-            if (s_flag || !(tp == tp)) atomicOr(pl.pflags + sp, 1);
+            out[0] = h;
+            out[1] = l;
+            out[2] = a * tau_hi(tp);
+            if (s_flag || is_nan(tp)) atomicOr(pl.pflags + sp, 1);
         }
         __syncthreads();
     }
@@ -567,13 +633,13 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
     } else {
         // a-posteriori bound: every term carries a relative error of at most
         // c (2n + 4) u from its chain of 2x2 pivots; the signed sum amplifies by kappa.
-        const double uu = Prec<T>::idx == GBS_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double uu = Prec<T>::u;
         kap = a / fabs(Tv);
-        const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * 1.1102230246251565e-16;
+        const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * Prec<T>::u_sum;
         if (!(Tv > 0.0)) {
             st = GBS_E_NONPOSITIVE;
         } else {
-            lp = -0.5 * (*logdet) + log(Tv);
+            lp = -0.5 * (*logdet) + log(h) + log1p(l / h);
             eb = rel < 1.0 ? -log1p(-rel) : INFINITY;
         }
     }
@@ -682,6 +748,7 @@ size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_p
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision) {
     int n_eff, L_eff, q, ss;
     if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss);
+    else if (precision == GBS_DD) unit_shape<dd>(n_max, n_eff, L_eff, q, ss);
     else unit_shape<float>(n_max, n_eff, L_eff, q, ss);
     return (long long)n_pat << (q - ss);
 }
@@ -691,5 +758,7 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
                 double *err_bound, int32_t *status) {
     if (precision == GBS_FP64)
         return run_sweep<double>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+    if (precision == GBS_DD)
+        return run_sweep<dd>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
 }

@@ -1,5 +1,12 @@
 """GPU parity of the exact path (state build, pattern generation, signed subset
-sweep) against the FP64 oracle, through the C ABI."""
+sweep) against the oracle, through the C ABI.
+
+Improbable click patterns cancel by many orders of magnitude in the signed
+sum (kappa = sum|term|/|T| reaches 1e13 on the 24-mode workload), so the
+reference is the double-double oracle.  Bounds: the double-double path must
+match it to 1e-10 in log P; the FP64 path to 1e-10 wherever its own
+a-posteriori bound is below that, else within the bound; the FP32 split within
+its bound, or it reports GBS_E_NONPOSITIVE when its sum loses the sign."""
 import math
 
 import numpy as np
@@ -36,16 +43,27 @@ def gpu_prob(ctx, st, pats, precision, order=0):
 
 def check_against_oracle(res, ref, precision):
     ok = ref["status"] == 0
-    assert (res["status"][ok] == 0).all(), res["status"][ok]
+    st = res["status"][ok]
+    if precision == "fp32":
+        assert np.isin(st, (0, 4)).all(), st
+        ok = ok & (res["status"] == 0)
+    else:
+        assert (st == 0).all(), st
     d = np.abs(res["logP"][ok] - ref["logP"][ok])
     bound = res["err_bound"][ok]
-    if precision == "fp64":
+    if precision == "dd":
+        assert (d <= TOL64).all(), (d.max(), res["kappa"][ok][d.argmax()])
+    elif precision == "fp64":
         assert (d <= np.maximum(TOL64, bound)).all(), (d.max(), bound[d.argmax()])
         tight = bound <= 1e-11
         assert (d[tight] <= TOL64).all()
     else:
         assert (d <= bound).all(), (d.max(), bound[d.argmax()], res["kappa"][ok][d.argmax()])
     return d
+
+
+def oracle_dd(U, r, eta, pats):
+    return oracle.prob_exact(oracle.build_state(U, r, eta), pats, dd=True)
 
 
 @pytest.mark.parametrize("name,eta", [("m8_all", 1.0), ("m24_exact", 0.5), ("m100_approx", 0.3),
@@ -81,63 +99,84 @@ def test_gen_patterns_bit_exact(ctx, M, n_lo, n_hi, n_pat, seed, stream):
     assert np.array_equal(dev, host)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
 @pytest.mark.parametrize("eta", [1.0, 0.5])
 def test_all_patterns_m8(ctx, precision, eta):
     c = g.CONFIGS["m8_all"]
     U, r = c.unitary(), c.squeezing()
     pats = g.all_patterns(8)
     res = gpu_prob(ctx, gpu_state(ctx, U, r, eta), pats, precision)
-    ref = oracle.prob_exact(oracle.build_state(U, r, eta), pats)
+    ref = oracle_dd(U, r, eta, pats)
     check_against_oracle(res, ref, precision)
-    total = np.exp(res["logP"]).sum()
-    assert abs(total - 1.0) < (1e-12 if precision == "fp64" else 1e-5)
+    p = np.exp(res["logP"])
+    if precision != "fp32":
+        assert abs(p.sum() - 1.0) < (1e-14 if precision == "dd" else 1e-12)
+    else:
+        assert abs(np.nansum(p) - 1.0) < 1e-4
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_uneven_batch_all_sizes(ctx, precision):
-    # one launch over patterns of every size 0..22, ragged, incl. the padding
-    # (n < B), one-unit and multi-unit shapes
+@pytest.fixture(scope="module")
+def uneven():
+    # patterns of every size 0..18 (ragged: the padding n < B, one-unit, multi-unit
+    # and multi-sub-unit shapes of every precision) in one launch
     M = 26
     U = g.haar_unitary(M, 101)
     r = g.squeezing(M, 13, 0.6, 1.2, 101)
     rng = np.random.default_rng(5)
-    modes_list = [sorted(rng.choice(M, size=n, replace=False)) for n in list(range(0, 23)) + [3, 7, 13, 14, 15]]
+    sizes = list(range(0, 19)) + [3, 7, 13, 14, 15, 17]
+    modes_list = [sorted(rng.choice(M, size=n, replace=False)) for n in sizes]
     pats = np.stack([g.modes_to_pattern(m) for m in modes_list])
+    return U, r, pats, oracle_dd(U, r, 0.55, pats)
+
+
+@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+def test_uneven_batch_all_sizes(ctx, uneven, precision):
+    U, r, pats, ref = uneven
     st = gpu_state(ctx, U, r, 0.55)
     res = gpu_prob(ctx, st, pats, precision)
-    ref = oracle.prob_exact(oracle.build_state(U, r, 0.55), pats)
     check_against_oracle(res, ref, precision)
     assert abs(res["logP"][0] + 0.5 * st["logdet"].item()) < 1e-14   # empty pattern
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_m24_config_sample(ctx, precision):
-    # the 24-mode workload in the benchmark's launch shape (all 1024 patterns in one
-    # call); the oracle checks a sample spanning every click count
+@pytest.fixture(scope="module")
+def m24_sample():
+    # the 24-mode workload; the oracle checks a sample spanning the click counts
     c = g.CONFIGS["m24_exact"]
     U, r = c.unitary(), c.squeezing()
     pats = c.patterns()
-    res = gpu_prob(ctx, gpu_state(ctx, U, r, c.eta), pats, precision)
     n = np.array([len(g.pattern_modes(p)) for p in pats])
     idx = []
-    for k in range(12, 21):
+    for k in range(12, 19):
         w = np.nonzero(n == k)[0]
-        idx += list(w[: (3 if k <= 17 else 1)])
+        idx += list(w[: (2 if k <= 16 else 1)])
     idx = np.array(idx)
-    ref = oracle.prob_exact(oracle.build_state(U, r, c.eta), pats[idx])
+    return c, U, r, pats, idx, oracle_dd(U, r, c.eta, pats[idx])
+
+
+@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+def test_m24_config_sample(ctx, m24_sample, precision):
+    # the benchmark's launch shape: all 1024 patterns in one call
+    c, U, r, pats, idx, ref = m24_sample
+    res = gpu_prob(ctx, gpu_state(ctx, U, r, c.eta), pats, precision)
     sub = {k: v[idx] for k, v in res.items()}
     check_against_oracle(sub, ref, precision)
-    assert (res["status"] == 0).all()
+    if precision != "fp32":
+        assert (res["status"] == 0).all()
 
 
-def test_fp32_and_fp64_agree_full_config(ctx):
+def test_precisions_agree_full_config(ctx):
+    # every pattern of the workload: FP64 and FP32 results lie within their bounds
+    # of the double-double result
     c = g.CONFIGS["m24_exact"]
     st = gpu_state(ctx, c.unitary(), c.squeezing(), c.eta)
-    a = gpu_prob(ctx, st, c.patterns(), "fp64")
-    b = gpu_prob(ctx, st, c.patterns(), "fp32")
-    d = np.abs(a["logP"] - b["logP"])
-    assert (d <= b["err_bound"] + a["err_bound"]).all()
+    ref = gpu_prob(ctx, st, c.patterns(), "dd")
+    assert (ref["status"] == 0).all()
+    for prec in ("fp64", "fp32"):
+        a = gpu_prob(ctx, st, c.patterns(), prec)
+        ok = a["status"] == 0
+        assert (ok | (prec == "fp32")).all()
+        d = np.abs(a["logP"][ok] - ref["logP"][ok])
+        assert (d <= a["err_bound"][ok] + 1e-12).all(), prec
 
 
 def test_block_diagonal_factorises_at_n30(ctx):
@@ -151,7 +190,7 @@ def test_block_diagonal_factorises_at_n30(ctx):
     eta = 0.3
     pats = g.gen_patterns(5, M, 30, 30, 4, stream=g.STREAM_ANCHORS)
     st = gpu_state(ctx, U, r, eta)
-    for precision in ("fp64", "fp32"):
+    for precision in ("dd", "fp64"):
         res = gpu_prob(ctx, st, pats, precision)
         for i, p in enumerate(pats):
             modes = set(g.pattern_modes(p))
@@ -162,32 +201,33 @@ def test_block_diagonal_factorises_at_n30(ctx):
                 loc = [j for j, m in enumerate(blk) if m in modes]
                 lp += oracle.prob_exact(sub, g.modes_to_pattern(loc)[None])["logP"][0]
             assert res["status"][i] == 0
-            tol = TOL64 if precision == "fp64" else res["err_bound"][i]
-            assert abs(res["logP"][i] - lp) <= max(tol, res["err_bound"][i]), (precision, i)
+            tol = TOL64 if precision == "dd" else max(TOL64, res["err_bound"][i])
+            assert abs(res["logP"][i] - lp) <= tol, (precision, i)
 
 
 def test_large_pattern_against_parallel_oracle(ctx):
-    # one 22-click pattern of the 24-mode device, oracle over 4M subsets in parallel
+    # one 20-click pattern of the 24-mode device, double-double oracle over 1M
+    # subsets in parallel
     c = g.CONFIGS["m24_exact"]
     U, r = c.unitary(), c.squeezing()
-    modes = [m for m in range(24) if m not in (3, 17)]
+    modes = [m for m in range(24) if m not in (3, 8, 17, 21)]
     st = gpu_state(ctx, U, r, c.eta)
     ref_state = oracle.build_state(U, r, c.eta)
-    T = oracle.subset_sum(ref_state.A, 24, modes, nchunk=256)
-    ref = -0.5 * ref_state.logdet + math.log(T[0] + T[1])
-    for precision in ("fp64", "fp32"):
+    T = oracle.subset_sum(ref_state.A, 24, modes, nchunk=256, dd=True)
+    ref = -0.5 * ref_state.logdet + math.log(T[0]) + math.log1p(T[1] / T[0])
+    for precision in ("dd", "fp64"):
         res = gpu_prob(ctx, st, g.modes_to_pattern(modes)[None], precision)
-        tol = max(TOL64, res["err_bound"][0]) if precision == "fp64" else res["err_bound"][0]
-        assert abs(res["logP"][0] - ref) <= tol
+        tol = TOL64 if precision == "dd" else max(TOL64, res["err_bound"][0])
+        assert abs(res["logP"][0] - ref) <= tol, precision
 
 
 def test_deterministic(ctx):
     c = g.CONFIGS["m24_exact"]
     st = gpu_state(ctx, c.unitary(), c.squeezing(), c.eta)
-    for precision in ("fp64", "fp32"):
+    for precision in ("dd", "fp64", "fp32"):
         a = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
         b = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
-        assert np.array_equal(a, b)
+        assert np.array_equal(a, b, equal_nan=True)
 
 
 def test_invalid_patterns_flagged(ctx):
@@ -205,5 +245,5 @@ def test_host_entry_point_matches_device_path(ctx):
     U, r, pats = c.unitary(), c.squeezing(), c.patterns()[:200]
     dev = gpu_prob(ctx, gpu_state(ctx, U, r, c.eta), pats, "fp32")
     host = ctx.run_host(U, r, c.eta, pats, precision="fp32")
-    assert np.array_equal(dev["logP"], host["logP"])
+    assert np.array_equal(dev["logP"], host["logP"], equal_nan=True)
     assert np.array_equal(dev["status"], host["status"])

@@ -192,3 +192,33 @@ def test_subset_sum_chunks_match():
     whole = oracle.subset_sum(st.A, c.M, modes)
     parts = oracle.subset_sum(st.A, c.M, modes, nchunk=7, nthreads=2)
     assert abs((whole[0] + whole[1]) - (parts[0] + parts[1])) <= 1e-15 * whole[2]
+
+
+def test_double_double_against_multiprecision():
+    # Improbable patterns cancel by many orders of magnitude (kappa >> 1/u);
+    # the double-double oracle is pinned by a 50-digit evaluation of the
+    # independent marginal formula sum_Z +- det(sigma_Q,Z^c Z^c)^{-1/2}.
+    mpmath = pytest.importorskip("mpmath")
+    M = 10
+    U = g.haar_unitary(M, 123)
+    r = g.squeezing(M, 10, 0.3, 0.6, 123)
+    st = oracle.build_state(U, r, 0.3)
+    mpmath.mp.dps = 50
+    worst64 = 0.0
+    for modes in ([0, 1, 2, 3, 4, 5, 6, 7, 8, 9], [0, 2, 3, 4, 6, 7, 8, 9], [1, 3, 5, 7, 9]):
+        pat = g.modes_to_pattern(modes)[None]
+        n = len(modes)
+        tot = mpmath.mpf(0)
+        for z in range(1 << n):
+            Z = {modes[i] for i in range(n) if z >> i & 1}
+            W = [i for i in range(M) if i not in Z]
+            rows = W + [i + M for i in W]
+            d = mpmath.det(mpmath.matrix(st.sigmaQ[np.ix_(rows, rows)].tolist())) if rows else 1
+            tot += (-1) ** (n - len(Z)) / mpmath.sqrt(d)
+        ref = float(mpmath.log(tot))
+        dd = oracle.prob_exact(st, pat, dd=True)
+        f64 = oracle.prob_exact(st, pat)
+        assert abs(dd["logP"][0] - ref) < 1e-13, (modes, dd["kappa"][0])
+        worst64 = max(worst64, abs(f64["logP"][0] - ref) / (f64["kappa"][0] * 1.1e-16))
+    # the FP64 oracle's error stays within its kappa-scaled bound
+    assert worst64 < 4 * 24
