@@ -107,6 +107,23 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
                  const uint64_t *patterns_host, int n_pat, int order, int precision,
                  double *logP_host, double *kappa_host, double *err_host, int32_t *status_host);
 
+/* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
+ * has no counterpart: this serves callers that cannot call cudaMalloc (code
+ * running under another owner's stream capture, processes whose device memory
+ * is held by another framework's pool, serving loops that must not wait on the
+ * allocator).  Its scratch is one fixed 8 MiB array in the library's device
+ * memory (held by every GPU that loads the library until exit): at most 16384
+ * patterns, and n_pat patterns of up to n_max clicks must fit in it, else the
+ * call returns GBS_E_INVALID with a message.  Patterns with more than n_max
+ * clicks may overflow it; then every pattern reports GBS_E_NOMEM.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  No allocation, no synchronisation. */
+int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                     const uint64_t *patterns, int n_pat, int n_max, int precision, double *logP,
+                     double *kappa, double *err_bound, int32_t *status);
+
 /* ---- synthetic click patterns -------------------------------------------
  * Pattern i draws uint32 words w_0, w_1, ... from Philox4x32-10 (Salmon et al.,
  * SC'11) with key (seed mod 2^32, seed / 2^32) and counters (i, block, stream, 0);

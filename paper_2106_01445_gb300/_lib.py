@@ -31,6 +31,7 @@ SIGNATURES = {
     "gbs_build_state": (_i, [_vp, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
     "gbs_prob": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_run_host": (_i, [_vp, _i, _vp, _vp, _d, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "gbs_prob_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_gen_patterns": (_i, [_vp, _u64, _u32, _i, _i, _i, _i, _vp]),
     "gbs_peak_flops": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "gbs_timing_enable": (_i, [_vp, _i]),

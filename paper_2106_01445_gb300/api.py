@@ -109,6 +109,23 @@ class Context:
                                       _ptr(out["err_bound"]), _ptr(out["status"])))
         return out
 
+    def prob_noalloc(self, O: torch.Tensor, logdet: torch.Tensor, patterns, n_max: int,
+                     precision="fp64", out=None):
+        """Exact log P without any device allocation inside the library (its scratch is a
+        fixed array in the library's device memory); out buffers are the caller's."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        if out is None:
+            out = dict(logP=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       kappa=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       err_bound=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                       status=torch.empty(n_pat, dtype=torch.int32, device=self.device))
+        self._check(self.lib.gbs_prob_noalloc(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), n_pat, n_max,
+                                              PRECISIONS[precision], _ptr(out["logP"]), _ptr(out["kappa"]),
+                                              _ptr(out["err_bound"]), _ptr(out["status"])))
+        return out
+
     def run_host(self, U, r, eta: float, patterns, order: int = 0, precision="fp64", out=None):
         """The whole path from host (numpy) buffers; returns numpy arrays."""
         U = np.ascontiguousarray(U, dtype=np.complex128)

@@ -61,6 +61,9 @@ int launch_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int
 int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
                 const uint64_t *patterns, int n_pat, int precision, double *logP,
                 double *kappa, double *err_bound, int32_t *status);
+int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
+                   const double *logdet, const uint64_t *patterns, int n_pat, int precision,
+                   double *logP, double *kappa, double *err_bound, int32_t *status);
 size_t sweep_workspace_bytes(int n_pat, long long units);
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision);
 int peak_flops(gbs_ctx *ctx, int kind, double *flops);

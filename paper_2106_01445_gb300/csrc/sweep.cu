@@ -741,7 +741,54 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
     return GBS_OK;
 }
 
+// The same launch sequence on a workspace the caller provides: no allocation,
+// no synchronisation.  A batch whose units do not fit reports GBS_E_NOMEM per pattern.
+template <typename T>
+int run_sweep_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
+                 const double *logdet, const uint64_t *pats, int n_pat, double *logP,
+                 double *kappa, double *err_bound, int32_t *status) {
+    using Lay = Layout<T>;
+    const int pi = Prec<T>::idx;
+    if (ctx->sweep_blocks_per_sm[pi] == 0) {
+        GBS_CUDA(ctx, cudaFuncSetAttribute(sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Lay::bytes));
+        int nb = 0;
+        GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T>, kThreads,
+                                                                    Lay::bytes));
+        if (nb < 1) return gbs_fail(ctx, GBS_E_CUDA, "sweep kernel does not fit on an SM");
+        ctx->sweep_blocks_per_sm[pi] = nb;
+    }
+    const size_t base = ws_offsets(n_pat, 0).partials;
+    if (ws_bytes < base)
+        return gbs_fail(ctx, GBS_E_INVALID, "workspace of %zu bytes cannot hold %d patterns", ws_bytes, n_pat);
+    const long long cap = (long long)((ws_bytes - base) / 24);
+    Plan pl = plan_from(ws, n_pat);
+    plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    const int grid = ctx->num_sms * ctx->sweep_blocks_per_sm[pi];
+    sweep_kernel<T><<<grid, kThreads, Lay::bytes, ctx->stream>>>(M, O, pats, n_pat, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    const int fthreads = 256, fblocks = (n_pat * 32 + fthreads - 1) / fthreads;
+    finalize_kernel<T><<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa,
+                                                             err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
+
 }  // namespace
+
+int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
+                   const double *logdet, const uint64_t *patterns, int n_pat, int precision,
+                   double *logP, double *kappa, double *err_bound, int32_t *status) {
+    if (precision == GBS_FP64)
+        return run_sweep_on<double>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
+                                    err_bound, status);
+    if (precision == GBS_DD)
+        return run_sweep_on<dd>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
+                                err_bound, status);
+    return run_sweep_on<float>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
+                               err_bound, status);
+}
 
 size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_pat, units).end; }
 
