@@ -86,8 +86,15 @@ int gbs_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, doubl
  *   P(S) = det(sigma_Q)^{-1/2} sum_{Z subset S} (-1)^{|S|-|Z|} det(I - O_Z)^{-1/2},
  * O_Z = rows/columns x and p of the modes in Z.
  * order 0: the exact sum over all 2^n subsets (n <= 40).
- * order 2..4: the paper's moment approximation (Methods, "Moments calculation"
- *   and "Approximation method") from minors removing <= order detectors.
+ * order j = 1..4 (the paper uses 2..4): the moment approximation (Methods,
+ *   "Partition function", "Moments calculation", "Approximation method"):
+ *   sector tables of the minors removing <= j detectors at t = e^{i nu} (nu on
+ *   L points, L - 1 a bound on the sector index with tail < 1e-14), inverse
+ *   DFT, per-sector maximum-entropy fit of moments 0..j, sum of the all-clicked
+ *   points.  precision GBS_FP64 (n <= 79) or GBS_FP32_SPLIT (FP32 complex
+ *   minors, FP64 sums and fits; n <= 112).  For order > 0, kappa returns the
+ *   sector bound K, err_bound is NaN, and status GBS_E_FIT marks a pattern where
+ *   some sector fit fell back to a lower order (logP is still returned).
  * Inputs: O (2M x 2M), logdet_sigmaQ (device, one double), patterns (n_pat x 2
  * uint64).  Outputs per pattern (each may be NULL except logP):
  *   logP      natural log of P(S)

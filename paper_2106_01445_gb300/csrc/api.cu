@@ -178,7 +178,8 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
     if (order == 0)
         return sweep_exact(ctx, M, O, logdet_sigmaQ, patterns, n_pat, precision, logP, kappa,
                            err_bound, status);
-    return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: order %d is not available", order);
+    return approx_prob(ctx, M, O, logdet_sigmaQ, patterns, n_pat, order, precision, logP, kappa,
+                       err_bound, status);
 }
 
 int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host, double eta,

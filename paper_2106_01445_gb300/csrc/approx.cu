@@ -1,0 +1,694 @@
+// The paper's moment approximation (Methods, "Partition function", "Moments
+// calculation", "Approximation method") for click patterns S of n detectors:
+//
+//  1. sectors: Z_Z(t) = det(I - t O_Z)^{-1/2} = sum_k c_k[Z] t^k, where
+//     c_k[Z] det(sigma_Q)^{-1/2} = P(k photons in Z, vacuum elsewhere).  The
+//     coefficients are extracted by a discrete Fourier transform over
+//     t_l = e^{i nu_l}, nu_l = 2 pi l / L (the paper's sum over nu);
+//  2. moments: the minors with w <= j detectors removed give the factorial
+//     moments of the vacuum count v in every sector,
+//        D_w(t) = sum_{|W| = w} Z_{S \ W}(t),  D_w^(k) = sum_v C(v, w) q_k(v);
+//     by Jacobi's identity Z_{S \ W}(t) = Z_S(t) det(G_WW)^{-1/2}, G = (I - t O_S)^{-1};
+//  3. inverse moment problem: q_k(v) ~ exp(-f(v)), deg f <= j, moments 0..j
+//     matched (convex maximum-entropy dual, damped Newton);
+//  4. P(S) ~ det(sigma_Q)^{-1/2} sum_k exp(-f_k(0)).
+//
+// Kernels: approx_plan (per pattern: a rigorous bound K on the sector index with
+// tail < 1e-14 Z_S(1), from Chernoff's inequality with det(I - rho O_S) at rho > 1;
+// DFT length L = K + 1), approx_minors (one CTA per (pattern, nu_l), l <= L/2 by
+// conjugate symmetry), approx_fit (one CTA per pattern: inverse DFT, fits, sum).
+#include <math.h>
+
+#include "gbs_internal.cuh"
+
+namespace {
+
+constexpr int kMaxOrder = 4;
+constexpr int kMinorThreads = 256;
+constexpr int kFitThreads = 128;
+constexpr int kPlanThreads = 256;
+constexpr double kTailEps = 1e-14;
+constexpr double kSectorEps = 1e-12;
+constexpr int kMaxK = 4095;
+constexpr int kApproxMaxN = 112;
+
+__host__ __device__ constexpr int sym(int d) { return d * (d + 1) / 2; }
+__host__ __device__ constexpr int pidx(int d, int i, int j) { return i * d - (i * (i - 1)) / 2 + (j - i); }
+__device__ __forceinline__ int pidx_any(int d, int i, int j) { return i <= j ? pidx(d, i, j) : pidx(d, j, i); }
+
+// ---- complex arithmetic ---------------------------------------------------------
+template <typename R> struct cx {
+    R re, im;
+};
+template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R> __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ cx<R> cinv(cx<R> a) {
+    R d = a.re * a.re + a.im * a.im;
+    return {a.re / d, -a.im / d};
+}
+// principal p^{-1/2} for Re p > 0: sqrt(p) = s + i q with s = sqrt((|p| + Re p)/2), q = Im p/(2 s)
+template <typename R> __device__ __forceinline__ cx<R> crsqrt(cx<R> p) {
+    R a = hypot(p.re, p.im);
+    R s = sqrt((a + p.re) * R(0.5));
+    R q = p.im / (R(2) * s);
+    return {s / a, -q / a};
+}
+__device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
+__device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
+
+// ---- plan: sector bound and DFT length per pattern ---------------------------------
+struct ApproxPlan {
+    int *pat_n;           // clicks (-1 invalid)
+    int *pat_L;           // DFT length
+    long long *unit_off;  // n_pat + 1: units (pattern, l) with l = 0..L/2
+    long long *total;     // total units (0 if over capacity)
+    int *overflow;
+    double *unit_D;       // 2 (j + 1) doubles per unit: D_w(t_l), w = 0..j
+    int *unit_flag;       // per pattern: non-positive pivot seen
+};
+
+// log det(I - rho O_S) by Cholesky in shared memory (packed); +inf if not positive definite
+__device__ double logdet_shift(const double *__restrict__ O, int M, const int *modes, int n, double rho,
+                               double *S, double *s_red) {
+    const int N = 2 * n, N2 = 2 * M, t = threadIdx.x;
+    for (int f = t; f < N * N; f += blockDim.x) {
+        int i = f / N, j = f - i * N;
+        if (j < i) continue;
+        int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
+        S[pidx(N, i, j)] = (i == j ? 1.0 : 0.0) - rho * O[(size_t)si * N2 + sj];
+    }
+    __syncthreads();
+    __shared__ int bad;
+    __shared__ double ld;
+    if (t == 0) { bad = 0; ld = 0.0; }
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        double d = S[pidx(N, k, k)];
+        if (!(d > 0.0)) { if (t == 0) bad = 1; }
+        __syncthreads();
+        if (bad) break;
+        double inv = 1.0 / d;
+        if (t == 0) ld += log(d);
+        const int Dt = N - k - 1;
+        for (int f = t; f < Dt * Dt; f += blockDim.x) {
+            int i = k + 1 + f / Dt, j = k + 1 + f % Dt;
+            if (j < i) continue;
+            S[pidx(N, i, j)] -= S[pidx(N, k, i)] * S[pidx(N, k, j)] * inv;
+        }
+        __syncthreads();
+    }
+    (void)s_red;
+    double r = bad ? INFINITY : ld;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) approx_plan_kernel(int M, const double *__restrict__ O,
+                                                                 const uint64_t *__restrict__ pats,
+                                                                 int n_pat, int order, int n_limit,
+                                                                 ApproxPlan pl) {
+    extern __shared__ double smem_d[];
+    __shared__ int modes[128];
+    __shared__ int s_n;
+    const int p = blockIdx.x, t = threadIdx.x;
+    const uint64_t lo = pats[2 * p], hi = pats[2 * p + 1];
+    if (t == 0) {
+        int n = 0;
+        bool ok = true;
+        for (int i = 0; i < 128; ++i) {
+            uint64_t w = i < 64 ? lo : hi;
+            if (w >> (i & 63) & 1ull) {
+                if (i >= M) ok = false;
+                else modes[n++] = i;
+            }
+        }
+        s_n = (ok && n <= n_limit) ? n : -1;
+    }
+    __syncthreads();
+    const int n = s_n;
+    int L = 1;
+    if (n > 0) {
+        double l1 = logdet_shift(O, M, modes, n, 1.0, smem_d, nullptr);
+        double best = INFINITY;
+        const double rhos[6] = {1.02, 1.06, 1.15, 1.35, 1.7, 2.5};
+        for (int q = 0; q < 6; ++q) {
+            double lr = logdet_shift(O, M, modes, n, rhos[q], smem_d, nullptr);
+            if (!isfinite(lr)) break;  // beyond the radius of convergence
+            // tail_{>K} <= rho^{-K} Z(rho), Z(rho)/Z(1) = exp((l1 - lr)/2)
+            double K = (0.5 * (l1 - lr) - log(kTailEps)) / log(rhos[q]);
+            best = fmin(best, K);
+        }
+        int K = isfinite(best) ? (int)ceil(best) : kMaxK;
+        if (K < n) K = n;
+        if (K > kMaxK) K = kMaxK;
+        L = K + 1;
+    }
+    if (t == 0) {
+        pl.pat_n[p] = n;
+        pl.pat_L[p] = n < 0 ? 0 : L;
+        pl.unit_flag[p] = 0;
+    }
+    (void)order;
+}
+
+__global__ void approx_scan_kernel(int n_pat, long long cap, ApproxPlan pl) {
+    // one thread: patterns are few thousand at most per call
+    if (threadIdx.x || blockIdx.x) return;
+    long long run = 0;
+    for (int p = 0; p < n_pat; ++p) {
+        pl.unit_off[p] = run;
+        int L = pl.pat_L[p];
+        run += L > 0 ? (L / 2 + 1) : 0;
+    }
+    pl.unit_off[n_pat] = run;
+    *pl.overflow = run > cap ? 1 : 0;
+    *pl.total = run > cap ? 0 : run;
+}
+
+// ---- minors at one nu point ------------------------------------------------------
+// unpivoted LDL^T pivots of a complex symmetric K x K matrix (packed, in registers);
+// returns prod p^{-1/2} (principal, Re p > 0 for accretive matrices)
+template <typename R, int K>
+__device__ __forceinline__ cx<R> ldl_rsqrt_prod(cx<R> (&a)[K * (K + 1) / 2], bool &bad) {
+    cx<R> f = mk<R>(R(1), R(0));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        cx<R> d = a[pidx(K, k, k)];
+        if (!(d.re > R(0))) bad = true;
+        f = f * crsqrt(d);
+        cx<R> inv = cinv(d);
+#pragma unroll
+        for (int i = k + 1; i < K; ++i) {
+            cx<R> li = a[pidx(K, k, i)] * inv;
+#pragma unroll
+            for (int j = i; j < K; ++j) a[pidx(K, i, j)] = a[pidx(K, i, j)] - li * a[pidx(K, k, j)];
+        }
+    }
+    return f;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, const double *__restrict__ O,
+                                                                    const uint64_t *__restrict__ pats,
+                                                                    int n_pat, int order,
+                                                                    unsigned long long *counter,
+                                                                    ApproxPlan pl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *G = (cx<R> *)smem_raw;
+    __shared__ int modes[128];
+    __shared__ long long s_u;
+    __shared__ int s_bad;
+    __shared__ double red[kMinorThreads / 32][2 * (kMaxOrder + 1)];
+    __shared__ double s_zs[2];
+    const int t = threadIdx.x;
+    const long long total = *pl.total;
+    for (;;) {
+        if (t == 0) s_u = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long u = s_u;
+        if (u >= total) break;
+        int lo_ = 0, hi_ = n_pat;
+        while (hi_ - lo_ > 1) {
+            int mid = (lo_ + hi_) >> 1;
+            if (pl.unit_off[mid] <= u) lo_ = mid; else hi_ = mid;
+        }
+        // skip patterns without units (equal offsets): take the last pattern whose
+        // offset is <= u and whose range contains u
+        int p = lo_;
+        while (p + 1 < n_pat && pl.unit_off[p + 1] <= u) ++p;
+        const int l = (int)(u - pl.unit_off[p]);
+        const int n = pl.pat_n[p], L = pl.pat_L[p];
+        const uint64_t wlo = pats[2 * p], whi = pats[2 * p + 1];
+        if (t == 0) {
+            int c = 0;
+            for (int i = 0; i < M; ++i) {
+                uint64_t w = i < 64 ? wlo : whi;
+                if (w >> (i & 63) & 1ull) modes[c++] = i;
+            }
+            s_bad = 0;
+        }
+        __syncthreads();
+        const int N = 2 * n, N2 = 2 * M;
+        // t = e^{i nu}, nu = 2 pi l / L; M_t = I - t O_S (complex symmetric)
+        double sn, cs;
+        sincospi(2.0 * (double)l / (double)L, &sn, &cs);
+        for (int f = t; f < N * N; f += kMinorThreads) {
+            int i = f / N, j = f - i * N;
+            if (j < i) continue;
+            int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
+            double o = O[(size_t)si * N2 + sj];
+            G[pidx(N, i, j)] = mk<R>((R)((i == j ? 1.0 : 0.0) - cs * o), (R)(-sn * o));
+        }
+        __syncthreads();
+        // symmetric sweep operator on every pivot: G <- -(I - t O_S)^{-1};
+        // Z_S(t) = prod of principal pivot^{-1/2} (pivots are the LDL^T pivots)
+        cx<double> zs = mk<double>(1.0, 0.0);
+        for (int k = 0; k < N; ++k) {
+            const cx<R> d = G[pidx(N, k, k)];
+            if (!(d.re > R(0)) && t == 0) s_bad = 1;
+            if (t == 0) zs = zs * widen(crsqrt(d));
+            const cx<R> inv = cinv(d);
+            for (int f = t; f < N * N; f += kMinorThreads) {
+                int i = f / N, j = f - i * N;
+                if (j < i || i == k || j == k) continue;
+                G[pidx(N, i, j)] = G[pidx(N, i, j)] - G[pidx_any(N, i, k)] * G[pidx_any(N, k, j)] * inv;
+            }
+            __syncthreads();
+            for (int i = t; i < N; i += kMinorThreads) {
+                if (i == k) continue;
+                G[pidx_any(N, i, k)] = G[pidx_any(N, i, k)] * inv;
+            }
+            if (t == 0) G[pidx(N, k, k)] = mk<R>(R(0), R(0)) - inv;
+            __syncthreads();
+        }
+        if (t == 0) { s_zs[0] = zs.re; s_zs[1] = zs.im; }
+        __syncthreads();
+        // entries of G = (I - t O_S)^{-1} are minus the swept matrix
+        auto g = [&](int i, int j) -> cx<R> { cx<R> v = G[pidx_any(N, i, j)]; return mk<R>(-v.re, -v.im); };
+        double acc[2 * (kMaxOrder + 1)];
+#pragma unroll
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) acc[w] = 0.0;
+        bool bad = false;
+        // w = 1
+        if (order >= 1)
+            for (int a = t; a < n; a += kMinorThreads) {
+                cx<R> m[3] = {g(2 * a, 2 * a), g(2 * a, 2 * a + 1), g(2 * a + 1, 2 * a + 1)};
+                cx<double> f = widen(ldl_rsqrt_prod<R, 2>(m, bad));
+                acc[2] += f.re;
+                acc[3] += f.im;
+            }
+        // w = 2
+        if (order >= 2)
+            for (int idx = t; idx < n * (n - 1) / 2; idx += kMinorThreads) {
+                int a = 0, rem = idx;
+                while (rem >= n - 1 - a) { rem -= n - 1 - a; ++a; }
+                int b = a + 1 + rem;
+                int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
+                cx<R> m[10];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = i; j < 4; ++j) m[pidx(4, i, j)] = g(rr[i], rr[j]);
+                cx<double> f = widen(ldl_rsqrt_prod<R, 4>(m, bad));
+                acc[4] += f.re;
+                acc[5] += f.im;
+            }
+        // w = 3 (and w = 4 from each triple's factorisation)
+        if (order >= 3) {
+            const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
+            for (long long idx = t; idx < ntri; idx += kMinorThreads) {
+                int a = 0;
+                long long rem = idx;
+                for (;;) {
+                    long long c2 = (long long)(n - 1 - a) * (n - 2 - a) / 2;
+                    if (rem < c2) break;
+                    rem -= c2;
+                    ++a;
+                }
+                int b = a + 1;
+                for (;;) {
+                    long long c1 = n - 1 - b;
+                    if (rem < c1) break;
+                    rem -= c1;
+                    ++b;
+                }
+                int c = b + 1 + (int)rem;
+                int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
+                cx<R> m[21];
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+#pragma unroll
+                    for (int j = i; j < 6; ++j) m[pidx(6, i, j)] = g(rr[i], rr[j]);
+                // keep the triple's LDL^T: after ldl_rsqrt_prod, m holds the updated
+                // trailing blocks; redo the factorisation explicitly to keep L and D
+                cx<R> Lf[15], Dv[6];
+                cx<R> f3 = mk<R>(R(1), R(0));
+                {
+                    cx<R> w6[21];
+#pragma unroll
+                    for (int i = 0; i < 21; ++i) w6[i] = m[i];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        cx<R> d = w6[pidx(6, k, k)];
+                        if (!(d.re > R(0))) bad = true;
+                        Dv[k] = d;
+                        f3 = f3 * crsqrt(d);
+                        cx<R> inv = cinv(d);
+#pragma unroll
+                        for (int i = k + 1; i < 6; ++i) {
+                            cx<R> li = w6[pidx(6, k, i)] * inv;
+                            Lf[pidx(5, k, i - 1)] = li;  // L[i][k], k < i
+#pragma unroll
+                            for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = w6[pidx(6, i, j)] - li * w6[pidx(6, k, j)];
+                        }
+                    }
+                }
+                cx<double> f3d = widen(f3);
+                acc[6] += f3d.re;
+                acc[7] += f3d.im;
+                if (order >= 4)
+                    for (int d4 = c + 1; d4 < n; ++d4) {
+                        // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2)
+                        cx<R> y0[6], y1[6];
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) {
+                            cx<R> v0 = g(rr[i], 2 * d4), v1 = g(rr[i], 2 * d4 + 1);
+#pragma unroll
+                            for (int k = 0; k < i; ++k) {
+                                v0 = v0 - Lf[pidx(5, k, i - 1)] * y0[k];
+                                v1 = v1 - Lf[pidx(5, k, i - 1)] * y1[k];
+                            }
+                            y0[i] = v0;
+                            y1[i] = v1;
+                        }
+                        cx<R> s00 = g(2 * d4, 2 * d4), s01 = g(2 * d4, 2 * d4 + 1), s11 = g(2 * d4 + 1, 2 * d4 + 1);
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            cx<R> di = cinv(Dv[k]);
+                            cx<R> z0 = y0[k] * di, z1 = y1[k] * di;
+                            s00 = s00 - z0 * y0[k];
+                            s01 = s01 - z0 * y1[k];
+                            s11 = s11 - z1 * y1[k];
+                        }
+                        cx<R> m2[3] = {s00, s01, s11};
+                        cx<double> f4 = widen(f3 * ldl_rsqrt_prod<R, 2>(m2, bad));
+                        acc[8] += f4.re;
+                        acc[9] += f4.im;
+                    }
+            }
+        }
+        if (bad) s_bad = 1;
+        // deterministic block reduction of the (j + 1) complex sums
+#pragma unroll
+        for (int w = 2; w < 2 * (kMaxOrder + 1); ++w)
+            for (int off = 16; off; off >>= 1) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], off);
+        if ((t & 31) == 0)
+#pragma unroll
+            for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) red[t >> 5][w] = acc[w];
+        __syncthreads();
+        if (t == 0) {
+            const cx<double> z = mk<double>(s_zs[0], s_zs[1]);
+            double *out = pl.unit_D + (size_t)u * 2 * (kMaxOrder + 1);
+            out[0] = z.re;
+            out[1] = z.im;
+            for (int w = 1; w <= kMaxOrder; ++w) {
+                double re = 0.0, im = 0.0;
+                for (int q = 0; q < kMinorThreads / 32; ++q) {
+                    re += red[q][2 * w];
+                    im += red[q][2 * w + 1];
+                }
+                cx<double> v = z * mk<double>(re, im);
+                out[2 * w] = w <= order ? v.re : 0.0;
+                out[2 * w + 1] = w <= order ? v.im : 0.0;
+            }
+            if (s_bad) atomicOr(pl.unit_flag + p, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- per-sector fit (maximum-entropy dual, damped Newton) ----------------------------
+// support x_s = v_s / n for v in [v0, n-1]; moments m (m_0 = 1); J + 1 coefficients
+__device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
+    const int S = n - v0;
+    auto phi_grad = [&](const double *aa, double *g, double *H, double &phi) {
+        double pw[2 * kMaxOrder + 1];
+        for (int q = 0; q <= 2 * J; ++q) pw[q] = 0.0;
+        phi = 0.0;
+        for (int s = 0; s < S; ++s) {
+            double x = (double)(v0 + s) / n, f = 0.0, xp = 1.0;
+            for (int i = 0; i <= J; ++i) { f += aa[i] * xp; xp *= x; }
+            double q = exp(-f);
+            phi += q;
+            xp = 1.0;
+            for (int i = 0; i <= 2 * J; ++i) { pw[i] += xp * q; xp *= x; }
+        }
+        for (int i = 0; i <= J; ++i) {
+            phi += aa[i] * m[i];
+            if (g) g[i] = m[i] - pw[i];
+            if (H)
+                for (int k = 0; k <= J; ++k) H[i * (kMaxOrder + 1) + k] = pw[i + k];
+        }
+    };
+    for (int i = 0; i <= J; ++i) a[i] = 0.0;
+    a[0] = log((double)S);
+    double g[kMaxOrder + 1], H[(kMaxOrder + 1) * (kMaxOrder + 1)], phi;
+    phi_grad(a, g, H, phi);
+    for (int it = 0; it < 200; ++it) {
+        double gmax = 0.0;
+        for (int i = 0; i <= J; ++i) gmax = fmax(gmax, fabs(g[i]));
+        if (gmax <= 1e-13) return true;
+        // Cholesky solve H step = g
+        double Lc[(kMaxOrder + 1) * (kMaxOrder + 1)], st[kMaxOrder + 1];
+        for (int i = 0; i <= J; ++i)
+            for (int k = 0; k <= i; ++k) {
+                double v = H[i * (kMaxOrder + 1) + k];
+                for (int q = 0; q < k; ++q) v -= Lc[i * (kMaxOrder + 1) + q] * Lc[k * (kMaxOrder + 1) + q];
+                if (i == k) {
+                    if (!(v > 0.0)) return false;
+                    Lc[i * (kMaxOrder + 1) + i] = sqrt(v);
+                } else {
+                    Lc[i * (kMaxOrder + 1) + k] = v / Lc[k * (kMaxOrder + 1) + k];
+                }
+            }
+        for (int i = 0; i <= J; ++i) {
+            double v = g[i];
+            for (int q = 0; q < i; ++q) v -= Lc[i * (kMaxOrder + 1) + q] * st[q];
+            st[i] = v / Lc[i * (kMaxOrder + 1) + i];
+        }
+        for (int i = J; i >= 0; --i) {
+            double v = st[i];
+            for (int q = i + 1; q <= J; ++q) v -= Lc[q * (kMaxOrder + 1) + i] * st[q];
+            st[i] = v / Lc[i * (kMaxOrder + 1) + i];
+        }
+        double gst = 0.0;
+        for (int i = 0; i <= J; ++i) gst += g[i] * st[i];
+        double tstep = 1.0, an[kMaxOrder + 1], gn[kMaxOrder + 1], Hn[(kMaxOrder + 1) * (kMaxOrder + 1)], phin;
+        for (;;) {
+            for (int i = 0; i <= J; ++i) an[i] = a[i] - tstep * st[i];
+            phi_grad(an, gn, Hn, phin);
+            if (isfinite(phin) && phin <= phi - 1e-4 * tstep * gst) break;
+            double gnmax = 0.0;
+            for (int i = 0; i <= J; ++i) gnmax = fmax(gnmax, fabs(gn[i]));
+            if (isfinite(phin) && phin <= phi + 1e-14 * fabs(phi) && gnmax <= 0.5 * gmax) break;
+            tstep *= 0.5;
+            if (tstep < 1e-12) return false;
+        }
+        for (int i = 0; i <= J; ++i) { a[i] = an[i]; g[i] = gn[i]; }
+        for (int i = 0; i < (kMaxOrder + 1) * (kMaxOrder + 1); ++i) H[i] = Hn[i];
+        phi = phin;
+    }
+    double gmax = 0.0;
+    for (int i = 0; i <= J; ++i) gmax = fmax(gmax, fabs(g[i]));
+    return gmax <= 1e-10;
+}
+
+__device__ __forceinline__ double stirling2(int i, int w) {
+    // S(i, w) for i, w <= 4
+    const double tab[5][5] = {{1, 0, 0, 0, 0}, {0, 1, 0, 0, 0}, {0, 1, 1, 0, 0}, {0, 1, 3, 1, 0}, {0, 1, 7, 6, 1}};
+    return tab[i][w];
+}
+
+__global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int order,
+                                                               const double *__restrict__ logdet,
+                                                               ApproxPlan pl, double *__restrict__ logP,
+                                                               double *__restrict__ kappa,
+                                                               double *__restrict__ err_bound,
+                                                               int32_t *__restrict__ status) {
+    extern __shared__ double fsm[];
+    const int p = blockIdx.x, t = threadIdx.x;
+    const int n = pl.pat_n[p], L = pl.pat_L[p];
+    __shared__ double s_max;
+    __shared__ int s_fallback;
+    if (n < 0 || *pl.overflow) {
+        if (t == 0) {
+            logP[p] = nan("");
+            if (kappa) kappa[p] = nan("");
+            if (err_bound) err_bound[p] = nan("");
+            if (status) status[p] = n < 0 ? GBS_E_INVALID : GBS_E_NOMEM;
+        }
+        return;
+    }
+    const int K = L - 1, H = L / 2;
+    double *D = fsm;                       // (order + 1) x (K + 1) sector tables
+    double *part = fsm + (order + 1) * (K + 1);  // K + 1 fitted last points
+    const double *U = pl.unit_D + (size_t)pl.unit_off[p] * 2 * (kMaxOrder + 1);
+    // inverse DFT (real coefficients; conjugate symmetry of the real matrix O)
+    for (int idx = t; idx < (order + 1) * (K + 1); idx += kFitThreads) {
+        int w = idx / (K + 1), k = idx - w * (K + 1);
+        double s = U[2 * w];  // l = 0
+        for (int l = 1; l <= H; ++l) {
+            double sn, cs;
+            sincospi(2.0 * (double)(((long long)k * l) % L) / (double)L, &sn, &cs);
+            const double re = U[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w];
+            const double im = U[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w + 1];
+            double term = re * cs + im * sn;       // Re(D(t_l) e^{-i 2 pi k l / L})
+            s += (2 * l == L) ? term : 2.0 * term;
+        }
+        D[w * (K + 1) + k] = s / L;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double mx = 0.0;
+        for (int k = 0; k <= K; ++k) mx = fmax(mx, D[k]);
+        s_max = mx;
+        s_fallback = 0;
+    }
+    __syncthreads();
+    const double floor_ = kSectorEps * s_max;
+    for (int k = t; k <= K; k += kFitThreads) {
+        double val = 0.0;
+        const double D0 = D[k];
+        if (n == 0) {
+            val = (k == 0) ? D0 : 0.0;
+        } else if (k >= n && D0 >= floor_ && D0 > 0.0) {
+            const int v0 = n - k > 0 ? n - k : 0;
+            const int S = n - v0;
+            const int Jmax = order < S - 1 ? order : S - 1;
+            double mu[kMaxOrder + 1];
+            for (int i = 0; i <= Jmax; ++i) {
+                double s = 0.0, fw = 1.0;
+                for (int w = 0; w <= i; ++w) {
+                    s += stirling2(i, w) * fw * D[w * (K + 1) + k];
+                    fw *= (w + 1);
+                }
+                mu[i] = s;
+            }
+            bool done = false;
+            for (int J = Jmax; J >= 0 && !done; --J) {
+                double m[kMaxOrder + 1], a[kMaxOrder + 1];
+                double np = 1.0;
+                for (int i = 0; i <= J; ++i) { m[i] = mu[i] / np / mu[0]; np *= n; }
+                if (maxent_fit(v0, n, J, m, a)) {
+                    val = mu[0] * exp(-a[0]);
+                    done = true;
+                    if (J != Jmax) s_fallback = 1;
+                }
+            }
+            if (!done) s_fallback = 1;
+        }
+        part[k] = val;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int k = 0; k <= K; ++k) s += part[k];
+        logP[p] = s > 0.0 ? -0.5 * (*logdet) + log(s) : -INFINITY;
+        if (kappa) kappa[p] = (double)K;
+        if (err_bound) err_bound[p] = nan("");
+        int st = GBS_OK;
+        if (pl.unit_flag[p]) st = GBS_E_NOT_SPD;
+        else if (s_fallback) st = GBS_E_FIT;
+        if (status) status[p] = st;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct ApproxOffsets {
+    size_t counter, total, overflow, pat_n, pat_L, unit_off, unit_flag, unit_D, end;
+};
+
+ApproxOffsets approx_offsets(int n_pat, long long units) {
+    ApproxOffsets o;
+    o.counter = 0;
+    o.total = 8;
+    o.overflow = 16;
+    o.pat_n = align256(20);
+    o.pat_L = align256(o.pat_n + 4 * (size_t)n_pat);
+    o.unit_off = align256(o.pat_L + 4 * (size_t)n_pat);
+    o.unit_flag = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
+    o.unit_D = align256(o.unit_flag + 4 * (size_t)n_pat);
+    o.end = o.unit_D + 8 * 2 * (kMaxOrder + 1) * (size_t)units;
+    return o;
+}
+
+ApproxPlan approx_plan_from(void *ws, int n_pat) {
+    ApproxOffsets o = approx_offsets(n_pat, 0);
+    char *b = (char *)ws;
+    ApproxPlan pl;
+    pl.total = (long long *)(b + o.total);
+    pl.overflow = (int *)(b + o.overflow);
+    pl.pat_n = (int *)(b + o.pat_n);
+    pl.pat_L = (int *)(b + o.pat_L);
+    pl.unit_off = (long long *)(b + o.unit_off);
+    pl.unit_flag = (int *)(b + o.unit_flag);
+    pl.unit_D = (double *)(b + o.unit_D);
+    return pl;
+}
+
+template <typename R>
+int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
+               int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status) {
+    // shared memory: the packed complex inverse of the largest pattern allowed
+    const int nmax_smem = sizeof(R) == 8 ? 79 : kApproxMaxN;
+    const size_t minor_smem = sizeof(cx<R>) * (size_t)sym(2 * nmax_smem);
+    static_assert(kMaxK + 1 <= 4096, "sector table");
+    if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
+        int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
+        if (st) return st;
+    }
+    ApproxPlan pl = approx_plan_from(ctx->ws, n_pat);
+    const size_t plan_smem = sizeof(double) * (size_t)sym(2 * kApproxMaxN);
+    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)plan_smem));
+    approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
+                                                                        nmax_smem, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    long long cap = (long long)((ctx->ws_bytes - approx_offsets(n_pat, 0).unit_D) / (8 * 2 * (kMaxOrder + 1)));
+    approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, cap, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    // size the per-unit results (one readback), then re-plan if the workspace grew
+    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.unit_off + n_pat, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    long long need = *(long long *)ctx->pinned;
+    if (need > cap) {
+        int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, need).end);
+        if (st) return st;
+        pl = approx_plan_from(ctx->ws, n_pat);
+        approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
+                                                                            nmax_smem, pl);
+        cap = (long long)((ctx->ws_bytes - approx_offsets(n_pat, 0).unit_D) / (8 * 2 * (kMaxOrder + 1)));
+        approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, cap, pl);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    GBS_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, 8, ctx->stream));  // work counter
+    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)minor_smem));
+    int nb = 0;
+    GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, approx_minors_kernel<R>, kMinorThreads,
+                                                                minor_smem));
+    if (nb < 1) nb = 1;
+    int st = gbs_timing_begin(ctx);
+    if (st) return st;
+    approx_minors_kernel<R><<<ctx->num_sms * nb, kMinorThreads, minor_smem, ctx->stream>>>(
+        M, O, pats, n_pat, order, (unsigned long long *)ctx->ws, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    st = gbs_timing_end(ctx);
+    if (st) return st;
+    const size_t fit_smem = sizeof(double) * (size_t)(kMaxOrder + 2) * (kMaxK + 1);
+    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fit_smem));
+    approx_fit_kernel<<<n_pat, kFitThreads, fit_smem, ctx->stream>>>(n_pat, order, logdet, pl, logP, kappa,
+                                                                    err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
+
+}  // namespace
+
+int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
+                int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
+                int32_t *status) {
+    if (order < 1 || order > kMaxOrder)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: approximation order %d not in 1..%d", order, kMaxOrder);
+    if (precision == GBS_FP64)
+        return run_approx<double>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
+    if (precision == GBS_FP32_SPLIT)
+        return run_approx<float>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
+    return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: the approximation runs in FP64 or the FP32 split");
+}

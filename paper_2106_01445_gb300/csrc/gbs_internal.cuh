@@ -66,4 +66,7 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
                    double *logP, double *kappa, double *err_bound, int32_t *status);
 size_t sweep_workspace_bytes(int n_pat, long long units);
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision);
+int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
+                int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
+                int32_t *status);
 int peak_flops(gbs_ctx *ctx, int kind, double *flops);
