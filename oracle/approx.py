@@ -30,9 +30,10 @@ Readings where the paper is silent (each listed in the design notes):
 * x = v / n is the variable inside the Newton solve (conditioning only);
 * the sector sum stops at K_max, the first K whose partial sum of c_k[S]
   reaches (1 - 1e-14) det(I - O_S)^{-1/2};
-* a sector whose mass D_0^(k) is below eps_sector times the largest sector
-  mass is rounding noise (e.g. the odd sectors of a lossless state, which are
-  exactly zero) and contributes nothing.
+* a sector whose mass D_0^(k) is below eps_sector = 1e-9 times the largest
+  sector mass contributes nothing: such sectors are rounding noise (e.g. the
+  odd sectors of a lossless state, exactly zero) or far tails whose moments a
+  Fourier extraction over nu resolves only to ~1e-16 K / eps_sector.
 """
 from __future__ import annotations
 
@@ -42,7 +43,7 @@ from itertools import combinations
 import numpy as np
 
 TAIL_EPS = 1e-14
-EPS_SECTOR = 1e-12
+EPS_SECTOR = 1e-9
 
 
 def sub_rows(modes, M):

@@ -28,7 +28,7 @@ constexpr int kMinorThreads = 256;
 constexpr int kFitThreads = 128;
 constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
-constexpr double kSectorEps = 1e-12;
+constexpr double kSectorEps = 1e-9;  // sectors below this share of the largest are dropped
 constexpr int kMaxK = 4095;
 constexpr int kApproxMaxN = 112;
 
