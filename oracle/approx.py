@@ -28,12 +28,16 @@ Readings where the paper is silent (each listed in the design notes):
 * the polynomial degree is min(j, |support| - 1), so the fit is exact when
   the support has at most j + 1 points;
 * x = v / n is the variable inside the Newton solve (conditioning only);
-* the sector sum stops at K_max, the first K whose partial sum of c_k[S]
-  reaches (1 - 1e-14) det(I - O_S)^{-1/2};
-* a sector whose mass D_0^(k) is below eps_sector = 1e-9 times the largest
-  sector mass contributes nothing: such sectors are rounding noise (e.g. the
-  odd sectors of a lossless state, exactly zero) or far tails whose moments a
-  Fourier extraction over nu resolves only to ~1e-16 K / eps_sector.
+* the paper's discrete set of nu is a circle |t| = rho: rho is the Chernoff
+  saddle for sector n, rho = argmin over the radii RHOS at which I -+ rho O_S
+  stay positive definite (the largest excluded) of log Z_S(rho) - n log rho,
+  so that the sectors carrying the all-clicked point sit near the peak of
+  c_k rho^k (for improbable patterns they lie far in the upper tail);
+* the sector sum stops at K_max, the first K whose partial sum of c_k rho^k
+  reaches (1 - 1e-14) Z_S(rho);
+* a sector whose tilted mass D_0^(k) rho^k is below eps_sector = 1e-12 of the
+  largest contributes nothing: such sectors are rounding noise (e.g. the odd
+  sectors of a lossless state, exactly zero).
 """
 from __future__ import annotations
 
@@ -43,7 +47,8 @@ from itertools import combinations
 import numpy as np
 
 TAIL_EPS = 1e-14
-EPS_SECTOR = 1e-9
+EPS_SECTOR = 1e-12
+RHOS = (1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0)
 
 
 def sub_rows(modes, M):
@@ -70,10 +75,38 @@ def series_coeffs(Osub: np.ndarray, K: int) -> np.ndarray:
     return c
 
 
-def choose_kmax(O: np.ndarray, M: int, modes) -> int:
-    """Smallest K with sum_{k<=K} c_k[S] >= (1 - TAIL_EPS) det(I - O_S)^{-1/2}."""
+def _pd_logdet(X: np.ndarray):
+    """log det X if X is positive definite, else None."""
+    try:
+        L = np.linalg.cholesky(X)
+    except np.linalg.LinAlgError:
+        return None
+    return 2.0 * np.log(np.diag(L)).sum()
+
+
+def choose_tilt(O: np.ndarray, M: int, modes) -> float:
+    """rho = argmin_{rho in RHOS, valid, not the largest valid} log Z_S(rho) - n log rho."""
     rows = sub_rows(modes, M)
     Os = O[np.ix_(rows, rows)]
+    n = len(modes)
+    if n == 0:
+        return 1.0
+    I = np.eye(len(rows))
+    valid = []
+    for rho in RHOS:
+        l_minus = _pd_logdet(I - rho * Os)
+        if l_minus is None or (rho > 1.0 and _pd_logdet(I + rho * Os) is None):
+            break
+        valid.append((rho, -0.5 * l_minus))          # (rho, log Z_S(rho))
+    cands = valid[:-1] if len(valid) > 1 else valid
+    best = min(cands, key=lambda v: (v[1] - n * math.log(v[0]), v[0]))
+    return best[0]
+
+
+def choose_kmax(O: np.ndarray, M: int, modes, rho: float = 1.0) -> int:
+    """Smallest K with sum_{k<=K} c_k rho^k >= (1 - TAIL_EPS) Z_S(rho)."""
+    rows = sub_rows(modes, M)
+    Os = O[np.ix_(rows, rows)] * rho
     if Os.size == 0:
         return 0
     total = np.linalg.det(np.eye(len(rows)) - Os) ** -0.5
@@ -89,8 +122,9 @@ def choose_kmax(O: np.ndarray, M: int, modes) -> int:
         K *= 2
 
 
-def factorial_moment_tables(O: np.ndarray, M: int, modes, j: int, K: int) -> np.ndarray:
-    """D[w, k] = sum over groups W of S with |W| = w of c_k[S \\ W], w = 0..j."""
+def factorial_moment_tables(O: np.ndarray, M: int, modes, j: int, K: int,
+                            rho: float = 1.0) -> np.ndarray:
+    """D[w, k] rho^k with D[w, k] = sum over groups W of S with |W| = w of c_k[S \\ W], w = 0..j."""
     modes = list(modes)
     n = len(modes)
     D = np.zeros((j + 1, K + 1))
@@ -98,7 +132,7 @@ def factorial_moment_tables(O: np.ndarray, M: int, modes, j: int, K: int) -> np.
         for W in combinations(range(n), w):
             keep = [modes[a] for a in range(n) if a not in W]
             rows = sub_rows(keep, M)
-            D[w] += series_coeffs(O[np.ix_(rows, rows)], K)
+            D[w] += series_coeffs(rho * O[np.ix_(rows, rows)], K)
     return D
 
 
@@ -185,21 +219,29 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
     """log P(S) by the order-j approximation.  Returns (logP, info dict)."""
     modes = list(modes)
     n = len(modes)
+    rho = choose_tilt(O, M, modes)
     if K is None:
-        K = choose_kmax(O, M, modes)
-    D = factorial_moment_tables(O, M, modes, j, K)
-    total, flags = 0.0, 0
-    parts = np.zeros(K + 1)
+        K = choose_kmax(O, M, modes, rho)
+    D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
+    flags = 0
+    parts = np.zeros(K + 1)                                  # tilted last points
     floor = eps_sector * D[0].max()
     for k in range(K + 1):
         if D[0, k] < floor:
             continue
         val, fl = sector_last_point(D[:, k], n, k, j)
         parts[k] = val
-        total += val
         flags = max(flags, fl)
-    logP = -0.5 * logdet_sigmaQ + (math.log(total) if total > 0 else -math.inf)
-    return logP, dict(K=K, D=D, parts=parts, flag=flags)
+    # sum_k parts[k] rho^{-k}, in logs (rho^{-k} can leave the double range)
+    nz = np.nonzero(parts > 0)[0]
+    if nz.size:
+        lg = np.log(parts[nz]) - nz * math.log(rho)
+        top = lg.max()
+        logsum = top + math.log(np.exp(lg - top).sum())
+    else:
+        logsum = -math.inf
+    logP = -0.5 * logdet_sigmaQ + logsum
+    return logP, dict(K=K, D=D, parts=parts, flag=flags, rho=rho)
 
 
 def exact_sector_last_points(O: np.ndarray, M: int, modes, K: int) -> np.ndarray:

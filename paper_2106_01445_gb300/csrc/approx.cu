@@ -13,10 +13,13 @@
 //     matched (convex maximum-entropy dual, damped Newton);
 //  4. P(S) ~ det(sigma_Q)^{-1/2} sum_k exp(-f_k(0)).
 //
-// Kernels: approx_plan (per pattern: a rigorous bound K on the sector index with
-// tail < 1e-14 Z_S(1), from Chernoff's inequality with det(I - rho O_S) at rho > 1;
-// DFT length L = K + 1), approx_minors (one CTA per (pattern, nu_l), l <= L/2 by
-// conjugate symmetry), approx_fit (one CTA per pattern: inverse DFT, fits, sum).
+// The circle |t| = rho is tilted to the Chernoff saddle of sector n so that the
+// sectors carrying the all-clicked point (far in the upper tail for improbable
+// patterns) sit near the peak of c_k rho^k and keep their relative precision.
+// Kernels: approx_plan (per pattern: rho, and a rigorous bound K on the sector
+// index with tilted tail < 1e-14 Z_S(rho) from Chernoff's inequality; DFT length
+// L = K + 1), approx_minors (one CTA per (pattern, nu_l), l <= L/2 by conjugate
+// symmetry), approx_fit (one CTA per pattern: inverse DFT, fits, sum).
 #include <math.h>
 
 #include "gbs_internal.cuh"
@@ -28,7 +31,9 @@ constexpr int kMinorThreads = 256;
 constexpr int kFitThreads = 128;
 constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
-constexpr double kSectorEps = 1e-9;  // sectors below this share of the largest are dropped
+constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
+constexpr int kNumRho = 8;
+__constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0};
 constexpr int kMaxK = 4095;
 constexpr int kApproxMaxN = 112;
 
@@ -64,6 +69,7 @@ __device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
 struct ApproxPlan {
     int *pat_n;           // clicks (-1 invalid)
     int *pat_L;           // DFT length
+    double *pat_rho;      // contour radius
     long long *unit_off;  // n_pat + 1: units (pattern, l) with l = 0..L/2
     long long *total;     // total units (0 if over capacity)
     int *overflow;
@@ -131,17 +137,29 @@ __global__ void __launch_bounds__(kPlanThreads) approx_plan_kernel(int M, const 
     __syncthreads();
     const int n = s_n;
     int L = 1;
+    double rho_t = 1.0;
     if (n > 0) {
-        double l1 = logdet_shift(O, M, modes, n, 1.0, smem_d, nullptr);
-        double best = INFINITY;
-        const double rhos[6] = {1.02, 1.06, 1.15, 1.35, 1.7, 2.5};
-        for (int q = 0; q < 6; ++q) {
-            double lr = logdet_shift(O, M, modes, n, rhos[q], smem_d, nullptr);
-            if (!isfinite(lr)) break;  // beyond the radius of convergence
-            // tail_{>K} <= rho^{-K} Z(rho), Z(rho)/Z(1) = exp((l1 - lr)/2)
-            double K = (0.5 * (l1 - lr) - log(kTailEps)) / log(rhos[q]);
-            best = fmin(best, K);
+        // log Z_S(rho) = -1/2 log det(I - rho O_S) on the radii where I -+ rho O_S are
+        // positive definite (then I - t O_S is accretive on the whole circle |t| = rho)
+        double lz[kNumRho];
+        int nv = 0;
+        for (int q = 0; q < kNumRho; ++q) {
+            double lm = logdet_shift(O, M, modes, n, kRhos[q], smem_d, nullptr);
+            if (!isfinite(lm)) break;
+            if (q > 0 && !isfinite(logdet_shift(O, M, modes, n, -kRhos[q], smem_d, nullptr))) break;
+            lz[q] = -0.5 * lm;
+            nv = q + 1;
         }
+        // contour radius: Chernoff saddle for sector n, argmin log Z(rho) - n log rho
+        const int nc = nv > 1 ? nv - 1 : 1;
+        int qt = 0;
+        for (int q = 1; q < nc; ++q)
+            if (lz[q] - n * log(kRhos[q]) < lz[qt] - n * log(kRhos[qt])) qt = q;
+        rho_t = kRhos[qt];
+        // sector range: sum_{k > K} c_k rho_t^k <= (rho_t/rho)^K Z(rho) <= eps Z(rho_t)
+        double best = INFINITY;
+        for (int q = qt + 1; q < nv; ++q)
+            best = fmin(best, (lz[q] - lz[qt] - log(kTailEps)) / log(kRhos[q] / rho_t));
         int K = isfinite(best) ? (int)ceil(best) : kMaxK;
         if (K < n) K = n;
         if (K > kMaxK) K = kMaxK;
@@ -150,6 +168,7 @@ __global__ void __launch_bounds__(kPlanThreads) approx_plan_kernel(int M, const 
     if (t == 0) {
         pl.pat_n[p] = n;
         pl.pat_L[p] = n < 0 ? 0 : L;
+        pl.pat_rho[p] = rho_t;
         pl.unit_flag[p] = 0;
     }
     (void)order;
@@ -233,9 +252,12 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
         }
         __syncthreads();
         const int N = 2 * n, N2 = 2 * M;
-        // t = e^{i nu}, nu = 2 pi l / L; M_t = I - t O_S (complex symmetric)
+        // t = rho e^{i nu}, nu = 2 pi l / L; M_t = I - t O_S (complex symmetric)
         double sn, cs;
         sincospi(2.0 * (double)l / (double)L, &sn, &cs);
+        const double rho = pl.pat_rho[p];
+        sn *= rho;
+        cs *= rho;
         for (int f = t; f < N * N; f += kMinorThreads) {
             int i = f / N, j = f - i * N;
             if (j < i) continue;
@@ -575,9 +597,15 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
     }
     __syncthreads();
     if (t == 0) {
+        // sum_k part_k rho^{-k} in logs (the tables are tilted by rho^k)
+        const double lr = log(pl.pat_rho[p]);
+        double top = -INFINITY;
+        for (int k = 0; k <= K; ++k)
+            if (part[k] > 0.0) top = fmax(top, log(part[k]) - k * lr);
         double s = 0.0;
-        for (int k = 0; k <= K; ++k) s += part[k];
-        logP[p] = s > 0.0 ? -0.5 * (*logdet) + log(s) : -INFINITY;
+        for (int k = 0; k <= K; ++k)
+            if (part[k] > 0.0) s += exp(log(part[k]) - k * lr - top);
+        logP[p] = s > 0.0 ? -0.5 * (*logdet) + top + log(s) : -INFINITY;
         if (kappa) kappa[p] = (double)K;
         if (err_bound) err_bound[p] = nan("");
         int st = GBS_OK;
@@ -590,7 +618,7 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct ApproxOffsets {
-    size_t counter, total, overflow, pat_n, pat_L, unit_off, unit_flag, unit_D, end;
+    size_t counter, total, overflow, pat_n, pat_L, pat_rho, unit_off, unit_flag, unit_D, end;
 };
 
 ApproxOffsets approx_offsets(int n_pat, long long units) {
@@ -600,7 +628,8 @@ ApproxOffsets approx_offsets(int n_pat, long long units) {
     o.overflow = 16;
     o.pat_n = align256(20);
     o.pat_L = align256(o.pat_n + 4 * (size_t)n_pat);
-    o.unit_off = align256(o.pat_L + 4 * (size_t)n_pat);
+    o.pat_rho = align256(o.pat_L + 4 * (size_t)n_pat);
+    o.unit_off = align256(o.pat_rho + 8 * (size_t)n_pat);
     o.unit_flag = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
     o.unit_D = align256(o.unit_flag + 4 * (size_t)n_pat);
     o.end = o.unit_D + 8 * 2 * (kMaxOrder + 1) * (size_t)units;
@@ -615,6 +644,7 @@ ApproxPlan approx_plan_from(void *ws, int n_pat) {
     pl.overflow = (int *)(b + o.overflow);
     pl.pat_n = (int *)(b + o.pat_n);
     pl.pat_L = (int *)(b + o.pat_L);
+    pl.pat_rho = (double *)(b + o.pat_rho);
     pl.unit_off = (long long *)(b + o.unit_off);
     pl.unit_flag = (int *)(b + o.unit_flag);
     pl.unit_D = (double *)(b + o.unit_D);

@@ -79,6 +79,25 @@ def test_order_covering_support_is_exact(ctx):
         assert np.abs(res["logP"] - ref["logP"]).max() < 1e-9
 
 
+def test_improbable_patterns_tilted_contour(ctx):
+    # weak squeezing and strong loss: the sectors that matter sit in the far
+    # upper tail; exact for n <= j + 1, oracle parity above
+    M = 10
+    U = g.haar_unitary(M, 401)
+    r = g.squeezing(M, 10, 0.2, 0.4, 401)
+    mode_sets = [[0, 1, 2, 3, 4], [0, 1, 2, 3, 4, 5, 6, 7, 8], [1, 3, 5, 6, 7, 8, 9]]
+    pats = np.stack([g.modes_to_pattern(m) for m in mode_sets])
+    for eta in (0.3, 0.9):
+        st = oracle.build_state(U, r, eta)
+        res = run(ctx, U, r, eta, pats, 4, "fp64")
+        ex = oracle.prob_exact(st, pats[:1], dd=True)["logP"][0]
+        assert abs(res["logP"][0] - ex) < 1e-9
+        for i, modes in enumerate(mode_sets):
+            ref, info = ap.approx_logprob(st.O, st.logdet, M, modes, 4)
+            assert info["rho"] > 1.0
+            assert abs(res["logP"][i] - ref) < 1e-8, (eta, i)
+
+
 def test_m50_workload_sample(ctx):
     # the 50-mode workload's launch shape on a slice of its patterns; the oracle
     # checks the smaller ones
@@ -90,7 +109,8 @@ def test_m50_workload_sample(ctx):
     assert np.isin(res["status"], (0, 7)).all()
     assert np.isfinite(res["logP"]).all()
     st = oracle.build_state(U, r, c.eta)
-    for i in np.nonzero(n <= 13)[0][:4]:
+    idx = list(np.nonzero(n <= 13)[0][:3]) + list(np.nonzero(n >= 30)[0][:1])
+    for i in idx:
         ref, _ = ap.approx_logprob(st.O, st.logdet, c.M, g.pattern_modes(pats[i]), 4)
         assert abs(res["logP"][i] - ref) < 1e-8, (i, n[i])
 

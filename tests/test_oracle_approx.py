@@ -101,6 +101,22 @@ def test_order_at_least_support_is_exact(eta):
         assert abs(lp - ex) < 1e-10
 
 
+def test_tilted_contour_keeps_exactness_for_improbable_patterns():
+    # weak squeezing, strong loss: all-clicked patterns are improbable and the
+    # contour radius moves into the upper sector tail; with n <= j + 1 the
+    # approximation must still be exact
+    M = 10
+    U = g.haar_unitary(M, 401)
+    r = g.squeezing(M, 10, 0.2, 0.4, 401)
+    for eta in (0.3, 0.9):
+        st = oracle.build_state(U, r, eta)
+        modes = [0, 1, 2, 3, 4]
+        ex = oracle.prob_exact(st, g.modes_to_pattern(modes)[None], dd=True)["logP"][0]
+        lp, info = ap.approx_logprob(st.O, st.logdet, M, modes, 4)
+        assert info["rho"] > 1.0
+        assert abs(lp - ex) < 1e-10
+
+
 def test_order_two_is_a_discrete_gaussian():
     # Methods, "Approximation method": the second-order scheme is a Gaussian
     # c0 exp(-(v - c1)^2 / (2 c2^2)) matching moments 0, 1, 2.
