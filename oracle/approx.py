@@ -27,6 +27,11 @@ Readings where the paper is silent (each listed in the design notes):
 * sector k >= 1 lives on v in [max(0, n-k), n-1]; sectors k < n add nothing;
 * the polynomial degree is min(j, |support| - 1), so the fit is exact when
   the support has at most j + 1 points;
+* "iteratively find parameters" is iterated to convergence of the parameters:
+  after the moment residual reaches 1e-13 one more full Newton step is taken
+  (the extrapolation to v = 0 is ill-conditioned, a residual alone leaves the
+  last point uncertain); a fallback to a lower order is reported only for a
+  sector carrying >= 1e-6 of the largest tilted mass;
 * x = v / n is the variable inside the Newton solve (conditioning only);
 * the paper's discrete set of nu is a circle |t| = rho: rho is the Chernoff
   saddle for sector n, rho = argmin over the radii RHOS at which I -+ rho O_S
@@ -48,6 +53,7 @@ import numpy as np
 
 TAIL_EPS = 1e-14
 EPS_SECTOR = 1e-12
+FLAG_SECTOR = 1e-6
 RHOS = (1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0)
 
 
@@ -165,13 +171,15 @@ def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter:
     for it in range(max_iter):
         q = np.exp(-X @ a)
         g = m - X.T @ q
-        if np.max(np.abs(g)) <= tol:
-            return a, True
         H = (X * q[:, None]).T @ X
         try:
             step = np.linalg.solve(H, g)
         except np.linalg.LinAlgError:
             return a, False
+        if np.max(np.abs(g)) <= tol:
+            # one last full Newton step: near the optimum it squares the error, so
+            # the parameters (and the extrapolated q(0)) converge, not only the moments
+            return a - step, True
         # gradient of phi is g; Newton direction -step; Armijo backtracking.
         # Near the optimum the decrease of phi is below its rounding, so a step
         # that halves the gradient is accepted as well.
@@ -231,7 +239,8 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
             continue
         val, fl = sector_last_point(D[:, k], n, k, j)
         parts[k] = val
-        flags = max(flags, fl)
+        if D[0, k] >= FLAG_SECTOR * D[0].max():      # fallbacks reported for sectors that matter
+            flags = max(flags, fl)
     # sum_k parts[k] rho^{-k}, in logs (rho^{-k} can leave the double range)
     nz = np.nonzero(parts > 0)[0]
     if nz.size:

@@ -32,6 +32,8 @@ constexpr int kFitThreads = 128;
 constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
 constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
+constexpr double kSectorEpsF32 = 1e-6;  // the same for FP32 minors (moments resolved to ~1e-7 K)
+constexpr double kFlagSector = 1e-6;    // fit fallbacks reported for sectors above this share
 constexpr int kNumRho = 8;
 __constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0};
 constexpr int kMaxK = 4095;
@@ -463,7 +465,6 @@ __device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
     for (int it = 0; it < 200; ++it) {
         double gmax = 0.0;
         for (int i = 0; i <= J; ++i) gmax = fmax(gmax, fabs(g[i]));
-        if (gmax <= 1e-13) return true;
         // Cholesky solve H step = g
         double Lc[(kMaxOrder + 1) * (kMaxOrder + 1)], st[kMaxOrder + 1];
         for (int i = 0; i <= J; ++i)
@@ -486,6 +487,11 @@ __device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
             double v = st[i];
             for (int q = i + 1; q <= J; ++q) v -= Lc[q * (kMaxOrder + 1) + i] * st[q];
             st[i] = v / Lc[i * (kMaxOrder + 1) + i];
+        }
+        if (gmax <= 1e-13) {
+            // a last full Newton step: the parameters converge, not only the moments
+            for (int i = 0; i <= J; ++i) a[i] -= st[i];
+            return true;
         }
         double gst = 0.0;
         for (int i = 0; i <= J; ++i) gst += g[i] * st[i];
@@ -515,7 +521,7 @@ __device__ __forceinline__ double stirling2(int i, int w) {
     return tab[i][w];
 }
 
-__global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int order,
+__global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int order, double sector_eps,
                                                                const double *__restrict__ logdet,
                                                                ApproxPlan pl, double *__restrict__ logP,
                                                                double *__restrict__ kappa,
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
         s_fallback = 0;
     }
     __syncthreads();
-    const double floor_ = kSectorEps * s_max;
+    const double floor_ = sector_eps * s_max;
     for (int k = t; k <= K; k += kFitThreads) {
         double val = 0.0;
         const double D0 = D[k];
@@ -588,10 +594,10 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
                 if (maxent_fit(v0, n, J, m, a)) {
                     val = mu[0] * exp(-a[0]);
                     done = true;
-                    if (J != Jmax) s_fallback = 1;
+                    if (J != Jmax && D0 >= kFlagSector * s_max) s_fallback = 1;
                 }
             }
-            if (!done) s_fallback = 1;
+            if (!done && D0 >= kFlagSector * s_max) s_fallback = 1;
         }
         part[k] = val;
     }
@@ -703,8 +709,8 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     const size_t fit_smem = sizeof(double) * (size_t)(kMaxOrder + 2) * (kMaxK + 1);
     GBS_CUDA(ctx, cudaFuncSetAttribute(approx_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fit_smem));
-    approx_fit_kernel<<<n_pat, kFitThreads, fit_smem, ctx->stream>>>(n_pat, order, logdet, pl, logP, kappa,
-                                                                    err_bound, status);
+    approx_fit_kernel<<<n_pat, kFitThreads, fit_smem, ctx->stream>>>(
+        n_pat, order, sizeof(R) == 8 ? kSectorEps : kSectorEpsF32, logdet, pl, logP, kappa, err_bound, status);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }
