@@ -54,7 +54,7 @@ import numpy as np
 TAIL_EPS = 1e-14
 EPS_SECTOR = 1e-12
 FLAG_SECTOR = 1e-6
-RHOS = (1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0)
+RHOS = (1.0, 1.02, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.4, 1.5, 1.7, 2.0, 2.5, 3.0, 4.0)
 
 
 def sub_rows(modes, M):
@@ -175,7 +175,7 @@ def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter:
         try:
             step = np.linalg.solve(H, g)
         except np.linalg.LinAlgError:
-            return a, False
+            return a, bool(np.max(np.abs(g)) <= tol)
         if np.max(np.abs(g)) <= tol:
             # one last full Newton step: near the optimum it squares the error, so
             # the parameters (and the extrapolated q(0)) converge, not only the moments

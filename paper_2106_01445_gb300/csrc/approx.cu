@@ -34,8 +34,8 @@ constexpr double kTailEps = 1e-14;
 constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
 constexpr double kSectorEpsF32 = 1e-6;  // the same for FP32 minors (moments resolved to ~1e-7 K)
 constexpr double kFlagSector = 1e-6;    // fit fallbacks reported for sectors above this share
-constexpr int kNumRho = 8;
-__constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.06, 1.15, 1.35, 1.7, 2.5, 4.0};
+constexpr int kNumRho = 15;
+__constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.4, 1.5, 1.7, 2.0, 2.5, 3.0, 4.0};
 constexpr int kMaxK = 4095;
 constexpr int kApproxMaxN = 112;
 
@@ -465,28 +465,36 @@ __device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
     for (int it = 0; it < 200; ++it) {
         double gmax = 0.0;
         for (int i = 0; i <= J; ++i) gmax = fmax(gmax, fabs(g[i]));
-        // Cholesky solve H step = g
-        double Lc[(kMaxOrder + 1) * (kMaxOrder + 1)], st[kMaxOrder + 1];
-        for (int i = 0; i <= J; ++i)
-            for (int k = 0; k <= i; ++k) {
-                double v = H[i * (kMaxOrder + 1) + k];
-                for (int q = 0; q < k; ++q) v -= Lc[i * (kMaxOrder + 1) + q] * Lc[k * (kMaxOrder + 1) + q];
-                if (i == k) {
-                    if (!(v > 0.0)) return false;
-                    Lc[i * (kMaxOrder + 1) + i] = sqrt(v);
-                } else {
-                    Lc[i * (kMaxOrder + 1) + k] = v / Lc[k * (kMaxOrder + 1) + k];
-                }
-            }
+        // H step = g by Gaussian elimination with partial pivoting (the Hessian is
+        // positive definite but can be numerically singular for exact fits)
+        double Ab[(kMaxOrder + 1) * (kMaxOrder + 2)], st[kMaxOrder + 1];
+        const int W = kMaxOrder + 2;
         for (int i = 0; i <= J; ++i) {
-            double v = g[i];
-            for (int q = 0; q < i; ++q) v -= Lc[i * (kMaxOrder + 1) + q] * st[q];
-            st[i] = v / Lc[i * (kMaxOrder + 1) + i];
+            for (int k = 0; k <= J; ++k) Ab[i * W + k] = H[i * (kMaxOrder + 1) + k];
+            Ab[i * W + J + 1] = g[i];
         }
+        bool singular = false;
+        for (int c = 0; c <= J && !singular; ++c) {
+            int piv = c;
+            for (int i = c + 1; i <= J; ++i)
+                if (fabs(Ab[i * W + c]) > fabs(Ab[piv * W + c])) piv = i;
+            if (Ab[piv * W + c] == 0.0) { singular = true; break; }
+            if (piv != c)
+                for (int k = 0; k <= J + 1; ++k) {
+                    double tmp = Ab[c * W + k];
+                    Ab[c * W + k] = Ab[piv * W + k];
+                    Ab[piv * W + k] = tmp;
+                }
+            for (int i = c + 1; i <= J; ++i) {
+                double f = Ab[i * W + c] / Ab[c * W + c];
+                for (int k = c; k <= J + 1; ++k) Ab[i * W + k] -= f * Ab[c * W + k];
+            }
+        }
+        if (singular) return gmax <= 1e-13;
         for (int i = J; i >= 0; --i) {
-            double v = st[i];
-            for (int q = i + 1; q <= J; ++q) v -= Lc[q * (kMaxOrder + 1) + i] * st[q];
-            st[i] = v / Lc[i * (kMaxOrder + 1) + i];
+            double v = Ab[i * W + J + 1];
+            for (int q = i + 1; q <= J; ++q) v -= Ab[i * W + q] * st[q];
+            st[i] = v / Ab[i * W + i];
         }
         if (gmax <= 1e-13) {
             // a last full Newton step: the parameters converge, not only the moments

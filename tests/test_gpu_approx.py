@@ -109,10 +109,13 @@ def test_m50_workload_sample(ctx):
     assert np.isin(res["status"], (0, 7)).all()
     assert np.isfinite(res["logP"]).all()
     st = oracle.build_state(U, r, c.eta)
+    # Patterns far above the mean click count draw P from sectors ~1e-10 below the
+    # largest tilted sector, which any FP64 extraction (the oracle's series or the
+    # GPU's Fourier sum) resolves only to ~1e-16 of the largest: parity 1e-5 there.
     idx = list(np.nonzero(n <= 13)[0][:3]) + list(np.nonzero(n >= 30)[0][:1])
     for i in idx:
         ref, _ = ap.approx_logprob(st.O, st.logdet, c.M, g.pattern_modes(pats[i]), 4)
-        assert abs(res["logP"][i] - ref) < 1e-8, (i, n[i])
+        assert abs(res["logP"][i] - ref) < (1e-8 if n[i] <= 13 else 1e-5), (i, n[i])
 
 
 def test_approx_invalid_patterns(ctx):
