@@ -30,8 +30,8 @@ Readings where the paper is silent (each listed in the design notes):
 * "iteratively find parameters" is iterated to convergence of the parameters:
   after the moment residual reaches 1e-13 one more full Newton step is taken
   (the extrapolation to v = 0 is ill-conditioned, a residual alone leaves the
-  last point uncertain); a fallback to a lower order is reported only for a
-  sector carrying >= 1e-6 of the largest tilted mass;
+  last point uncertain); a fallback to a lower order is reported only when the
+  sectors that fell back carry >= 1e-4 of the summed last points;
 * x = v / n is the variable inside the Newton solve (conditioning only);
 * the paper's discrete set of nu is a circle |t| = rho: rho is the Chernoff
   saddle for sector n, rho = argmin over the radii RHOS at which I -+ rho O_S
@@ -53,7 +53,7 @@ import numpy as np
 
 TAIL_EPS = 1e-14
 EPS_SECTOR = 1e-12
-FLAG_SECTOR = 1e-6
+FLAG_SHARE = 1e-4
 RHOS = (1.0, 1.02, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.4, 1.5, 1.7, 2.0, 2.5, 3.0, 4.0)
 
 
@@ -195,7 +195,10 @@ def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter:
                 break
             t *= 0.5
             if t < 1e-12:
-                return a, False
+                # no further decrease: the moments sit on the boundary of the moment
+                # cone (a support point of vanishing weight) up to their rounding;
+                # the fit stands if the residual is at that level
+                return a, bool(gmax <= 1e3 * tol)
         a, f = an, fn
     q = np.exp(-X @ a)
     return a, bool(np.max(np.abs(m - X.T @ q)) <= 1e3 * tol)
@@ -231,22 +234,26 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
     if K is None:
         K = choose_kmax(O, M, modes, rho)
     D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
-    flags = 0
     parts = np.zeros(K + 1)                                  # tilted last points
+    fell = np.zeros(K + 1, dtype=bool)
     floor = eps_sector * D[0].max()
     for k in range(K + 1):
         if D[0, k] < floor:
             continue
         val, fl = sector_last_point(D[:, k], n, k, j)
         parts[k] = val
-        if D[0, k] >= FLAG_SECTOR * D[0].max():      # fallbacks reported for sectors that matter
-            flags = max(flags, fl)
+        fell[k] = fl > 0
     # sum_k parts[k] rho^{-k}, in logs (rho^{-k} can leave the double range)
     nz = np.nonzero(parts > 0)[0]
+    flags = 0
     if nz.size:
         lg = np.log(parts[nz]) - nz * math.log(rho)
         top = lg.max()
-        logsum = top + math.log(np.exp(lg - top).sum())
+        w = np.exp(lg - top)
+        logsum = top + math.log(w.sum())
+        # a fallback is reported when the sectors that fell back carry >= FLAG_SHARE of the sum
+        if w[fell[nz]].sum() >= FLAG_SHARE * w.sum():
+            flags = 1
     else:
         logsum = -math.inf
     logP = -0.5 * logdet_sigmaQ + logsum

@@ -33,7 +33,7 @@ constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
 constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
 constexpr double kSectorEpsF32 = 1e-6;  // the same for FP32 minors (moments resolved to ~1e-7 K)
-constexpr double kFlagSector = 1e-6;    // fit fallbacks reported for sectors above this share
+constexpr double kFlagShare = 1e-4;     // fallback reported when such sectors carry this share of P
 constexpr int kNumRho = 15;
 __constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.4, 1.5, 1.7, 2.0, 2.5, 3.0, 4.0};
 constexpr int kMaxK = 4095;
@@ -512,7 +512,9 @@ __device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
             for (int i = 0; i <= J; ++i) gnmax = fmax(gnmax, fabs(gn[i]));
             if (isfinite(phin) && phin <= phi + 1e-14 * fabs(phi) && gnmax <= 0.5 * gmax) break;
             tstep *= 0.5;
-            if (tstep < 1e-12) return false;
+            // no further decrease: moments on the boundary of the moment cone up to
+            // their rounding; the fit stands if the residual is at that level
+            if (tstep < 1e-12) return gmax <= 1e-10;
         }
         for (int i = 0; i <= J; ++i) { a[i] = an[i]; g[i] = gn[i]; }
         for (int i = 0; i < (kMaxOrder + 1) * (kMaxOrder + 1); ++i) H[i] = Hn[i];
@@ -578,6 +580,7 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
     const double floor_ = sector_eps * s_max;
     for (int k = t; k <= K; k += kFitThreads) {
         double val = 0.0;
+        bool fell = false;
         const double D0 = D[k];
         if (n == 0) {
             val = (k == 0) ? D0 : 0.0;
@@ -602,12 +605,12 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
                 if (maxent_fit(v0, n, J, m, a)) {
                     val = mu[0] * exp(-a[0]);
                     done = true;
-                    if (J != Jmax && D0 >= kFlagSector * s_max) s_fallback = 1;
+                    if (J != Jmax) fell = true;
                 }
             }
-            if (!done && D0 >= kFlagSector * s_max) s_fallback = 1;
+            if (!done) fell = true;
         }
-        part[k] = val;
+        part[k] = fell ? -val : val;   // the sign marks a sector that fell back
     }
     __syncthreads();
     if (t == 0) {
@@ -615,10 +618,15 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
         const double lr = log(pl.pat_rho[p]);
         double top = -INFINITY;
         for (int k = 0; k <= K; ++k)
-            if (part[k] > 0.0) top = fmax(top, log(part[k]) - k * lr);
-        double s = 0.0;
+            if (part[k] != 0.0) top = fmax(top, log(fabs(part[k])) - k * lr);
+        double s = 0.0, sf = 0.0;
         for (int k = 0; k <= K; ++k)
-            if (part[k] > 0.0) s += exp(log(part[k]) - k * lr - top);
+            if (part[k] != 0.0) {
+                double w = exp(log(fabs(part[k])) - k * lr - top);
+                s += w;
+                if (part[k] < 0.0) sf += w;
+            }
+        s_fallback = sf >= kFlagShare * s;
         logP[p] = s > 0.0 ? -0.5 * (*logdet) + top + log(s) : -INFINITY;
         if (kappa) kappa[p] = (double)K;
         if (err_bound) err_bound[p] = nan("");
