@@ -9,7 +9,8 @@ imports, links or runs anything here, and nothing here uses the library.
   double-double variant for sums that cancel beyond FP64 precision.
 * ``approx.py``  -- the paper's moment approximation, step by step, with
   exact power series of every minor's generating function (numpy).
-* ``grad.py``    -- gradients of log P from the trace formula, per subset.
+* ``grad.py``    -- gradients of log P from the trace formula, per subset in
+  double-double (C), chained to (r, eta, U) and the mesh phases (numpy).
 """
 from __future__ import annotations
 
@@ -59,6 +60,7 @@ def lib():
                                          dp, ip, ctypes.c_int, ctypes.c_int]
             L.orc_subset_sum_dd.argtypes = L.orc_subset_sum.argtypes
             L.orc_subset_sum_dd_parallel.argtypes = L.orc_subset_sum_parallel.argtypes
+            L.orc_grad_subsets_dd.argtypes = [ctypes.c_int, dp, ip, ctypes.c_int, dp, dp, dp]
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
     return _lib

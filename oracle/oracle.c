@@ -298,6 +298,68 @@ int orc_subset_sum_dd_parallel(int M, const double *A, const int *modes, int n, 
     return bad ? ORC_NOT_SPD : ORC_OK;
 }
 
+/*
+ * Adjoint of the signed subset sum (the gradient path; not in the paper): with
+ * d det(A_Z)^{-1/2} = -1/2 det(A_Z)^{-1/2} tr(A_Z^{-1} dA_Z),
+ *     dT = tr(Gbar dA_S),  Gbar = sum_Z (-1)^{n-|Z|} (-1/2) tau_Z embed(A_Z^{-1}).
+ * Every subset Cholesky, inverse and the sums are double-double.  Rows of the
+ * 2n x 2n Gbar are (x, p) pairs of the modes of S in order: row 2a + alpha.
+ * Outputs: Gbar as hi and lo arrays (2n x 2n each), T as (hi, lo).
+ */
+int orc_grad_subsets_dd(int M, const double *A, const int *modes, int n, double *g_hi,
+                        double *g_lo, double *T) {
+    int N = 2 * M, D = 2 * n;
+    dd *G = calloc((size_t)D * D + 1, sizeof(dd));
+    dd *B = malloc(sizeof(dd) * (size_t)D * D + 1);
+    dd *Li = malloc(sizeof(dd) * (size_t)D * D + 1);
+    int *idx = malloc(sizeof(int) * (size_t)D + 1), *loc = malloc(sizeof(int) * (size_t)D + 1);
+    if (!G || !B || !Li || !idx || !loc) { free(G); free(B); free(Li); free(idx); free(loc); return ORC_INVALID; }
+    dd sum = {0.0, 0.0};
+    int status = ORC_OK;
+    for (uint64_t z = 0; z < ((uint64_t)1 << n); ++z) {
+        int k = 0;
+        for (int a = 0; a < n; ++a)
+            if (z >> a & 1) {
+                idx[2 * k] = modes[a]; idx[2 * k + 1] = modes[a] + M;
+                loc[2 * k] = 2 * a; loc[2 * k + 1] = 2 * a + 1;
+                ++k;
+            }
+        int d = 2 * k;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) B[i * d + j] = (dd){A[idx[i] * N + idx[j]], 0.0};
+        dd tau = {1.0, 0.0};
+        if (d) {
+            if (cholesky_dd(B, d)) { status = ORC_NOT_SPD; break; }
+            for (int i = 0; i < d; ++i) tau = dd_div(tau, B[i * d + i]);
+            /* Li = L^{-1} (lower triangular) */
+            for (int c = 0; c < d; ++c) {
+                for (int i = 0; i < c; ++i) Li[i * d + c] = (dd){0.0, 0.0};
+                Li[c * d + c] = dd_div((dd){1.0, 0.0}, B[c * d + c]);
+                for (int i = c + 1; i < d; ++i) {
+                    dd s2 = {0.0, 0.0};
+                    for (int m = c; m < i; ++m) s2 = dd_add(s2, dd_mul(B[i * d + m], Li[m * d + c]));
+                    Li[i * d + c] = dd_neg(dd_div(s2, B[i * d + i]));
+                }
+            }
+            /* (A_Z^{-1})_{ij} = sum_m Li_mi Li_mj, weighted into Gbar */
+            dd c0 = dd_mul(tau, (dd){((n - k) & 1) ? 0.5 : -0.5, 0.0});
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    dd s2 = {0.0, 0.0};
+                    int m0 = i > j ? i : j;
+                    for (int m = m0; m < d; ++m) s2 = dd_add(s2, dd_mul(Li[m * d + i], Li[m * d + j]));
+                    dd *gp = &G[loc[i] * D + loc[j]];
+                    *gp = dd_add(*gp, dd_mul(c0, s2));
+                }
+        }
+        sum = ((n - k) & 1) ? dd_sub(sum, tau) : dd_add(sum, tau);
+    }
+    for (int i = 0; i < D * D; ++i) { g_hi[i] = G[i].hi; g_lo[i] = G[i].lo; }
+    T[0] = sum.hi; T[1] = sum.lo;
+    free(G); free(B); free(Li); free(idx); free(loc);
+    return status;
+}
+
 static int pattern_modes(uint64_t lo, uint64_t hi, int M, int *modes) {
     int n = 0;
     for (int i = 0; i < M; ++i) {
