@@ -131,6 +131,38 @@ int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const double *logdet_
                      const uint64_t *patterns, int n_pat, int n_max, int precision, double *logP,
                      double *kappa, double *err_bound, int32_t *status);
 
+/* ---- gradients (not in the paper) ---------------------------------------
+ * L = sum_p w[p] log P(S_p) (exact probabilities, n <= 16 clicks per pattern).
+ * With A = sigma_Q^{-1}, dT = tr(Gbar dA_S), Gbar = sum_Z (-1)^{n-|Z|} (-1/2)
+ * det(A_Z)^{-1/2} A_Z^{-1} (the trace formula d det^{-1/2} = -1/2 det^{-1/2}
+ * tr(A^{-1} dA)), computed per subset in double-double because Gbar and T
+ * cancel alike:
+ *   dL/dsigma_Q = -1/2 (sum w) A - A H A,  H = sum_p (w_p / T_p) Gbar_p (embedded).
+ * w: n_pat doubles (device).  dsigmaQ: 2M x 2M out (device).  logP, status:
+ * optional per-pattern outputs (the double-double log P).  Synchronises once
+ * (pattern sizes are checked on the host); GBS_E_INVALID for a pattern with
+ * more than 16 clicks or a detector >= M. */
+int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+             const uint64_t *patterns, int n_pat, const double *w, double *dsigmaQ, double *logP,
+             int32_t *status);
+
+/* Chain to the state parameters of gbs_build_state: from dL/dsigma_Q (= dL/dsigma)
+ * to dU (M x M complex interleaved: dL/dRe U + i dL/dIm U), dr (M) and deta (one
+ * double), all on the device. */
+int gbs_grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
+                    const double *dsigmaQ, double *dU, double *dr, double *deta);
+
+/* Rectangular interferometer mesh (Clements et al., Optica 3, 1460 (2016)):
+ * U = T_{last} ... T_1, cell c acts on modes (m_c, m_c + 1) as
+ * [[e^{i phi} cos theta, -sin theta], [e^{i phi} sin theta, cos theta]]; layer
+ * l = 0..M-1 holds the pairs whose first mode has the parity of l.  theta, phi:
+ * M(M-1)/2 doubles each; U: M x M complex interleaved (device). */
+int gbs_clements_unitary(gbs_ctx *ctx, int M, const double *theta, const double *phi, double *U);
+/* Reverse pass through the mesh: dtheta, dphi from dU (same convention as
+ * gbs_grad_params) and the mesh's U. */
+int gbs_clements_grad(gbs_ctx *ctx, int M, const double *theta, const double *phi, const double *U,
+                      const double *dU, double *dtheta, double *dphi);
+
 /* ---- synthetic click patterns -------------------------------------------
  * Pattern i draws uint32 words w_0, w_1, ... from Philox4x32-10 (Salmon et al.,
  * SC'11) with key (seed mod 2^32, seed / 2^32) and counters (i, block, stream, 0);

@@ -33,6 +33,10 @@ SIGNATURES = {
     "gbs_run_host": (_i, [_vp, _i, _vp, _vp, _d, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_prob_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_gen_patterns": (_i, [_vp, _u64, _u32, _i, _i, _i, _i, _vp]),
+    "gbs_grad": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "gbs_grad_params": (_i, [_vp, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
+    "gbs_clements_unitary": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "gbs_clements_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gbs_peak_flops": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "gbs_timing_enable": (_i, [_vp, _i]),
     "gbs_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),

@@ -162,6 +162,45 @@ class Context:
         self._check(self.lib.gbs_build_state(self.h, Ud.shape[0], _ptr(Ud), _ptr(rd), float(eta), None,
                                              _ptr(O), _ptr(logdet), _ptr(status)))
 
+    def grad(self, O: torch.Tensor, logdet: torch.Tensor, patterns, w: torch.Tensor):
+        """dL/dsigma_Q for L = sum_p w_p log P_p; also the double-double log P and status."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        w = w.to(device=self.device, dtype=torch.float64).contiguous()
+        dsq = torch.empty_like(O)
+        logP = torch.empty(n_pat, dtype=torch.float64, device=self.device)
+        status = torch.empty(n_pat, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gbs_grad(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), n_pat, _ptr(w), _ptr(dsq),
+                                      _ptr(logP), _ptr(status)))
+        return dsq, logP, status
+
+    def grad_params(self, Ud: torch.Tensor, rd: torch.Tensor, eta: float, dsq: torch.Tensor):
+        """(dU interleaved (M, 2M), dr (M,), deta (1,)) from dL/dsigma_Q."""
+        M = Ud.shape[0]
+        dU = torch.empty_like(Ud)
+        dr = torch.empty_like(rd)
+        deta = torch.empty(1, dtype=torch.float64, device=self.device)
+        self._check(self.lib.gbs_grad_params(self.h, M, _ptr(Ud), _ptr(rd), float(eta), _ptr(dsq), _ptr(dU),
+                                             _ptr(dr), _ptr(deta)))
+        return dU, dr, deta
+
+    def clements_unitary(self, theta: torch.Tensor, phi: torch.Tensor, M: int) -> torch.Tensor:
+        """U (M, 2M) interleaved complex from the mesh phases (device)."""
+        U = torch.empty((M, 2 * M), dtype=torch.float64, device=self.device)
+        th = theta.to(device=self.device, dtype=torch.float64).contiguous()
+        ph = phi.to(device=self.device, dtype=torch.float64).contiguous()
+        self._check(self.lib.gbs_clements_unitary(self.h, M, _ptr(th), _ptr(ph), _ptr(U)))
+        return U
+
+    def clements_grad(self, theta, phi, Ud, dU):
+        th = theta.to(device=self.device, dtype=torch.float64).contiguous()
+        ph = phi.to(device=self.device, dtype=torch.float64).contiguous()
+        dth, dph = torch.empty_like(th), torch.empty_like(ph)
+        self._check(self.lib.gbs_clements_grad(self.h, Ud.shape[0], _ptr(th), _ptr(ph), _ptr(Ud), _ptr(dU),
+                                               _ptr(dth), _ptr(dph)))
+        return dth, dph
+
     def peak_flops(self, kind: str = "fp32") -> float:
         v = ctypes.c_double()
         self._check(self.lib.gbs_peak_flops(self.h, 0 if kind == "fp32" else 1, ctypes.byref(v)))
@@ -171,3 +210,34 @@ class Context:
 def patterns_numpy(t: torch.Tensor) -> np.ndarray:
     """(n, 2) uint64 numpy array from a device pattern tensor."""
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+class LogProbClements(torch.autograd.Function):
+    """log P of click patterns as a differentiable function of the squeezing r,
+    the transmission eta and the mesh phases (theta, phi).  Forward: mesh
+    unitary, state build and the exact double-double sweep in libgbs; backward:
+    the double-double adjoint (gbs_grad), the state-build chain (gbs_grad_params)
+    and the reverse pass through the mesh (gbs_clements_grad).
+
+        logP = LogProbClements.apply(r, eta, theta, phi, patterns, ctx)
+    """
+
+    @staticmethod
+    def forward(fctx, r, eta, theta, phi, patterns, gbs: Context):
+        M = r.shape[0]
+        Ud = gbs.clements_unitary(theta, phi, M)
+        rd = r.detach().to(device=gbs.device, dtype=torch.float64).contiguous()
+        st = gbs.build_state(torch.view_as_complex(Ud.view(M, M, 2)), rd, float(eta), check=False)
+        out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="dd")
+        fctx.save_for_backward(rd, theta.detach(), phi.detach(), Ud, st["O"], st["logdet"])
+        fctx.gbs, fctx.eta, fctx.patterns = gbs, float(eta), patterns
+        return out["logP"]
+
+    @staticmethod
+    def backward(fctx, grad_logP):
+        rd, theta, phi, Ud, O, logdet = fctx.saved_tensors
+        gbs = fctx.gbs
+        dsq, _, _ = gbs.grad(O, logdet, fctx.patterns, grad_logP.detach())
+        dU, dr, deta = gbs.grad_params(Ud, rd, fctx.eta, dsq)
+        dth, dph = gbs.clements_grad(theta, phi, Ud, dU)
+        return dr, deta[0], dth, dph, None, None

@@ -240,6 +240,42 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
     return GBS_OK;
 }
 
+int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+             const uint64_t *patterns, int n_pat, const double *w, double *dsigmaQ, double *logP,
+             int32_t *status) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 1 || !O || !logdet_sigmaQ || !patterns || !w || !dsigmaQ)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad: bad arguments (M=%d, n_pat=%d)", M, n_pat);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return grad_sigmaQ(ctx, M, O, logdet_sigmaQ, patterns, n_pat, w, dsigmaQ, logP, status);
+}
+
+int gbs_grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
+                    const double *dsigmaQ, double *dU, double *dr, double *deta) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || !U || !r || !dsigmaQ || !dU || !dr || !deta || !(eta > 0.0) || eta > 1.0)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad_params: bad arguments");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return grad_params(ctx, M, U, r, eta, dsigmaQ, dU, dr, deta);
+}
+
+int gbs_clements_unitary(gbs_ctx *ctx, int M, const double *theta, const double *phi, double *U) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 2 || M > 128 || !theta || !phi || !U)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_clements_unitary: bad arguments");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return clements_unitary(ctx, M, theta, phi, U);
+}
+
+int gbs_clements_grad(gbs_ctx *ctx, int M, const double *theta, const double *phi, const double *U,
+                      const double *dU, double *dtheta, double *dphi) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 2 || M > 128 || !theta || !phi || !U || !dU || !dtheta || !dphi)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_clements_grad: bad arguments");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return clements_grad(ctx, M, theta, phi, U, dU, dtheta, dphi);
+}
+
 int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_lo, int n_hi,
                      int n_pat, uint64_t *out) {
     if (!ctx) return GBS_E_INVALID;

@@ -69,4 +69,11 @@ long long sweep_units_upper_bound(int n_pat, int n_max, int precision);
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);
+int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
+                int n_pat, const double *w, double *dsq, double *logP, int32_t *status);
+int grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta, const double *dsq,
+                double *dU, double *dr, double *deta);
+int clements_unitary(gbs_ctx *ctx, int M, const double *theta, const double *phi, double *U);
+int clements_grad(gbs_ctx *ctx, int M, const double *theta, const double *phi, const double *U,
+                  const double *dU, double *dtheta, double *dphi);
 int peak_flops(gbs_ctx *ctx, int kind, double *flops);
