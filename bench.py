@@ -3,12 +3,16 @@
 One step = the whole exact path on one batch: state build (sigma, O, log det
 sigma_Q from U, r, eta) plus the signed subset sweep for every click pattern of
 the batch.  Default workload: 24 modes, 12 squeezed inputs r ~ U[0.6, 1.2],
-eta = 0.5, Haar U, 1024 patterns with n ~ U{12..20} clicks (2.4e8 subsets),
-FP32-determinant / compensated-sum split.  Metric: subset log-dets per second
-(whole job), plus patterns per second and the error against the FP64 oracle.
+eta = 0.5, Haar U, 1024 patterns with n ~ U{12..20} clicks (2.4e8 subsets).
+These uniformly drawn patterns are improbable and their signed sums cancel by
+kappa = 1e10..1e15, so the default precision is double-double (the only one
+that meets 1e-10 in log P here); FP64 and the FP32 split are timed alongside
+and their error against the double-double oracle is reported.  Metric: subset
+log-dets per second (whole job), plus patterns per second.
 
-    python bench.py [--gpus N --steps K --warmup W --precision fp32|fp64]
+    python bench.py [--gpus N --steps K --warmup W --precision dd|fp64|fp32]
     python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+    python bench.py --profile sweep|approx --precision ...   # one call, for ncu
 """
 from __future__ import annotations
 
@@ -29,6 +33,9 @@ sys.path.insert(0, ROOT)
 import gbs_inputs as g  # noqa: E402
 
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
+# (ncu captures summarised under profiles/); None where no capture of the current kernel exists
+DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None}
 UNIT = "subset logdets/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
@@ -268,21 +275,27 @@ def run_gpu(args):
             "gpu_launches": 4 * args.steps}
     if rank != 0:
         return 0
-    # roofline of the dominant kernel (the subset sweep): plain FP32/FP64 pipe, no tensor cores
+    # roofline of the dominant kernel (the subset sweep): plain FP32 / FP64 pipes, no
+    # tensor cores, no DRAM traffic to speak of.  FP32: algorithmic flops against
+    # SMs x 128 lanes x 2 x max clock.  FP64: against the measured FP64 FMA loop.
+    # Double-double: algorithmic flops against the FP64 peak divided by the FP64
+    # instructions one algorithmic flop costs in the error-free formulas
+    # (a multiply-subtract c - w b = 7 + 11 = 18 instructions for 2 flops: 9 per flop;
+    # the FMA loop's TFLOP/s count 2 flops per instruction, hence / (2 * 9)).
     props = torch.cuda.get_device_properties(dev)
     smax = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6
     meas = {"fp32": ctx.peak_flops("fp32"), "fp64": ctx.peak_flops("fp64")}
-    peak = fp32_peak if prec == "fp32" else meas["fp64"]
+    DD_INSTR_PER_FLOP = 9.0
+    peak = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["fp64"] / (2 * DD_INSTR_PER_FLOP)}[prec]
     achieved = flops / (sweep_ms / max(launches, 1) * 1e-3)
-    # double-double: one algorithmic flop costs ~20 FP64 pipe operations; the
-    # roofline is stated in algorithmic flops against the FP64 pipe peak
     line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get(prec),
                         "kernel": "sweep_kernel<%s>" % {"fp32": "float", "fp64": "double", "dd": "dd"}[prec],
                         "kernel_ms": sweep_ms / max(launches, 1), "flops_per_launch": flops,
-                        "peak_basis": ("SMs x 128 FP32 lanes x 2 x max SM clock" if prec == "fp32"
-                                       else "measured FP64 FMA loop"),
+                        "peak_basis": {"fp32": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
+                                       "fp64": "measured FP64 FMA loop",
+                                       "dd": "measured FP64 FMA loop / 18 (double-double cost per algorithmic flop)"}[prec],
                         "fma_loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
     line["other_precisions"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
                                 for k, v in others.items()}
@@ -325,10 +338,29 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """One warm-up and one measured call of a kernel path, for ncu captures."""
+    import torch
+    from paper_2106_01445_gb300 import build as b
+    b.build()
+    from paper_2106_01445_gb300.api import Context
+    c = g.CONFIGS[args.workload if args.profile == "sweep" else "m50_approx"]
+    ctx = Context(0)
+    st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
+    pats = c.patterns() if args.profile == "sweep" else c.patterns()[:args.npat]
+    order = 0 if args.profile == "sweep" else args.order
+    for _ in range(2):
+        out = ctx.prob(st["O"], st["logdet"], pats, order=order, precision=args.precision)
+    torch.cuda.synchronize()
+    print("profile case %s %s: %d patterns, %d ok" % (args.profile, args.precision, len(pats),
+                                                      int((out["status"] == 0).sum().item())))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="dd", choices=["fp32", "fp64", "dd"])
@@ -336,7 +368,13 @@ def main():
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--profile", choices=["sweep", "approx"], default=None,
+                    help="run one kernel path twice (for ncu) instead of the benchmark")
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--npat", type=int, default=128)
     args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
