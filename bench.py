@@ -35,7 +35,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": 115200.0, "dd": 350720.0, "fp64": None}
+DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None}
 UNIT = "subset logdets/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
@@ -279,14 +279,14 @@ def run_gpu(args):
     # tensor cores, no DRAM traffic to speak of.  FP32: algorithmic flops against
     # SMs x 128 lanes x 2 x max clock.  FP64: against the measured FP64 FMA loop.
     # Double-double: algorithmic flops against the FP64 peak divided by the FP64
-    # instructions one algorithmic flop costs in the error-free formulas
-    # (a multiply-subtract c - w b = 7 + 11 = 18 instructions for 2 flops: 9 per flop;
-    # the FMA loop's TFLOP/s count 2 flops per instruction, hence / (2 * 9)).
+    # instructions one algorithmic flop costs in the fused error-free formulas (the
+    # rank-2 update entry c - w0 b0 - w1 b1: 27 instructions for its 4 flops, 6.75 per
+    # flop; the FMA loop's TFLOP/s count 2 flops per instruction, hence / (2 * 6.75)).
     props = torch.cuda.get_device_properties(dev)
     smax = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6
     meas = {"fp32": ctx.peak_flops("fp32"), "fp64": ctx.peak_flops("fp64")}
-    DD_INSTR_PER_FLOP = 9.0
+    DD_INSTR_PER_FLOP = 27.0 / 4.0
     peak = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["fp64"] / (2 * DD_INSTR_PER_FLOP)}[prec]
     achieved = flops / (sweep_ms / max(launches, 1) * 1e-3)
     line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
@@ -295,7 +295,7 @@ def run_gpu(args):
                         "kernel_ms": sweep_ms / max(launches, 1), "flops_per_launch": flops,
                         "peak_basis": {"fp32": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
                                        "fp64": "measured FP64 FMA loop",
-                                       "dd": "measured FP64 FMA loop / 18 (double-double cost per algorithmic flop)"}[prec],
+                                       "dd": "measured FP64 FMA loop / 13.5 (fused double-double cost per algorithmic flop)"}[prec],
                         "fma_loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
     line["other_precisions"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
                                 for k, v in others.items()}

@@ -46,16 +46,19 @@ template <typename T> struct Prec;
 template <> struct Prec<float> {
     static constexpr int B = 6, idx = GBS_FP32_SPLIT;
     using Tau = double;
+    using Abs = float;
     static constexpr double u = 5.9604644775390625e-08, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<double> {
     static constexpr int B = 4, idx = GBS_FP64;
     using Tau = double;
+    using Abs = double;
     static constexpr double u = 1.1102230246251565e-16, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<dd> {
     static constexpr int B = 3, idx = GBS_DD;
     using Tau = dd;
+    using Abs = double;
     static constexpr double u = 1.2325951644078309e-32, u_sum = 1.2325951644078309e-32;
 };
 
@@ -69,6 +72,13 @@ __device__ __forceinline__ double rsq_tau(float x) { return rsqrt((double)x); }
 __device__ __forceinline__ double rsq_tau(double x) { return rsqrt(x); }
 __device__ __forceinline__ dd rsq_tau(dd x) { return dd_rsqrt(x); }
 
+// the Schur-update kernels: a0 b0 + a1 b1, c - a0 b0 - a1 b1, det of a 2x2 block
+template <typename T> __device__ __forceinline__ T dot2(T a0, T b0, T a1, T b1) { return a0 * b0 + a1 * b1; }
+template <> __device__ __forceinline__ dd dot2<dd>(dd a0, dd b0, dd a1, dd b1) { return dd_dot2(a0, b0, a1, b1); }
+template <typename T> __device__ __forceinline__ T fms2(T c, T a0, T b0, T a1, T b1) { return c - a0 * b0 - a1 * b1; }
+template <> __device__ __forceinline__ dd fms2<dd>(dd c, dd a0, dd b0, dd a1, dd b1) { return dd_fms2(c, a0, b0, a1, b1); }
+template <typename T> __device__ __forceinline__ T det2(T p00, T p01, T p11) { return dot2(p00, p11, -p01, p01); }
+
 // an entry of A = I - O from its FP64 data (exact in double-double)
 template <typename T> __device__ __forceinline__ T a_entry(double delta, double o) { return (T)(delta - o); }
 template <> __device__ __forceinline__ dd a_entry<dd>(double delta, double o) { return dd_two_sum(delta, -o); }
@@ -76,6 +86,10 @@ template <> __device__ __forceinline__ dd a_entry<dd>(double delta, double o) { 
 __device__ __forceinline__ double to_hi(float x) { return x; }
 __device__ __forceinline__ double to_hi(double x) { return x; }
 __device__ __forceinline__ double to_hi(dd x) { return x.hi; }
+// leading part of a (positive) term, in the type its magnitude is summed in
+__device__ __forceinline__ float abs_part(float x) { return x; }
+__device__ __forceinline__ double abs_part(double x) { return x; }
+__device__ __forceinline__ double abs_part(dd x) { return x.hi; }
 __device__ __forceinline__ double to_lo(float) { return 0.0; }
 __device__ __forceinline__ double to_lo(double) { return 0.0; }
 __device__ __forceinline__ double to_lo(dd x) { return x.lo; }
@@ -84,6 +98,10 @@ __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 
 // ---- shared-memory layout ----------------------------------------------------
+// X and Y alternate as source and destination of the breadth-first levels; the
+// unit's prefix-elimination matrix (up to 2 kMaxN rows) spans both before the
+// levels start.  Ub holds the unit's trailing block, W the rows W = B P^{-1} of the
+// level (or prefix pivot) being eliminated, Q the inverse pivots of a level's parents.
 template <typename T> struct Layout {
     static constexpr int B = Prec<T>::B;
     static constexpr int R = kL + B;  // modes of a unit's level-0 matrix
@@ -94,8 +112,16 @@ template <typename T> struct Layout {
         return m;
     }
     static constexpr int max_odd() {
-        int m = sym(2 * kMaxN);  // prefix-elimination matrix lives here first
+        int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots
         for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
+        return m;
+    }
+    static constexpr int w_entries() {
+        int m = 2 * (2 * kMaxN);
+        for (int l = 0; l < kL; ++l) {
+            const int v = (1 << l) * 2 * (2 * (R - l - 1));
+            m = v > m ? v : m;
+        }
         return m;
     }
     static constexpr int dec_entries() {
@@ -108,7 +134,9 @@ template <typename T> struct Layout {
     static constexpr size_t off_Y = off_X + sizeof(T) * max_even();
     static constexpr int ublk() { return sym(2 * (kS + R)); }
     static constexpr size_t off_U = off_Y + sizeof(T) * max_odd();
-    static constexpr size_t off_tauX = off_U + sizeof(T) * ublk();
+    static constexpr size_t off_W = off_U + sizeof(T) * ublk();
+    static constexpr size_t off_Q = off_W + sizeof(T) * w_entries();
+    static constexpr size_t off_tauX = off_Q + sizeof(T) * 3 * (kThreads / 2);
     static constexpr size_t off_tauY = off_tauX + sizeof(T) * kThreads;
     static constexpr size_t off_red = off_tauY + sizeof(T) * kThreads;      // 3 doubles per warp
     static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
@@ -116,6 +144,7 @@ template <typename T> struct Layout {
     static constexpr size_t off_decoff = off_pos + sizeof(int) * 2 * kMaxN;
     static constexpr size_t off_dec = off_decoff + sizeof(int) * (R + 2);
     static constexpr size_t bytes = (off_dec + sizeof(uint16_t) * dec_entries() + 15) / 16 * 16;
+    static_assert(sizeof(T) * sym(2 * kMaxN) <= off_U, "prefix matrix must fit in X and Y");
 };
 
 // ---- error-free accumulation ----------------------------------------------------
@@ -126,7 +155,8 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 }
 
 template <typename T> struct Acc {
-    T hi, lo, abs;
+    T hi, lo;
+    typename Prec<T>::Abs abs;  // sum of |terms|, for kappa only
 };
 
 template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
@@ -185,7 +215,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
     constexpr int m = MD - O;
     constexpr int o = 2 * O;
     const T p00 = A(o, o), p01 = A(o, o + 1), p11 = A(o + 1, o + 1);
-    const T det = p00 * p11 - p01 * p01;
+    const T det = det2(p00, p01, p11);
     const T rs = rsq<T>(det);
     const bool real = depth < nreal;
     if constexpr (m == 1) {
@@ -193,7 +223,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
         const T inc = tau * rs;
         T comb = real ? inc - tau : inc;
         acc_add(acc, NEG ? -comb : comb);
-        acc.abs += real ? inc + tau : inc;
+        acc.abs += real ? abs_part(inc) + abs_part(tau) : abs_part(inc);
     } else {
         constexpr int d = 2 * (m - 1);
         const T inv = rs * rs;
@@ -203,15 +233,15 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
         for (int i = 0; i < d; ++i) {
             b0[i] = A(o, o + 2 + i);
             b1[i] = A(o + 1, o + 2 + i);
-            w0[i] = q00 * b0[i] + q01 * b1[i];
-            w1[i] = q01 * b0[i] + q11 * b1[i];
+            w0[i] = dot2(q00, b0[i], q01, b1[i]);
+            w1[i] = dot2(q01, b0[i], q11, b1[i]);
         }
         RegMat<T, m - 1> C;
 #pragma unroll
         for (int i = 0; i < d; ++i)
 #pragma unroll
             for (int j = i; j < d; ++j)
-                C.v[pidx(d, i, j)] = A(o + 2 + i, o + 2 + j) - w0[i] * b0[j] - w1[i] * b1[j];
+                C.v[pidx(d, i, j)] = fms2(A(o + 2 + i, o + 2 + j), w0[i], b0[j], w1[i], b1[j]);
         dfs<T, m - 1, 0, NEG>(C, tau * rs, depth + 1, nreal, acc);
         if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc);
     }
@@ -309,6 +339,48 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
     }
 }
 
+// ---- one 2x2 block pivot eliminated by the whole CTA ---------------------------------
+// Mx: packed D x D matrix (D even); the pivot block sits on rows c0, c0 + 1.  Rows and
+// columns >= c0 + 2 receive C - W B^T, W = B P^{-1} (its rows staged in Wb first).
+// Returns 1/sqrt(det P) in the prefix type; a non-positive det sets *flag.
+template <typename T>
+__device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0, T *Wb, int *flag) {
+    const int t = threadIdx.x;
+    const T p00 = Mx[pidx(D, c0, c0)], p01 = Mx[pidx(D, c0, c0 + 1)], p11 = Mx[pidx(D, c0 + 1, c0 + 1)];
+    const T det = det2(p00, p01, p11);
+    if (t == 0 && !(det > T(0))) *flag = 1;
+    const int Dt = D - c0 - 2;
+    if (t < Dt) {
+        const T rs = rsq<T>(det);
+        const T inv = rs * rs;
+        const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+        for (int i = t; i < Dt; i += kThreads) {
+            const T b0 = Mx[pidx(D, c0, c0 + 2 + i)], b1 = Mx[pidx(D, c0 + 1, c0 + 2 + i)];
+            Wb[2 * i] = dot2(q00, b0, q01, b1);
+            Wb[2 * i + 1] = dot2(q01, b0, q11, b1);
+        }
+    }
+    const typename Prec<T>::Tau rt = rsq_tau(det);
+    __syncthreads();
+    // the trailing triangle, rows p and Dt - 1 - p folded into one run of Dt + 1 entries
+    const int w = Dt + 1, E = (Dt >> 1) * w;
+    for (int f = t; f < E; f += kThreads) {
+        const int p = f / w, k = f - p * w;
+        int i, j;
+        if (k < Dt - p) {
+            i = p;
+            j = p + k;
+        } else {
+            i = Dt - 1 - p;
+            j = i + (k - (Dt - p));
+        }
+        T &c = Mx[pidx(D, c0 + 2 + i, c0 + 2 + j)];
+        c = fms2(c, Wb[2 * i], Mx[pidx(D, c0, c0 + 2 + j)], Wb[2 * i + 1], Mx[pidx(D, c0 + 1, c0 + 2 + j)]);
+    }
+    __syncthreads();
+    return rt;
+}
+
 // ---- the sweep ------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__restrict__ O,
@@ -329,6 +401,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
     T *Ub = (T *)(smem + Lay::off_U);
+    T *Wb = (T *)(smem + Lay::off_W);
+    T *Qb = (T *)(smem + Lay::off_Q);
     using Tau = typename Prec<T>::Tau;
     __shared__ Tau s_tpre;
 
@@ -392,8 +466,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         __syncthreads();
         const int k = s_k;
         const int D0 = 2 * (k + rp);
-        // gather G = (I - O) on those rows into Y (packed), padding modes as identity;
-        // every thread takes entries of the whole matrix (independent loads in flight)
+        // gather G = (I - O) on those rows into X (packed; the prefix matrix spans X and Y),
+        // padding modes as identity; every thread takes entries of the whole matrix
         for (int f = t; f < D0 * D0; f += kThreads) {
             const int i = f / D0, j = f - i * D0;
             if (j < i) continue;
@@ -403,37 +477,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 v = (i == j) ? T(1) : T(0);
             } else {
                 const int si = modes[a] + (i & 1) * M, sj = modes[b] + (j & 1) * M;
-                    v = a_entry<T>(i == j ? 1.0 : 0.0, O[(size_t)si * N2 + sj]);
+                v = a_entry<T>(i == j ? 1.0 : 0.0, O[(size_t)si * N2 + sj]);
             }
-            Y[pidx(D0, i, j)] = v;
+            X[pidx(D0, i, j)] = v;
         }
         __syncthreads();
         // eliminate the included prefix modes (2x2 block pivots)
         Tau tpre = Tau(1.0);
-        for (int e = 0; e < k; ++e) {
-            const int c0 = 2 * e, Dt = D0 - c0 - 2;
-            const T p00 = Y[pidx(D0, c0, c0)], p01 = Y[pidx(D0, c0, c0 + 1)],
-                    p11 = Y[pidx(D0, c0 + 1, c0 + 1)];
-            const T det = p00 * p11 - p01 * p01;
-            if (!(det > T(0))) s_flag = 1;
-            tpre = tpre * rsq_tau(det);
-            const T inv = T(1) / det;
-            const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-            for (int f = t; f < Dt * Dt; f += kThreads) {
-                const int i = c0 + 2 + f / Dt, j = c0 + 2 + f % Dt;
-                if (j < i) continue;
-                const T bi0 = Y[pidx(D0, c0, i)], bi1 = Y[pidx(D0, c0 + 1, i)];
-                const T bj0 = Y[pidx(D0, c0, j)], bj1 = Y[pidx(D0, c0 + 1, j)];
-                Y[pidx(D0, i, j)] -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
-            }
-            __syncthreads();
-        }
+        for (int e = 0; e < k; ++e) tpre = tpre * elim_pivot<T>(X, D0, 2 * e, Wb, &s_flag);
         // the unit's trailing 2rp x 2rp block -> Ublk
         {
             const int d = 2 * rp, o = 2 * k;
             for (int f = t; f < d * d; f += kThreads) {
                 const int i = f / d, j = f - i * d;
-                if (j >= i) Ub[pidx(d, i, j)] = Y[pidx(D0, o + i, o + j)];
+                if (j >= i) Ub[pidx(d, i, j)] = X[pidx(D0, o + i, o + j)];
             }
         }
         __syncthreads();
@@ -465,24 +522,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             }
             __syncthreads();
             Tau tsub = Tau(1.0);
-            for (int e = 0; e < kk; ++e) {
-                const int c0 = 2 * e, Dt = Ds - c0 - 2;
-                const T p00 = Y[pidx(Ds, c0, c0)], p01 = Y[pidx(Ds, c0, c0 + 1)],
-                        p11 = Y[pidx(Ds, c0 + 1, c0 + 1)];
-                const T det = p00 * p11 - p01 * p01;
-                if (!(det > T(0))) s_flag = 1;
-                tsub = tsub * rsq_tau(det);
-                const T inv = T(1) / det;
-                const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-                for (int f = t; f < Dt * Dt; f += kThreads) {
-                    const int i = c0 + 2 + f / Dt, j = c0 + 2 + f % Dt;
-                    if (j < i) continue;
-                    const T bi0 = Y[pidx(Ds, c0, i)], bi1 = Y[pidx(Ds, c0 + 1, i)];
-                    const T bj0 = Y[pidx(Ds, c0, j)], bj1 = Y[pidx(Ds, c0 + 1, j)];
-                    Y[pidx(Ds, i, j)] -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
-                }
-                __syncthreads();
-            }
+            for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Wb, &s_flag);
             // level 0 of the expansion: the trailing 2r x 2r block, packed into X
             {
                 const int d = 2 * r, o = 2 * kk;
@@ -493,7 +533,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 if (t == 0) tauX[0] = T(1);
             }
             __syncthreads();
-            // breadth-first expansion of L_eff levels
+            // breadth-first expansion of L_eff levels: node c at level l + 1 is child
+            // c & 1 (0 exclude, 1 include) of parent c >> 1
             for (int l = 0; l < L_eff; ++l) {
                 const T *src = (l & 1) ? Y : X;
                 T *dst = (l & 1) ? X : Y;
@@ -501,32 +542,51 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 T *tdst = (l & 1) ? tauX : tauY;
                 const int d = 2 * (r - l), dc = d - 2;
                 const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
-                const int lg_tpc = kL - (l + 1);
-                const int c = t >> lg_tpc, sb = t & ((1 << lg_tpc) - 1);
-                const int parent = c >> 1;
-                const bool inc = c & 1;
-                const T *P = src + parent * sstr;
-                T *Cd = dst + c * dstr;
-                const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
-                const T det = p00 * p11 - p01 * p01;
-                const T rs = rsq<T>(det);
-                const T inv = rs * rs;
-                const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-                const uint16_t *dd = dec + decoff[dc >> 1];
-                for (int e = sb; e < Ec; e += (1 << lg_tpc)) {
-                    const int ij = dd[e];
-                    const int i = ij & 0xff, j = ij >> 8;
-                    T v = P[pidx(d, i + 2, j + 2)];
-                    if (inc) {
-                        const T bi0 = P[pidx(d, 0, i + 2)], bi1 = P[pidx(d, 1, i + 2)];
-                        const T bj0 = P[pidx(d, 0, j + 2)], bj1 = P[pidx(d, 1, j + 2)];
-                        v -= (q00 * bi0 + q01 * bi1) * bj0 + (q01 * bi0 + q11 * bi1) * bj1;
-                    }
-                    Cd[e] = v;
-                }
-                if (sb == 0) {
-                    tdst[c] = inc ? tsrc[parent] * rs : tsrc[parent];
+                const int np = 1 << l;
+                // (a) the parents' inverse pivots and the children's prefactors
+                if (t < np) {
+                    const T *P = src + t * sstr;
+                    const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
+                    const T det = det2(p00, p01, p11);
+                    const T rs = rsq<T>(det);
+                    const T inv = rs * rs;
+                    Qb[3 * t] = p11 * inv;
+                    Qb[3 * t + 1] = -p01 * inv;
+                    Qb[3 * t + 2] = p00 * inv;
+                    tdst[2 * t] = tsrc[t];
+                    tdst[2 * t + 1] = tsrc[t] * rs;
                     if (!(det > T(0))) s_flag = 1;
+                }
+                __syncthreads();
+                // (b) W = B P^{-1} for every parent, dc rows each
+                for (int f = t; f < np * dc; f += kThreads) {
+                    const int cp = f / dc, i = f - cp * dc;
+                    const T *P = src + cp * sstr;
+                    const T b0 = P[pidx(d, 0, i + 2)], b1 = P[pidx(d, 1, i + 2)];
+                    const T q00 = Qb[3 * cp], q01 = Qb[3 * cp + 1], q11 = Qb[3 * cp + 2];
+                    Wb[2 * f] = dot2(q00, b0, q01, b1);
+                    Wb[2 * f + 1] = dot2(q01, b0, q11, b1);
+                }
+                __syncthreads();
+                // (c) both children of every parent: the exclude child is the parent's
+                // trailing block, the include child its Schur complement
+                const uint16_t *dtab = dec + decoff[dc >> 1];
+                const int qstep = kThreads / Ec, rstep = kThreads - qstep * Ec;
+                int cp = t / Ec, e = t - cp * Ec;
+                for (int f = t; f < np * Ec; f += kThreads) {
+                    const int ij = dtab[e];
+                    const int i = ij & 0xff, j = ij >> 8;
+                    const T *P = src + cp * sstr;
+                    const T *Wr = Wb + 2 * (cp * dc + i);
+                    const T v = P[pidx(d, i + 2, j + 2)];
+                    dst[(2 * cp) * dstr + e] = v;
+                    dst[(2 * cp + 1) * dstr + e] = fms2(v, Wr[0], P[pidx(d, 0, j + 2)], Wr[1], P[pidx(d, 1, j + 2)]);
+                    e += rstep;
+                    cp += qstep;
+                    if (e >= Ec) {
+                        e -= Ec;
+                        ++cp;
+                    }
                 }
                 __syncthreads();
             }
@@ -535,7 +595,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
                 const T tau_node = ((L_eff & 1) ? tauY : tauX)[t];
                 const int nreal = n - (n_eff - B);
-                Acc<T> acc{T(0), T(0), T(0)};
+                Acc<T> acc{T(0), T(0), 0};
                 SmemMat<T, B> A{node};
                 dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
                 const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
