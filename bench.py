@@ -5,12 +5,13 @@ sigma_Q from U, r, eta) plus the signed subset sweep for every click pattern of
 the batch.  Default workload: 24 modes, 12 squeezed inputs r ~ U[0.6, 1.2],
 eta = 0.5, Haar U, 1024 patterns with n ~ U{12..20} clicks (2.4e8 subsets).
 These uniformly drawn patterns are improbable and their signed sums cancel by
-kappa = 1e10..1e15, so the default precision is double-double (the only one
-that meets 1e-10 in log P here); FP64 and the FP32 split are timed alongside
-and their error against the double-double oracle is reported.  Metric: subset
-log-dets per second (whole job), plus patterns per second.
+kappa = 1e10..1e15, so the default precision is the 128-bit fixed-point sweep
+(accuracy of double-double, the other precision that meets 1e-10 in log P here,
+on the integer pipes); double-double, FP64 and the FP32 split are timed
+alongside and the error of each against the double-double oracle is reported.
+Metric: subset log-dets per second (whole job), plus patterns per second.
 
-    python bench.py [--gpus N --steps K --warmup W --precision dd|fp64|fp32]
+    python bench.py [--gpus N --steps K --warmup W --precision fx|dd|fp64|fp32]
     python bench.py --impl reference     # the FP64 CPU oracle on the host cores
     python bench.py --profile sweep|approx --precision ...   # one call, for ncu
 """
@@ -35,7 +36,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None}
+DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None, "fx": None}
 UNIT = "subset logdets/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
@@ -244,7 +245,7 @@ def run_gpu(args):
     ms, sweep_ms, launches, ck = timed(prec, args.steps, args.warmup, clocks)
     # the other precisions, for the comparison (shorter runs)
     others = {}
-    for other in ("dd", "fp64", "fp32"):
+    for other in ("fx", "dd", "fp64", "fp32"):
         if other == prec:
             continue
         Ko = max(3, args.steps // 20)
@@ -265,7 +266,7 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "dd": "f64x2"}[prec],
+            "dtype": {"fp32": "f32", "fp64": "f64", "dd": "f64x2", "fx": "i128"}[prec],
             "data": "synthetic",
             "config": {"workload": c.name, "M": c.M, "squeezed": c.K, "r": [c.r_lo, c.r_hi], "eta": c.eta,
                        "interferometer": c.interferometer, "n_pat": len(pats), "clicks": [c.n_lo, c.n_hi],
@@ -275,28 +276,27 @@ def run_gpu(args):
             "gpu_launches": 4 * args.steps}
     if rank != 0:
         return 0
-    # roofline of the dominant kernel (the subset sweep): plain FP32 / FP64 pipes, no
-    # tensor cores, no DRAM traffic to speak of.  FP32: algorithmic flops against
-    # SMs x 128 lanes x 2 x max clock.  FP64: against the measured FP64 FMA loop.
-    # Double-double: algorithmic flops against the FP64 peak divided by the FP64
-    # instructions one algorithmic flop costs in the fused error-free formulas (the
-    # rank-2 update entry c - w0 b0 - w1 b1: 27 instructions for its 4 flops, 6.75 per
-    # flop; the FMA loop's TFLOP/s count 2 flops per instruction, hence / (2 * 6.75)).
+    # roofline of the dominant kernel (the subset sweep): plain ALU pipes, no tensor
+    # cores, no DRAM traffic to speak of.  FP32: algorithmic flops against SMs x 128
+    # lanes x 2 x max clock.  FP64: against the measured FP64 FMA loop.  Double-double
+    # and fixed point: against the measured loop of the fused rank-2 update entry
+    # c - w0 b0 - w1 b1 in that arithmetic (4 flops per entry), i.e. the rate the
+    # sweep would reach if every algorithmic flop cost what its main update costs.
     props = torch.cuda.get_device_properties(dev)
     smax = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6
-    meas = {"fp32": ctx.peak_flops("fp32"), "fp64": ctx.peak_flops("fp64")}
-    DD_INSTR_PER_FLOP = 27.0 / 4.0
-    peak = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["fp64"] / (2 * DD_INSTR_PER_FLOP)}[prec]
+    meas = {k: ctx.peak_flops(k) for k in ("fp32", "fp64", "dd", "fx")}
+    peak = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["dd"], "fx": meas["fx"]}[prec]
     achieved = flops / (sweep_ms / max(launches, 1) * 1e-3)
     line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get(prec),
-                        "kernel": "sweep_kernel<%s>" % {"fp32": "float", "fp64": "double", "dd": "dd"}[prec],
+                        "kernel": "sweep_kernel<%s>" % {"fp32": "float", "fp64": "double", "dd": "dd", "fx": "fx"}[prec],
                         "kernel_ms": sweep_ms / max(launches, 1), "flops_per_launch": flops,
                         "peak_basis": {"fp32": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
                                        "fp64": "measured FP64 FMA loop",
-                                       "dd": "measured FP64 FMA loop / 13.5 (fused double-double cost per algorithmic flop)"}[prec],
-                        "fma_loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
+                                       "dd": "measured double-double update-entry loop (4 flops per entry)",
+                                       "fx": "measured fixed-point update-entry loop (4 flops per entry)"}[prec],
+                        "loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
     line["other_precisions"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
                                 for k, v in others.items()}
     line["clocks"] = ck
@@ -363,7 +363,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="dd", choices=["fp32", "fp64", "dd"])
+    ap.add_argument("--precision", default="fx", choices=["fp32", "fp64", "dd", "fx"])
     ap.add_argument("--dd-sample", type=int, default=24)
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")

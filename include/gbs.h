@@ -40,14 +40,21 @@ typedef enum {
     GBS_E_NONPOSITIVE = 4, /* signed sum T <= its error bound: log P undefined */
     GBS_E_NOT_SPD = 5,     /* a pivot of an SPD factorisation was not positive */
     GBS_E_TIMEOUT = 6,     /* a bounded device loop ran out of iterations */
-    GBS_E_FIT = 7          /* approximation: a sector fit fell back to a lower order */
+    GBS_E_FIT = 7,         /* approximation: a sector fit fell back to a lower order */
+    GBS_E_RANGE = 8        /* GBS_FX: a pivot determinant below 2^-8 or an entry of O beyond
+                              4 left the fixed-point range (evaluate in GBS_DD instead) */
 } gbs_status;
 
 typedef enum {
     GBS_FP64 = 0,        /* every factorisation and sum in FP64 */
     GBS_FP32_SPLIT = 1,  /* subset factorisations in FP32; signed sum compensated, FP64 result */
-    GBS_DD = 2           /* double-double (~106-bit) factorisations and sum, on the FP64 pipes:
+    GBS_DD = 2,          /* double-double (~106-bit) factorisations and sum, on the FP64 pipes:
                             for patterns whose signed sum cancels beyond FP64 (kappa u64 >~ 1e-10) */
+    GBS_FX = 3           /* exact sum only: 128-bit fixed-point (Q16.112) factorisations on the
+                            integer pipes, double-double prefactors and sum; accuracy as GBS_DD
+                            (~2^-100 per term) at a fraction of its cost.  Needs every pivot
+                            determinant of the Schur recursion >= 2^-8 (true when the largest
+                            eigenvalue of sigma_Q is below 16); else GBS_E_RANGE */
 } gbs_precision;
 
 /* ---- context ------------------------------------------------------------ */
@@ -91,7 +98,8 @@ int gbs_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, doubl
  *   sector tables of the minors removing <= j detectors at t = e^{i nu} (nu on
  *   L points, L - 1 a bound on the sector index with tail < 1e-14), inverse
  *   DFT, per-sector maximum-entropy fit of moments 0..j, sum of the all-clicked
- *   points.  precision GBS_FP64 (n <= 79) or GBS_FP32_SPLIT (FP32 complex
+ *   points.  Order 0 takes every precision; order > 0 takes
+ *   precision GBS_FP64 (n <= 79) or GBS_FP32_SPLIT (FP32 complex
  *   minors, FP64 sums and fits; n <= 112).  For order > 0, kappa returns the
  *   sector bound K, err_bound is NaN, and status GBS_E_FIT marks a pattern where
  *   some sector fit fell back to a lower order (logP is still returned).
@@ -182,9 +190,12 @@ int gbs_timing_enable(gbs_ctx *ctx, int enable);
 int gbs_timing_read(gbs_ctx *ctx, int reset, double *sweep_ms, long long *sweep_launches);
 
 /*
- * Peak arithmetic throughput of this GPU's FP32 (kind 0) and FP64 (kind 1) FMA
- * pipes from a register-resident dependent-FMA loop; result in FLOP/s (one FMA
- * = 2 FLOP) at the clocks of the run.  Synchronous. */
+ * Peak arithmetic throughput of this GPU at the clocks of the run, in FLOP/s.
+ * kind 0 / 1: the FP32 / FP64 FMA pipes from a register-resident dependent-FMA
+ * loop (one FMA = 2 FLOP).  kind 2 / 3: the fused Schur-update entry
+ * c - w0 b0 - w1 b1 (4 FLOP) in double-double / in 128-bit fixed point, from a
+ * loop of independent entries: the ceiling of the sweep in those precisions.
+ * Synchronous.  The scratch buffer it writes is the context's own. */
 int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops);
 
 #ifdef __cplusplus

@@ -11,10 +11,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX
 
-PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, GBS_FP64: GBS_FP64,
-              GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD}
+PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, "fx": GBS_FX, GBS_FP64: GBS_FP64,
+              GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX}
 
 
 def _ptr(t) -> ctypes.c_void_p:
@@ -202,8 +202,11 @@ class Context:
         return dth, dph
 
     def peak_flops(self, kind: str = "fp32") -> float:
+        """FLOP/s of the FP32 / FP64 FMA loops ("fp32", "fp64") or of the fused
+        Schur-update loops in double-double / fixed point ("dd", "fx")."""
         v = ctypes.c_double()
-        self._check(self.lib.gbs_peak_flops(self.h, 0 if kind == "fp32" else 1, ctypes.byref(v)))
+        code = {"fp32": 0, "fp64": 1, "dd": 2, "fx": 3}[kind]
+        self._check(self.lib.gbs_peak_flops(self.h, code, ctypes.byref(v)))
         return v.value
 
 

@@ -171,7 +171,7 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
     if (!ctx) return GBS_E_INVALID;
     if (M < 1 || M > 128 || n_pat < 0 || !O || !logdet_sigmaQ || (n_pat && (!patterns || !logP)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: bad arguments (M=%d, n_pat=%d)", M, n_pat);
-    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD)
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: unknown precision %d", precision);
     if (n_pat == 0) return GBS_OK;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -287,7 +287,7 @@ int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_
 }
 
 int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops) {
-    if (!ctx || !flops || (kind != 0 && kind != 1)) return GBS_E_INVALID;
+    if (!ctx || !flops || kind < 0 || kind > 3) return GBS_E_INVALID;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     return peak_flops(ctx, kind, flops);
 }

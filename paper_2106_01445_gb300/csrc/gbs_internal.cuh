@@ -25,7 +25,7 @@ struct gbs_ctx {
     void *host_io = nullptr;
     size_t host_io_bytes = 0;
     // persistent-grid sizes of the sweep kernels (CTAs per SM), by precision
-    int sweep_blocks_per_sm[3] = {0, 0, 0};
+    int sweep_blocks_per_sm[4] = {0, 0, 0, 0};
     // optional event timing of the sweep kernel launches
     static const int kTimingRing = 4096;
     bool timing = false;

@@ -52,7 +52,7 @@ extern "C" int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const doub
         (n_pat && (!patterns || !logP)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_noalloc: bad arguments (M=%d, n_pat=%d, n_max=%d)",
                         M, n_pat, n_max);
-    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD)
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_noalloc: unknown precision %d", precision);
     if (n_pat > kNoAllocMaxPatterns)
         return gbs_fail(ctx, GBS_E_INVALID,

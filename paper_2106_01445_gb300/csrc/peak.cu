@@ -1,6 +1,10 @@
-// Pipe-peak microbenchmark: FP32 and FP64 FMA throughput of the whole GPU,
-// register-resident, eight independent dependency chains per thread.  Used as
-// the denominator of the arithmetic roofline of the subset sweep.
+// Pipe-peak microbenchmarks: FP32 and FP64 FMA throughput of the whole GPU,
+// register-resident, eight independent dependency chains per thread; and the
+// throughput of the fused Schur-update entry c - w0 b0 - w1 b1 in double-double and
+// in 128-bit fixed point, four independent chains per thread with loop-carried
+// operands.  Used as the denominators of the arithmetic roofline of the subset sweep.
+#include "dd.cuh"
+#include "fx.cuh"
 #include "gbs_internal.cuh"
 
 namespace {
@@ -20,11 +24,40 @@ __global__ void fma_loop(T *out, int iters, T a, T b) {
     if (s == (T)-12345.678) out[0] = s;  // keeps the loop alive
 }
 
+__global__ void dd_update_loop(double *out, int iters) {
+    dd c0(0.5 + threadIdx.x * 1e-6, 1e-20), c1(0.25, 1e-21), c2(0.125, 0.0), c3(0.0625, 0.0);
+    const dd w0(0.3, 1e-18), w1(0.1, 3e-19);
+    for (int it = 0; it < iters; ++it) {
+        const dd n0 = dd_fms2(c0, c1, c2, c3, w0);
+        const dd n1 = dd_fms2(c1, c2, c3, c0, w1);
+        const dd n2 = dd_fms2(c2, c3, c0, c1, w0);
+        const dd n3 = dd_fms2(c3, c0, c1, c2, w1);
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    const double s = (c0.hi + c1.hi) + (c2.hi + c3.hi);
+    if (s == -12345.678) out[0] = s;
+}
+
+__global__ void fx_update_loop(double *out, int iters) {
+    fx c0 = fx_from_double(0.5 + threadIdx.x * 1e-6), c1 = fx_from_double(0.25);
+    fx c2 = fx_from_double(-0.125), c3 = fx_from_double(0.0625);
+    const fx w0 = fx_from_double(0.3), w1 = fx_from_double(-0.1);
+    for (int it = 0; it < iters; ++it) {
+        const fx n0 = c0 - c1 * c2 - c3 * w0;
+        const fx n1 = c1 - c2 * c3 - c0 * w1;
+        const fx n2 = c2 - c3 * c0 - c1 * w0;
+        const fx n3 = c3 - c0 * c1 - c2 * w1;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    const uint32_t s = c0.w[0] ^ c1.w[1] ^ c2.w[2] ^ c3.w[3];
+    if (s == 0x9e3779b9u) out[0] = 1.0;
+}
+
 }  // namespace
 
 int peak_flops(gbs_ctx *ctx, int kind, double *flops) {
     int threads = 256, blocks = ctx->num_sms * 8;
-    int iters = kind == 0 ? 4096 : 128;
+    const int iters = kind == 0 ? 4096 : kind == 1 ? 128 : kind == 2 ? 128 : 1024;
     cudaEvent_t e0, e1;
     GBS_CUDA(ctx, cudaEventCreate(&e0));
     GBS_CUDA(ctx, cudaEventCreate(&e1));
@@ -34,9 +67,13 @@ int peak_flops(gbs_ctx *ctx, int kind, double *flops) {
         if (kind == 0)
             fma_loop<float><<<blocks, threads, 0, ctx->stream>>>((float *)ctx->dscratch, iters,
                                                                  0.999999f, 1e-7f);
-        else
+        else if (kind == 1)
             fma_loop<double><<<blocks, threads, 0, ctx->stream>>>((double *)ctx->dscratch, iters,
                                                                   0.999999, 1e-7);
+        else if (kind == 2)
+            dd_update_loop<<<blocks, threads, 0, ctx->stream>>>((double *)ctx->dscratch, iters);
+        else
+            fx_update_loop<<<blocks, threads, 0, ctx->stream>>>((double *)ctx->dscratch, iters);
         GBS_CUDA(ctx, cudaGetLastError());
         GBS_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
         GBS_CUDA(ctx, cudaEventSynchronize(e1));
@@ -46,7 +83,9 @@ int peak_flops(gbs_ctx *ctx, int kind, double *flops) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    double fl = 2.0 * 8 * 16 * (double)iters * threads * blocks;
+    // FMA loops: 8 chains x 16 FMA x 2 flops; update loops: 4 entries x 4 flops
+    const double per = kind <= 1 ? 2.0 * 8 * 16 : 4.0 * 4;
+    double fl = per * (double)iters * threads * blocks;
     *flops = fl / (best * 1e-3);
     return GBS_OK;
 }

@@ -24,6 +24,7 @@
 #include <stdlib.h>
 
 #include "dd.cuh"
+#include "fx.cuh"
 #include "gbs_internal.cuh"
 
 namespace {
@@ -47,30 +48,60 @@ template <> struct Prec<float> {
     static constexpr int B = 6, idx = GBS_FP32_SPLIT;
     using Tau = double;
     using Abs = float;
+    using Node = float;
+    static constexpr bool fixed = false;
     static constexpr double u = 5.9604644775390625e-08, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<double> {
     static constexpr int B = 4, idx = GBS_FP64;
     using Tau = double;
     using Abs = double;
+    using Node = double;
+    static constexpr bool fixed = false;
     static constexpr double u = 1.1102230246251565e-16, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<dd> {
     static constexpr int B = 3, idx = GBS_DD;
     using Tau = dd;
     using Abs = double;
+    using Node = dd;
+    static constexpr bool fixed = false;
     static constexpr double u = 1.2325951644078309e-32, u_sum = 1.2325951644078309e-32;
+};
+// Q16.112 fixed point: truncated products (2^-112) and the pivot rsqrt's Newton step
+// (~2^-104 relative) give each factor a relative error far below 2^-100 while its
+// pivot determinant stays >= 2^-8; prefactors and sums in double-double.
+template <> struct Prec<fx> {
+    static constexpr int B = 2, idx = GBS_FX;
+    using Tau = dd;
+    using Abs = float;
+    using Node = dd;
+    static constexpr bool fixed = true;
+    static constexpr double u = 7.888609052210118e-31, u_sum = 1.2325951644078309e-32;
 };
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
+template <> __device__ __forceinline__ fx rsq<fx>(fx x) { return fx_rsqrt(x); }
 
 // 1/sqrt(det) as a prefix factor, in the Tau type of the precision
 __device__ __forceinline__ double rsq_tau(float x) { return rsqrt((double)x); }
 __device__ __forceinline__ double rsq_tau(double x) { return rsqrt(x); }
 __device__ __forceinline__ dd rsq_tau(dd x) { return dd_rsqrt(x); }
+__device__ __forceinline__ dd rsq_tau(fx x) { return fx_to_dd(fx_rsqrt(x)); }
+
+// constants and conversions of the working type
+template <typename T> __device__ __forceinline__ T konst(double v) { return T(v); }
+template <> __device__ __forceinline__ fx konst<fx>(double v) { return fx_from_double(v); }
+__device__ __forceinline__ float to_node(float x) { return x; }
+__device__ __forceinline__ double to_node(double x) { return x; }
+__device__ __forceinline__ dd to_node(dd x) { return x; }
+__device__ __forceinline__ dd to_node(fx x) { return fx_to_dd(x); }
+// pivot check: 0 fine, 1 not positive (or NaN), 2 outside the fixed-point range
+template <typename T> __device__ __forceinline__ int pivot_bad(T det) { return det > T(0) ? 0 : 1; }
+template <> __device__ __forceinline__ int pivot_bad<fx>(fx det) { return fx_pivot_bad(det); }
 
 // the Schur-update kernels: a0 b0 + a1 b1, c - a0 b0 - a1 b1, det of a 2x2 block
 template <typename T> __device__ __forceinline__ T dot2(T a0, T b0, T a1, T b1) { return a0 * b0 + a1 * b1; }
@@ -82,20 +113,29 @@ template <typename T> __device__ __forceinline__ T det2(T p00, T p01, T p11) { r
 // an entry of A = I - O from its FP64 data (exact in double-double)
 template <typename T> __device__ __forceinline__ T a_entry(double delta, double o) { return (T)(delta - o); }
 template <> __device__ __forceinline__ dd a_entry<dd>(double delta, double o) { return dd_two_sum(delta, -o); }
+template <> __device__ __forceinline__ fx a_entry<fx>(double delta, double o) {
+    return fx_from_double(delta) - fx_from_double(o);
+}
 
 __device__ __forceinline__ double to_hi(float x) { return x; }
 __device__ __forceinline__ double to_hi(double x) { return x; }
-__device__ __forceinline__ double to_hi(dd x) { return x.hi; }
 // leading part of a (positive) term, in the type its magnitude is summed in
 __device__ __forceinline__ float abs_part(float x) { return x; }
 __device__ __forceinline__ double abs_part(double x) { return x; }
 __device__ __forceinline__ double abs_part(dd x) { return x.hi; }
-__device__ __forceinline__ double to_lo(float) { return 0.0; }
-__device__ __forceinline__ double to_lo(double) { return 0.0; }
-__device__ __forceinline__ double to_lo(dd x) { return x.lo; }
+__device__ __forceinline__ float abs_part(fx x) { return (float)(int32_t)x.w[3] * (1.0f / 65536.0f); }
 __device__ __forceinline__ bool is_nan(float x) { return x != x; }
 __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
+// a thread's subtree sum as (hi, lo) doubles
+__device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
+__device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
+__device__ __forceinline__ void sum_parts(dd h, dd l, double &oh, double &ol) { oh = h.hi; ol = h.lo + l.hi; }
+__device__ __forceinline__ void sum_parts(fx h, fx, double &oh, double &ol) {
+    const dd v = fx_to_dd(h);
+    oh = v.hi;
+    ol = v.lo;
+}
 
 // ---- shared-memory layout ----------------------------------------------------
 // X and Y alternate as source and destination of the breadth-first levels; the
@@ -114,7 +154,8 @@ template <typename T> struct Layout {
     static constexpr int max_odd() {
         int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots
         for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
-        return m;
+        // the unit's prefix matrix spans X and Y
+        return sym(2 * kMaxN) - max_even() > m ? sym(2 * kMaxN) - max_even() : m;
     }
     static constexpr int w_entries() {
         int m = 2 * (2 * kMaxN);
@@ -130,6 +171,7 @@ template <typename T> struct Layout {
         return s;
     }
     // byte offsets
+    using Node = typename Prec<T>::Node;
     static constexpr size_t off_X = 0;
     static constexpr size_t off_Y = off_X + sizeof(T) * max_even();
     static constexpr int ublk() { return sym(2 * (kS + R)); }
@@ -137,8 +179,8 @@ template <typename T> struct Layout {
     static constexpr size_t off_W = off_U + sizeof(T) * ublk();
     static constexpr size_t off_Q = off_W + sizeof(T) * w_entries();
     static constexpr size_t off_tauX = off_Q + sizeof(T) * 3 * (kThreads / 2);
-    static constexpr size_t off_tauY = off_tauX + sizeof(T) * kThreads;
-    static constexpr size_t off_red = off_tauY + sizeof(T) * kThreads;      // 3 doubles per warp
+    static constexpr size_t off_tauY = off_tauX + sizeof(Node) * kThreads;
+    static constexpr size_t off_red = off_tauY + sizeof(Node) * kThreads;      // 3 doubles per warp
     static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
     static constexpr size_t off_pos = off_modes + sizeof(int) * 128;
     static constexpr size_t off_decoff = off_pos + sizeof(int) * 2 * kMaxN;
@@ -157,6 +199,7 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 template <typename T> struct Acc {
     T hi, lo;
     typename Prec<T>::Abs abs;  // sum of |terms|, for kappa only
+    int bad;                    // fixed point: pivot checks of the register levels
 };
 
 template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
@@ -165,8 +208,9 @@ template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
     a.lo += (a.hi - (s - bp)) + (x - bp);
     a.hi = s;
 }
-// double-double sums need no further compensation
+// double-double sums need no further compensation; fixed-point sums are exact
 template <> __device__ __forceinline__ void acc_add<dd>(Acc<dd> &a, dd x) { a.hi += x; }
+template <> __device__ __forceinline__ void acc_add<fx>(Acc<fx> &a, fx x) { a.hi += x; }
 
 // (hi, lo) += sc * (x_hi + x_lo) for one thread's subtree sum
 __device__ __forceinline__ void unit_add(double &h, double &l, double sc, double xh, double xl) {
@@ -216,6 +260,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
     constexpr int o = 2 * O;
     const T p00 = A(o, o), p01 = A(o, o + 1), p11 = A(o + 1, o + 1);
     const T det = det2(p00, p01, p11);
+    if constexpr (Prec<T>::fixed) acc.bad |= pivot_bad(det);
     const T rs = rsq<T>(det);
     const bool real = depth < nreal;
     if constexpr (m == 1) {
@@ -348,7 +393,10 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
     const int t = threadIdx.x;
     const T p00 = Mx[pidx(D, c0, c0)], p01 = Mx[pidx(D, c0, c0 + 1)], p11 = Mx[pidx(D, c0 + 1, c0 + 1)];
     const T det = det2(p00, p01, p11);
-    if (t == 0 && !(det > T(0))) *flag = 1;
+    if (t == 0) {
+        const int bad = pivot_bad(det);
+        if (bad) atomicOr(flag, bad);
+    }
     const int Dt = D - c0 - 2;
     if (t < Dt) {
         const T rs = rsq<T>(det);
@@ -391,8 +439,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     extern __shared__ __align__(16) unsigned char smem[];
     T *X = (T *)(smem + Lay::off_X);
     T *Y = (T *)(smem + Lay::off_Y);
-    T *tauX = (T *)(smem + Lay::off_tauX);
-    T *tauY = (T *)(smem + Lay::off_tauY);
+    using Node = typename Prec<T>::Node;
+    Node *tauX = (Node *)(smem + Lay::off_tauX);
+    Node *tauY = (Node *)(smem + Lay::off_tauY);
     double *red = (double *)(smem + Lay::off_red);
     int *modes = (int *)(smem + Lay::off_modes);
     int *pos = (int *)(smem + Lay::off_pos);
@@ -474,10 +523,12 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             const int a = pos[i >> 1], b = pos[j >> 1];
             T v;
             if (a >= n || b >= n) {
-                v = (i == j) ? T(1) : T(0);
+                v = konst<T>((i == j) ? 1.0 : 0.0);
             } else {
                 const int si = modes[a] + (i & 1) * M, sj = modes[b] + (j & 1) * M;
-                v = a_entry<T>(i == j ? 1.0 : 0.0, O[(size_t)si * N2 + sj]);
+                const double o = O[(size_t)si * N2 + sj];
+                if (Prec<T>::fixed && !(fabs(o) <= 4.0)) atomicOr(&s_flag, 2);
+                v = a_entry<T>(i == j ? 1.0 : 0.0, o);
             }
             X[pidx(D0, i, j)] = v;
         }
@@ -530,7 +581,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int i = f / d, j = f - i * d;
                     if (j >= i) X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
                 }
-                if (t == 0) tauX[0] = T(1);
+                if (t == 0) tauX[0] = Node(1.0);
             }
             __syncthreads();
             // breadth-first expansion of L_eff levels: node c at level l + 1 is child
@@ -538,8 +589,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             for (int l = 0; l < L_eff; ++l) {
                 const T *src = (l & 1) ? Y : X;
                 T *dst = (l & 1) ? X : Y;
-                const T *tsrc = (l & 1) ? tauY : tauX;
-                T *tdst = (l & 1) ? tauX : tauY;
+                const Node *tsrc = (l & 1) ? tauY : tauX;
+                Node *tdst = (l & 1) ? tauX : tauY;
                 const int d = 2 * (r - l), dc = d - 2;
                 const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
                 const int np = 1 << l;
@@ -554,8 +605,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     Qb[3 * t + 1] = -p01 * inv;
                     Qb[3 * t + 2] = p00 * inv;
                     tdst[2 * t] = tsrc[t];
-                    tdst[2 * t + 1] = tsrc[t] * rs;
-                    if (!(det > T(0))) s_flag = 1;
+                    tdst[2 * t + 1] = tsrc[t] * to_node(rs);
+                    const int bad = pivot_bad(det);
+                    if (bad) atomicOr(&s_flag, bad);
                 }
                 __syncthreads();
                 // (b) W = B P^{-1} for every parent, dc rows each
@@ -593,16 +645,19 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             // register-resident bottom B levels, one node per thread
             if (t < (1 << L_eff)) {
                 const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
-                const T tau_node = ((L_eff & 1) ? tauY : tauX)[t];
+                const Node tau_node = ((L_eff & 1) ? tauY : tauX)[t];
                 const int nreal = n - (n_eff - B);
-                Acc<T> acc{T(0), T(0), 0};
+                Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
                 SmemMat<T, B> A{node};
-                dfs<T, B, 0, false>(A, T(1), 0, nreal, acc);
+                dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc);
                 const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
                 const Tau sc = Tau((excl & 1) ? -1.0 : 1.0) * Tau(tau_node) * tsub;
-                unit_add(u_hi, u_lo, sc, to_hi(acc.hi) , to_lo(acc.hi) + to_hi(acc.lo));
+                double sh, sl;
+                sum_parts(acc.hi, acc.lo, sh, sl);
+                unit_add(u_hi, u_lo, sc, sh, sl);
                 u_abs += tau_abs(sc) * to_hi(acc.abs);
-                if (is_nan(acc.abs) || is_nan(tau_node)) s_flag = 1;
+                if (is_nan(acc.abs) || is_nan(tau_node)) atomicOr(&s_flag, 1);
+                if (acc.bad) atomicOr(&s_flag, acc.bad);
             }
             __syncthreads();   // X / Y are rewritten by the next sub-unit
         }
@@ -640,7 +695,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             out[0] = h;
             out[1] = l;
             out[2] = a * tau_hi(tp);
-            if (s_flag || is_nan(tp)) atomicOr(pl.pflags + sp, 1);
+            const int fl = s_flag | (is_nan(tp) ? 1 : 0);
+            if (fl) atomicOr(pl.pflags + sp, fl);
         }
         __syncthreads();
     }
@@ -689,7 +745,7 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
     } else if (batch_over) {
         st = GBS_E_NOMEM;
     } else if (pl.pflags[sp] != 0) {
-        st = GBS_E_NOT_SPD;
+        st = (pl.pflags[sp] & 1) ? GBS_E_NOT_SPD : GBS_E_RANGE;
     } else {
         // a-posteriori bound: every term carries a relative error of at most
         // c (2n + 4) u from its chain of 2x2 pivots; the signed sum amplifies by kappa.
@@ -846,6 +902,9 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
     if (precision == GBS_DD)
         return run_sweep_on<dd>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
                                 err_bound, status);
+    if (precision == GBS_FX)
+        return run_sweep_on<fx>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
+                                err_bound, status);
     return run_sweep_on<float>(ctx, ws, ws_bytes, M, O, logdet, patterns, n_pat, logP, kappa,
                                err_bound, status);
 }
@@ -856,6 +915,7 @@ long long sweep_units_upper_bound(int n_pat, int n_max, int precision) {
     int n_eff, L_eff, q, ss;
     if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss);
     else if (precision == GBS_DD) unit_shape<dd>(n_max, n_eff, L_eff, q, ss);
+    else if (precision == GBS_FX) unit_shape<fx>(n_max, n_eff, L_eff, q, ss);
     else unit_shape<float>(n_max, n_eff, L_eff, q, ss);
     return (long long)n_pat << (q - ss);
 }
@@ -867,5 +927,7 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
         return run_sweep<double>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     if (precision == GBS_DD)
         return run_sweep<dd>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+    if (precision == GBS_FX)
+        return run_sweep<fx>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
 }

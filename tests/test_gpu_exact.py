@@ -3,8 +3,8 @@ sweep) against the oracle, through the C ABI.
 
 Improbable click patterns cancel by many orders of magnitude in the signed
 sum (kappa = sum|term|/|T| reaches 1e13 on the 24-mode workload), so the
-reference is the double-double oracle.  Bounds: the double-double path must
-match it to 1e-10 in log P; the FP64 path to 1e-10 wherever its own
+reference is the double-double oracle.  Bounds: the double-double and the
+fixed-point paths must match it to 1e-10 in log P; the FP64 path to 1e-10 wherever its own
 a-posteriori bound is below that, else within the bound; the FP32 split within
 its bound, or it reports GBS_E_NONPOSITIVE when its sum loses the sign."""
 import math
@@ -51,7 +51,7 @@ def check_against_oracle(res, ref, precision):
         assert (st == 0).all(), st
     d = np.abs(res["logP"][ok] - ref["logP"][ok])
     bound = res["err_bound"][ok]
-    if precision == "dd":
+    if precision in ("dd", "fx"):
         assert (d <= TOL64).all(), (d.max(), res["kappa"][ok][d.argmax()])
     elif precision == "fp64":
         assert (d <= np.maximum(TOL64, bound)).all(), (d.max(), bound[d.argmax()])
@@ -99,7 +99,7 @@ def test_gen_patterns_bit_exact(ctx, M, n_lo, n_hi, n_pat, seed, stream):
     assert np.array_equal(dev, host)
 
 
-@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["dd", "fx", "fp64", "fp32"])
 @pytest.mark.parametrize("eta", [1.0, 0.5])
 def test_all_patterns_m8(ctx, precision, eta):
     c = g.CONFIGS["m8_all"]
@@ -110,7 +110,7 @@ def test_all_patterns_m8(ctx, precision, eta):
     check_against_oracle(res, ref, precision)
     p = np.exp(res["logP"])
     if precision != "fp32":
-        assert abs(p.sum() - 1.0) < (1e-14 if precision == "dd" else 1e-12)
+        assert abs(p.sum() - 1.0) < (1e-14 if precision in ("dd", "fx") else 1e-12)
     else:
         assert abs(np.nansum(p) - 1.0) < 1e-4
 
@@ -129,7 +129,7 @@ def uneven():
     return U, r, pats, oracle_dd(U, r, 0.55, pats)
 
 
-@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["dd", "fx", "fp64", "fp32"])
 def test_uneven_batch_all_sizes(ctx, uneven, precision):
     U, r, pats, ref = uneven
     st = gpu_state(ctx, U, r, 0.55)
@@ -153,7 +153,7 @@ def m24_sample():
     return c, U, r, pats, idx, oracle_dd(U, r, c.eta, pats[idx])
 
 
-@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["dd", "fx", "fp64", "fp32"])
 def test_m24_config_sample(ctx, m24_sample, precision):
     # the benchmark's launch shape: all 1024 patterns in one call
     c, U, r, pats, idx, ref = m24_sample
@@ -203,12 +203,12 @@ def test_block_diagonal_factorises_at_n30(ctx):
             loc = list(range(bs)) if b in cb else []
             lp += oracle.prob_exact(sub, g.modes_to_pattern(loc)[None], dd=True)["logP"][0]
         refs.append(lp)
-    for precision in ("dd", "fp64"):
+    for precision in ("dd", "fx", "fp64"):
         res = gpu_prob(ctx, st, pats, precision)
         for i in range(len(pats)):
             assert res["status"][i] == 0
             d = abs(res["logP"][i] - refs[i])
-            if precision == "dd":
+            if precision in ("dd", "fx"):
                 assert res["err_bound"][i] < 1e-10 and d <= TOL64, (i, d, res["kappa"][i])
             else:
                 assert d <= max(TOL64, res["err_bound"][i]), (precision, i)
@@ -224,19 +224,40 @@ def test_large_pattern_against_parallel_oracle(ctx):
     ref_state = oracle.build_state(U, r, c.eta)
     T = oracle.subset_sum(ref_state.A, 24, modes, nchunk=256, dd=True)
     ref = -0.5 * ref_state.logdet + math.log(T[0]) + math.log1p(T[1] / T[0])
-    for precision in ("dd", "fp64"):
+    for precision in ("dd", "fx", "fp64"):
         res = gpu_prob(ctx, st, g.modes_to_pattern(modes)[None], precision)
-        tol = TOL64 if precision == "dd" else max(TOL64, res["err_bound"][0])
+        tol = TOL64 if precision in ("dd", "fx") else max(TOL64, res["err_bound"][0])
         assert abs(res["logP"][0] - ref) <= tol, precision
 
 
 def test_deterministic(ctx):
     c = g.CONFIGS["m24_exact"]
     st = gpu_state(ctx, c.unitary(), c.squeezing(), c.eta)
-    for precision in ("dd", "fp64", "fp32"):
+    for precision in ("dd", "fx", "fp64", "fp32"):
         a = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
         b = gpu_prob(ctx, st, c.patterns(), precision)["logP"]
         assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_fixed_point_range_flagged(ctx):
+    # two modes squeezed so strongly (r = 4: sigma_Q has eigenvalue ~1490) that their
+    # pivot determinants fall below 2^-8: the fixed-point path reports GBS_E_RANGE
+    # for every pattern that clicks one of them and stays exact on the others
+    M = 6
+    U = np.eye(M, dtype=complex)
+    r = np.array([4.0, 4.0, 0.5, 0.6, 0.7, 0.8])
+    mode_sets = [[2, 3], [2, 3, 4, 5], [4], [0], [1, 2], [0, 1, 4]]
+    pats = np.stack([g.modes_to_pattern(m) for m in mode_sets])
+    st = gpu_state(ctx, U, r, 1.0)
+    res = gpu_prob(ctx, st, pats, "fx")
+    ref = oracle_dd(U, r, 1.0, pats)
+    in_range = np.array([not ({0, 1} & set(m)) for m in mode_sets])
+    assert (res["status"][~in_range] == 8).all(), res["status"]
+    assert (res["status"][in_range] == 0).all(), res["status"]
+    assert np.abs(res["logP"][in_range] - ref["logP"][in_range]).max() <= TOL64
+    dd = gpu_prob(ctx, st, pats, "dd")
+    assert (dd["status"] == 0).all()
+    assert np.abs(dd["logP"] - ref["logP"]).max() <= TOL64
 
 
 def test_invalid_patterns_flagged(ctx):

@@ -20,7 +20,7 @@ def ctx(cuda_ok):
     return Context(0)
 
 
-@pytest.mark.parametrize("precision", ["dd", "fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["dd", "fx", "fp64", "fp32"])
 def test_noalloc_matches_gbs_prob_twice(ctx, precision):
     c = g.CONFIGS["m24_exact"]
     st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
@@ -36,7 +36,7 @@ def test_noalloc_matches_gbs_prob_twice(ctx, precision):
         assert np.array_equal(out["status"], ref["status"])
         ok = ref["status"] == 0
         d = np.abs(out["logP"][ok] - ref["logP"][ok])
-        tol = 1e-10 if precision == "dd" else np.maximum(1e-10, ref["err_bound"][ok])
+        tol = 1e-10 if precision in ("dd", "fx") else np.maximum(1e-10, ref["err_bound"][ok])
         assert (d <= tol).all()
 
 
