@@ -93,28 +93,66 @@ __device__ __forceinline__ void fx_mul_upper(const fx &a, const fx &b, uint32_t 
         : "r"(a.w[3]), "r"(b.w[0]), "r"(b.w[1]), "r"(b.w[2]), "r"(b.w[3]));
 }
 
-// signed product: the unsigned product minus 2^128 (b [a < 0] + a [b < 0]), bits 112..239
-__device__ __forceinline__ fx operator*(const fx &a, const fx &b) {
-    uint32_t p3, p4, p5, p6, p7;
-    fx_mul_upper(a, b, p3, p4, p5, p6, p7);
-    const uint32_t ma = (uint32_t)((int32_t)a.w[3] >> 31), mb = (uint32_t)((int32_t)b.w[3] >> 31);
-    asm("sub.cc.u32 %0, %0, %4;\n\t"
-        "subc.cc.u32 %1, %1, %5;\n\t"
-        "subc.cc.u32 %2, %2, %6;\n\t"
-        "subc.u32 %3, %3, %7;"
-        : "+r"(p4), "+r"(p5), "+r"(p6), "+r"(p7)
-        : "r"(b.w[0] & ma), "r"(b.w[1] & ma), "r"(b.w[2] & ma), "r"(b.w[3] & ma));
-    asm("sub.cc.u32 %0, %0, %4;\n\t"
-        "subc.cc.u32 %1, %1, %5;\n\t"
-        "subc.cc.u32 %2, %2, %6;\n\t"
-        "subc.u32 %3, %3, %7;"
-        : "+r"(p4), "+r"(p5), "+r"(p6), "+r"(p7)
-        : "r"(a.w[0] & mb), "r"(a.w[1] & mb), "r"(a.w[2] & mb), "r"(a.w[3] & mb));
+// bits 112..239 of the product held in limbs 3..7
+__device__ __forceinline__ fx fx_shift_out(uint32_t p3, uint32_t p4, uint32_t p5, uint32_t p6, uint32_t p7) {
     fx r;
     r.w[0] = __funnelshift_r(p3, p4, 16);
     r.w[1] = __funnelshift_r(p4, p5, 16);
     r.w[2] = __funnelshift_r(p5, p6, 16);
     r.w[3] = __funnelshift_r(p6, p7, 16);
+    return r;
+}
+// p4..p7 -= m & x  (the two's-complement correction 2^128 x [sign] of a signed factor)
+__device__ __forceinline__ void fx_sub_masked(uint32_t &p4, uint32_t &p5, uint32_t &p6, uint32_t &p7,
+                                              const fx &x, uint32_t m) {
+    asm("sub.cc.u32 %0, %0, %4;\n\t"
+        "subc.cc.u32 %1, %1, %5;\n\t"
+        "subc.cc.u32 %2, %2, %6;\n\t"
+        "subc.u32 %3, %3, %7;"
+        : "+r"(p4), "+r"(p5), "+r"(p6), "+r"(p7)
+        : "r"(x.w[0] & m), "r"(x.w[1] & m), "r"(x.w[2] & m), "r"(x.w[3] & m));
+}
+__device__ __forceinline__ uint32_t fx_sign_mask(const fx &a) { return (uint32_t)((int32_t)a.w[3] >> 31); }
+
+// signed product: the unsigned product minus 2^128 (b [a < 0] + a [b < 0]), bits 112..239
+__device__ __forceinline__ fx operator*(const fx &a, const fx &b) {
+    uint32_t p3, p4, p5, p6, p7;
+    fx_mul_upper(a, b, p3, p4, p5, p6, p7);
+    fx_sub_masked(p4, p5, p6, p7, b, fx_sign_mask(a));
+    fx_sub_masked(p4, p5, p6, p7, a, fx_sign_mask(b));
+    return fx_shift_out(p3, p4, p5, p6, p7);
+}
+// a * b for a, b >= 0
+__device__ __forceinline__ fx fx_mul_uu(const fx &a, const fx &b) {
+    uint32_t p3, p4, p5, p6, p7;
+    fx_mul_upper(a, b, p3, p4, p5, p6, p7);
+    return fx_shift_out(p3, p4, p5, p6, p7);
+}
+// a * b for b >= 0, a of either sign
+__device__ __forceinline__ fx fx_mul_su(const fx &a, const fx &b) {
+    uint32_t p3, p4, p5, p6, p7;
+    fx_mul_upper(a, b, p3, p4, p5, p6, p7);
+    fx_sub_masked(p4, p5, p6, p7, b, fx_sign_mask(a));
+    return fx_shift_out(p3, p4, p5, p6, p7);
+}
+__device__ __forceinline__ fx fx_abs(const fx &a) {
+    const uint32_t m = fx_sign_mask(a);
+    fx x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x.w[k] = a.w[k] ^ m;
+    fx r;
+    asm("sub.cc.u32 %0, %4, %8;\n\t"
+        "subc.cc.u32 %1, %5, %8;\n\t"
+        "subc.cc.u32 %2, %6, %8;\n\t"
+        "subc.u32 %3, %7, %8;"
+        : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3])
+        : "r"(x.w[0]), "r"(x.w[1]), "r"(x.w[2]), "r"(x.w[3]), "r"(m));
+    return r;
+}
+// a + k 2^-16 for a small integer k (top limb only: no carry below)
+__device__ __forceinline__ fx fx_add_top(const fx &a, int k) {
+    fx r = a;
+    r.w[3] = (uint32_t)((int32_t)a.w[3] + k);
     return r;
 }
 __device__ __forceinline__ fx &operator*=(fx &a, const fx &b) { return a = a * b; }
@@ -177,12 +215,57 @@ __device__ __forceinline__ int fx_pivot_bad(const fx &det) {
     if (!fx_positive(det)) return 1;
     return (int32_t)det.w[3] < 256 ? 2 : 0;
 }
+// the same for a pivot block given by its Cholesky quantities: p00 and the Schur
+// remainder x = det / p00 positive, rs = det^{-1/2} below 16 (det >= 2^-8)
+__device__ __forceinline__ int fx_chol_bad(const fx &p00, const fx &x, const fx &rs) {
+    if (!fx_positive(p00) || !fx_positive(x)) return 1;
+    return (int32_t)rs.w[3] >= (16 << 16) ? 2 : 0;
+}
 
-// det^{-1/2} for det in [2^-8, 4]: double estimate y, one Newton step y (1 + e/2),
-// e = 1 - det y^2, in fixed point: relative error ~ (3/8) (2^-52)^2.
-__device__ __forceinline__ fx fx_rsqrt(const fx &det) {
-    const double y = rsqrt(fx_to_double(det));
+// x^{-1/2} for x in [2^-9, 4]: double estimate y, one Newton step y (1 + e/2),
+// e = 1 - x y^2, in fixed point: relative error ~ (3/8) (2^-52)^2.  x <= 0 gives 0.
+__device__ __forceinline__ fx fx_rsqrt(const fx &x) {
+    const double y = rsqrt(fx_to_double(x));
     const fx y0 = fx_from_double(y);
-    const fx e = fx_one() - det * (y0 * y0);
-    return y0 + fx_half(y0 * e);
+    const fx e = fx_one() - fx_mul_uu(x, fx_mul_uu(y0, y0));
+    return y0 + fx_half(fx_mul_su(e, y0));
+}
+// det of the SPD 2x2 block [[p00, p01], [p01, p11]]
+__device__ __forceinline__ fx fx_det2(const fx &p00, const fx &p01, const fx &p11) {
+    const fx a = fx_abs(p01);
+    return fx_mul_uu(p00, p11) - fx_mul_uu(a, a);
+}
+
+// Symmetric form of the 2x2 block elimination used by the fixed-point sweep.  With
+// the pivot block P = R R^T (R lower triangular, 1/r00 = a, r10, 1/r11 = b), the
+// Schur update C - B P^{-1} B^T equals C - U U^T, U = B R^{-T}: row i of U is
+// u0 = b_i0 a, u1 = (b_i1 - r10 u0) b.  |u_ik| <= sqrt(c_ii) <= sqrt(2), so the rows
+// are stored offset, u' = u + 2 > 0, and each entry needs two unsigned products:
+//   c_ij - u_i . u_j = c_ij - (u'_i0 u'_j0 + u'_i1 u'_j1) + t_i + t_j,  t = 2 (u'0 + u'1) - 4.
+struct fx_piv {
+    fx a, r10, b, rs, x;  // x = det / p00
+};
+__device__ __forceinline__ fx_piv fx_pivot(const fx &p00, const fx &p01, const fx &p11) {
+    fx_piv v;
+    v.a = fx_rsqrt(p00);
+    v.r10 = fx_mul_su(p01, v.a);
+    const fx r = fx_abs(v.r10);
+    v.x = p11 - fx_mul_uu(r, r);
+    v.b = fx_rsqrt(v.x);
+    v.rs = fx_mul_uu(v.a, v.b);
+    return v;
+}
+// offset row (u'0, u'1, t) of U from the pivot-row entries b0 = P(0, .), b1 = P(1, .)
+__device__ __forceinline__ void fx_urow(const fx_piv &v, const fx &b0, const fx &b1, fx &u0, fx &u1, fx &t) {
+    const fx x0 = fx_mul_su(b0, v.a);
+    const fx x1 = fx_mul_su(b1 - x0 * v.r10, v.b);
+    u0 = fx_add_top(x0, 2 << 16);
+    u1 = fx_add_top(x1, 2 << 16);
+    const fx s = u0 + u1;
+    t = fx_add_top(s + s, -(4 << 16));
+}
+// c - u_i . u_j from the offset rows
+__device__ __forceinline__ fx fx_sym_update(const fx &c, const fx &ui0, const fx &ui1, const fx &ti,
+                                            const fx &uj0, const fx &uj1, const fx &tj) {
+    return ((c + ti) + tj) - (fx_mul_uu(ui0, uj0) + fx_mul_uu(ui1, uj1));
 }

@@ -50,6 +50,7 @@ template <> struct Prec<float> {
     using Abs = float;
     using Node = float;
     static constexpr bool fixed = false;
+    static constexpr int wrow = 2;  // entries per row of W
     static constexpr double u = 5.9604644775390625e-08, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<double> {
@@ -58,6 +59,7 @@ template <> struct Prec<double> {
     using Abs = double;
     using Node = double;
     static constexpr bool fixed = false;
+    static constexpr int wrow = 2;
     static constexpr double u = 1.1102230246251565e-16, u_sum = 1.1102230246251565e-16;
 };
 template <> struct Prec<dd> {
@@ -66,6 +68,7 @@ template <> struct Prec<dd> {
     using Abs = double;
     using Node = dd;
     static constexpr bool fixed = false;
+    static constexpr int wrow = 2;
     static constexpr double u = 1.2325951644078309e-32, u_sum = 1.2325951644078309e-32;
 };
 // Q16.112 fixed point: truncated products (2^-112) and the pivot rsqrt's Newton step
@@ -77,6 +80,7 @@ template <> struct Prec<fx> {
     using Abs = float;
     using Node = dd;
     static constexpr bool fixed = true;
+    static constexpr int wrow = 3;  // offset rows (u'0, u'1, t) of U = B R^{-T}
     static constexpr double u = 7.888609052210118e-31, u_sum = 1.2325951644078309e-32;
 };
 
@@ -99,6 +103,9 @@ __device__ __forceinline__ float to_node(float x) { return x; }
 __device__ __forceinline__ double to_node(double x) { return x; }
 __device__ __forceinline__ dd to_node(dd x) { return x; }
 __device__ __forceinline__ dd to_node(fx x) { return fx_to_dd(x); }
+// product of two non-negative factors
+template <typename T> __device__ __forceinline__ T mul_pos(T a, T b) { return a * b; }
+template <> __device__ __forceinline__ fx mul_pos<fx>(fx a, fx b) { return fx_mul_uu(a, b); }
 // pivot check: 0 fine, 1 not positive (or NaN), 2 outside the fixed-point range
 template <typename T> __device__ __forceinline__ int pivot_bad(T det) { return det > T(0) ? 0 : 1; }
 template <> __device__ __forceinline__ int pivot_bad<fx>(fx det) { return fx_pivot_bad(det); }
@@ -109,6 +116,7 @@ template <> __device__ __forceinline__ dd dot2<dd>(dd a0, dd b0, dd a1, dd b1) {
 template <typename T> __device__ __forceinline__ T fms2(T c, T a0, T b0, T a1, T b1) { return c - a0 * b0 - a1 * b1; }
 template <> __device__ __forceinline__ dd fms2<dd>(dd c, dd a0, dd b0, dd a1, dd b1) { return dd_fms2(c, a0, b0, a1, b1); }
 template <typename T> __device__ __forceinline__ T det2(T p00, T p01, T p11) { return dot2(p00, p11, -p01, p01); }
+template <> __device__ __forceinline__ fx det2<fx>(fx p00, fx p01, fx p11) { return fx_det2(p00, p01, p11); }
 
 // an entry of A = I - O from its FP64 data (exact in double-double)
 template <typename T> __device__ __forceinline__ T a_entry(double delta, double o) { return (T)(delta - o); }
@@ -139,9 +147,10 @@ __device__ __forceinline__ void sum_parts(fx h, fx, double &oh, double &ol) {
 
 // ---- shared-memory layout ----------------------------------------------------
 // X and Y alternate as source and destination of the breadth-first levels; the
-// unit's prefix-elimination matrix (up to 2 kMaxN rows) spans both before the
-// levels start.  Ub holds the unit's trailing block, W the rows W = B P^{-1} of the
-// level (or prefix pivot) being eliminated, Q the inverse pivots of a level's parents.
+// unit's prefix-elimination matrix (up to 2 kMaxN rows) spans X, Y, Ub and W before
+// the levels start.  Ub holds the unit's trailing block, W the rows W = B P^{-1} of
+// the level being eliminated, Q the pivot quantities of a level's parents (and the W
+// rows of a prefix pivot).
 template <typename T> struct Layout {
     static constexpr int B = Prec<T>::B;
     static constexpr int R = kL + B;  // modes of a unit's level-0 matrix
@@ -154,17 +163,17 @@ template <typename T> struct Layout {
     static constexpr int max_odd() {
         int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots
         for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
-        // the unit's prefix matrix spans X and Y
-        return sym(2 * kMaxN) - max_even() > m ? sym(2 * kMaxN) - max_even() : m;
+        return m;
     }
     static constexpr int w_entries() {
-        int m = 2 * (2 * kMaxN);
+        int m = 0;
         for (int l = 0; l < kL; ++l) {
-            const int v = (1 << l) * 2 * (2 * (R - l - 1));
+            const int v = (1 << l) * Prec<T>::wrow * (2 * (R - l - 1));
             m = v > m ? v : m;
         }
         return m;
     }
+    static constexpr int q_entries() { return 3 * (kThreads / 2) > 4 * kMaxN ? 3 * (kThreads / 2) : 4 * kMaxN; }
     static constexpr int dec_entries() {
         int s = 0;
         for (int m = 1; m <= R; ++m) s += sym(2 * m);
@@ -178,7 +187,7 @@ template <typename T> struct Layout {
     static constexpr size_t off_U = off_Y + sizeof(T) * max_odd();
     static constexpr size_t off_W = off_U + sizeof(T) * ublk();
     static constexpr size_t off_Q = off_W + sizeof(T) * w_entries();
-    static constexpr size_t off_tauX = off_Q + sizeof(T) * 3 * (kThreads / 2);
+    static constexpr size_t off_tauX = off_Q + sizeof(T) * q_entries();
     static constexpr size_t off_tauY = off_tauX + sizeof(Node) * kThreads;
     static constexpr size_t off_red = off_tauY + sizeof(Node) * kThreads;      // 3 doubles per warp
     static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
@@ -186,7 +195,7 @@ template <typename T> struct Layout {
     static constexpr size_t off_decoff = off_pos + sizeof(int) * 2 * kMaxN;
     static constexpr size_t off_dec = off_decoff + sizeof(int) * (R + 2);
     static constexpr size_t bytes = (off_dec + sizeof(uint16_t) * dec_entries() + 15) / 16 * 16;
-    static_assert(sizeof(T) * sym(2 * kMaxN) <= off_U, "prefix matrix must fit in X and Y");
+    static_assert(sizeof(T) * sym(2 * kMaxN) <= off_Q, "prefix matrix must fit in X, Y, Ub and W");
 };
 
 // ---- error-free accumulation ----------------------------------------------------
@@ -259,18 +268,36 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
     constexpr int m = MD - O;
     constexpr int o = 2 * O;
     const T p00 = A(o, o), p01 = A(o, o + 1), p11 = A(o + 1, o + 1);
-    const T det = det2(p00, p01, p11);
-    if constexpr (Prec<T>::fixed) acc.bad |= pivot_bad(det);
-    const T rs = rsq<T>(det);
     const bool real = depth < nreal;
     if constexpr (m == 1) {
+        const T det = det2(p00, p01, p11);
+        if constexpr (Prec<T>::fixed) acc.bad |= pivot_bad(det);
+        const T rs = rsq<T>(det);
         // the two leaves: include (+tau rs) and exclude (-tau)
-        const T inc = tau * rs;
+        const T inc = mul_pos(tau, rs);
         T comb = real ? inc - tau : inc;
         acc_add(acc, NEG ? -comb : comb);
         acc.abs += real ? abs_part(inc) + abs_part(tau) : abs_part(inc);
+    } else if constexpr (Prec<T>::fixed) {
+        // symmetric form C - U U^T, U = B R^{-T} (offset rows)
+        constexpr int d = 2 * (m - 1);
+        const fx_piv v = fx_pivot(p00, p01, p11);
+        acc.bad |= fx_chol_bad(p00, v.x, v.rs);
+        fx u0[d], u1[d], tt[d];
+#pragma unroll
+        for (int i = 0; i < d; ++i) fx_urow(v, A(o, o + 2 + i), A(o + 1, o + 2 + i), u0[i], u1[i], tt[i]);
+        RegMat<T, m - 1> C;
+#pragma unroll
+        for (int i = 0; i < d; ++i)
+#pragma unroll
+            for (int j = i; j < d; ++j)
+                C.v[pidx(d, i, j)] = fx_sym_update(A(o + 2 + i, o + 2 + j), u0[i], u1[i], tt[i], u0[j], u1[j], tt[j]);
+        dfs<T, m - 1, 0, NEG>(C, fx_mul_uu(tau, v.rs), depth + 1, nreal, acc);
+        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc);
     } else {
         constexpr int d = 2 * (m - 1);
+        const T det = det2(p00, p01, p11);
+        const T rs = rsq<T>(det);
         const T inv = rs * rs;
         const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
         T b0[d], b1[d], w0[d], w1[d];
@@ -535,13 +562,23 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         __syncthreads();
         // eliminate the included prefix modes (2x2 block pivots)
         Tau tpre = Tau(1.0);
-        for (int e = 0; e < k; ++e) tpre = tpre * elim_pivot<T>(X, D0, 2 * e, Wb, &s_flag);
-        // the unit's trailing 2rp x 2rp block -> Ublk
+        for (int e = 0; e < k; ++e) tpre = tpre * elim_pivot<T>(X, D0, 2 * e, Qb, &s_flag);
+        // the unit's trailing 2rp x 2rp block -> Ublk, through registers: the prefix
+        // matrix may extend over Ublk
         {
             const int d = 2 * rp, o = 2 * k;
-            for (int f = t; f < d * d; f += kThreads) {
-                const int i = f / d, j = f - i * d;
-                if (j >= i) Ub[pidx(d, i, j)] = X[pidx(D0, o + i, o + j)];
+            constexpr int kDm = 2 * (kS + Lay::R), kPer = (kDm * kDm + kThreads - 1) / kThreads;
+            T tmp[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int f = t + q * kThreads, i = f / d, j = f - (f / d) * d;
+                if (f < d * d && j >= i) tmp[q] = X[pidx(D0, o + i, o + j)];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int f = t + q * kThreads, i = f / d, j = f - (f / d) * d;
+                if (f < d * d && j >= i) Ub[pidx(d, i, j)] = tmp[q];
             }
         }
         __syncthreads();
@@ -573,7 +610,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             }
             __syncthreads();
             Tau tsub = Tau(1.0);
-            for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Wb, &s_flag);
+            for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Qb, &s_flag);
             // level 0 of the expansion: the trailing 2r x 2r block, packed into X
             {
                 const int d = 2 * r, o = 2 * kk;
@@ -594,30 +631,46 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const int d = 2 * (r - l), dc = d - 2;
                 const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
                 const int np = 1 << l;
-                // (a) the parents' inverse pivots and the children's prefactors
+                // (a) the parents' pivot quantities and the children's prefactors
                 if (t < np) {
                     const T *P = src + t * sstr;
                     const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
-                    const T det = det2(p00, p01, p11);
-                    const T rs = rsq<T>(det);
-                    const T inv = rs * rs;
-                    Qb[3 * t] = p11 * inv;
-                    Qb[3 * t + 1] = -p01 * inv;
-                    Qb[3 * t + 2] = p00 * inv;
+                    T rs;
+                    int bad;
+                    if constexpr (Prec<T>::fixed) {
+                        const fx_piv v = fx_pivot(p00, p01, p11);
+                        Qb[3 * t] = v.a;
+                        Qb[3 * t + 1] = v.r10;
+                        Qb[3 * t + 2] = v.b;
+                        rs = v.rs;
+                        bad = fx_chol_bad(p00, v.x, v.rs);
+                    } else {
+                        const T det = det2(p00, p01, p11);
+                        rs = rsq<T>(det);
+                        const T inv = rs * rs;
+                        Qb[3 * t] = p11 * inv;
+                        Qb[3 * t + 1] = -p01 * inv;
+                        Qb[3 * t + 2] = p00 * inv;
+                        bad = pivot_bad(det);
+                    }
                     tdst[2 * t] = tsrc[t];
                     tdst[2 * t + 1] = tsrc[t] * to_node(rs);
-                    const int bad = pivot_bad(det);
                     if (bad) atomicOr(&s_flag, bad);
                 }
                 __syncthreads();
-                // (b) W = B P^{-1} for every parent, dc rows each
+                // (b) the rows of W = B P^{-1} (fixed point: of U = B R^{-T}), dc per parent
                 for (int f = t; f < np * dc; f += kThreads) {
                     const int cp = f / dc, i = f - cp * dc;
                     const T *P = src + cp * sstr;
                     const T b0 = P[pidx(d, 0, i + 2)], b1 = P[pidx(d, 1, i + 2)];
-                    const T q00 = Qb[3 * cp], q01 = Qb[3 * cp + 1], q11 = Qb[3 * cp + 2];
-                    Wb[2 * f] = dot2(q00, b0, q01, b1);
-                    Wb[2 * f + 1] = dot2(q01, b0, q11, b1);
+                    if constexpr (Prec<T>::fixed) {
+                        const fx_piv v{Qb[3 * cp], Qb[3 * cp + 1], Qb[3 * cp + 2], fx_zero(), fx_zero()};
+                        fx_urow(v, b0, b1, Wb[3 * f], Wb[3 * f + 1], Wb[3 * f + 2]);
+                    } else {
+                        const T q00 = Qb[3 * cp], q01 = Qb[3 * cp + 1], q11 = Qb[3 * cp + 2];
+                        Wb[2 * f] = dot2(q00, b0, q01, b1);
+                        Wb[2 * f + 1] = dot2(q01, b0, q11, b1);
+                    }
                 }
                 __syncthreads();
                 // (c) both children of every parent: the exclude child is the parent's
@@ -629,10 +682,16 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int ij = dtab[e];
                     const int i = ij & 0xff, j = ij >> 8;
                     const T *P = src + cp * sstr;
-                    const T *Wr = Wb + 2 * (cp * dc + i);
                     const T v = P[pidx(d, i + 2, j + 2)];
                     dst[(2 * cp) * dstr + e] = v;
-                    dst[(2 * cp + 1) * dstr + e] = fms2(v, Wr[0], P[pidx(d, 0, j + 2)], Wr[1], P[pidx(d, 1, j + 2)]);
+                    if constexpr (Prec<T>::fixed) {
+                        const T *Ui = Wb + 3 * (cp * dc + i), *Uj = Wb + 3 * (cp * dc + j);
+                        dst[(2 * cp + 1) * dstr + e] = fx_sym_update(v, Ui[0], Ui[1], Ui[2], Uj[0], Uj[1], Uj[2]);
+                    } else {
+                        const T *Wr = Wb + 2 * (cp * dc + i);
+                        dst[(2 * cp + 1) * dstr + e] =
+                            fms2(v, Wr[0], P[pidx(d, 0, j + 2)], Wr[1], P[pidx(d, 1, j + 2)]);
+                    }
                     e += rstep;
                     cp += qstep;
                     if (e >= Ec) {
