@@ -269,3 +269,64 @@ __device__ __forceinline__ fx fx_sym_update(const fx &c, const fx &ui0, const fx
                                             const fx &uj0, const fx &uj1, const fx &tj) {
     return ((c + ti) + tj) - (fx_mul_uu(ui0, uj0) + fx_mul_uu(ui1, uj1));
 }
+
+// ---- prefactors as mantissa x 2^e, and exponent-aligned sums -------------------------
+// The breadth-first prefactors (products of up to seven det^{-1/2} in [1/2, 16]) leave
+// the fixed-point range, so they are kept as m 2^e with m in [1, 2).
+struct __align__(16) fxe {
+    fx m;
+    int e;
+};
+__device__ __forceinline__ fxe fxe_one() { return fxe{fx_one(), 0}; }
+// a >> k for 0 <= k <= 31 (arithmetic)
+__device__ __forceinline__ fx fx_shr_small(const fx &a, int k) {
+    fx r;
+    r.w[0] = __funnelshift_r(a.w[0], a.w[1], k);
+    r.w[1] = __funnelshift_r(a.w[1], a.w[2], k);
+    r.w[2] = __funnelshift_r(a.w[2], a.w[3], k);
+    r.w[3] = (uint32_t)((int32_t)a.w[3] >> k);
+    return r;
+}
+// a << k for 0 <= k <= 31
+__device__ __forceinline__ fx fx_shl_small(const fx &a, int k) {
+    fx r;
+    r.w[3] = __funnelshift_l(a.w[2], a.w[3], k);
+    r.w[2] = __funnelshift_l(a.w[1], a.w[2], k);
+    r.w[1] = __funnelshift_l(a.w[0], a.w[1], k);
+    r.w[0] = a.w[0] << k;
+    return r;
+}
+// a >> s for any s >= 0 (arithmetic; s >= 127 leaves the sign)
+__device__ __forceinline__ fx fx_shr(const fx &a, int s) {
+    const uint32_t sg = (uint32_t)((int32_t)a.w[3] >> 31);
+    if (s > 127) s = 127;
+    const int q = s >> 5, b = s & 31;
+    // limb shift by q (selects, no indexed local memory), then the bit shift
+    const uint32_t w0 = q == 0 ? a.w[0] : q == 1 ? a.w[1] : q == 2 ? a.w[2] : a.w[3];
+    const uint32_t w1 = q == 0 ? a.w[1] : q == 1 ? a.w[2] : q == 2 ? a.w[3] : sg;
+    const uint32_t w2 = q == 0 ? a.w[2] : q == 1 ? a.w[3] : sg;
+    const uint32_t w3 = q == 0 ? a.w[3] : sg;
+    return fx_shr_small(fx{{w0, w1, w2, w3}}, b);
+}
+// m r 2^e renormalised, for r in (0, 32)
+__device__ __forceinline__ fxe fxe_mul(const fxe &a, const fx &r) {
+    const fx p = fx_mul_uu(a.m, r);  // (0, 64)
+    const int k = (31 - __clz((int)p.w[3])) - 16;  // floor(log2 p), in [-2, 5] for p >= 1/4
+    fxe o;
+    o.m = k >= 0 ? fx_shr_small(p, k) : fx_shl_small(p, -k);
+    o.e = a.e + k;
+    return o;
+}
+// m 2^e as a double-double
+__device__ __forceinline__ dd fxe_to_dd(const fxe &a) {
+    const dd v = fx_to_dd(a.m);
+    const double s = ldexp(1.0, a.e);
+    return dd(v.hi * s, v.lo * s);
+}
+__device__ __forceinline__ fx fx_shfl_xor(const fx &a, int mask) {
+    fx r;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.w[k] = __shfl_xor_sync(0xffffffffu, a.w[k], mask);
+    return r;
+}
+__device__ __forceinline__ fx fx_neg_if(const fx &a, bool neg) { return neg ? -a : a; }

@@ -78,7 +78,7 @@ template <> struct Prec<fx> {
     static constexpr int B = 2, idx = GBS_FX;
     using Tau = dd;
     using Abs = float;
-    using Node = dd;
+    using Node = fxe;  // prefactors m 2^e
     static constexpr bool fixed = true;
     static constexpr int wrow = 3;  // offset rows (u'0, u'1, t) of U = B R^{-T}
     static constexpr double u = 7.888609052210118e-31, u_sum = 1.2325951644078309e-32;
@@ -102,7 +102,11 @@ template <> __device__ __forceinline__ fx konst<fx>(double v) { return fx_from_d
 __device__ __forceinline__ float to_node(float x) { return x; }
 __device__ __forceinline__ double to_node(double x) { return x; }
 __device__ __forceinline__ dd to_node(dd x) { return x; }
-__device__ __forceinline__ dd to_node(fx x) { return fx_to_dd(x); }
+// a child's prefactor: the parent's times det^{-1/2} of the parent's pivot
+template <typename N, typename T> __device__ __forceinline__ N node_times(const N &p, const T &rs) { return p * to_node(rs); }
+template <> __device__ __forceinline__ fxe node_times<fxe, fx>(const fxe &p, const fx &rs) { return fxe_mul(p, rs); }
+template <typename N> __device__ __forceinline__ N node_one() { return N(1.0); }
+template <> __device__ __forceinline__ fxe node_one<fxe>() { return fxe_one(); }
 // product of two non-negative factors
 template <typename T> __device__ __forceinline__ T mul_pos(T a, T b) { return a * b; }
 template <> __device__ __forceinline__ fx mul_pos<fx>(fx a, fx b) { return fx_mul_uu(a, b); }
@@ -139,11 +143,6 @@ __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(dd h, dd l, double &oh, double &ol) { oh = h.hi; ol = h.lo + l.hi; }
-__device__ __forceinline__ void sum_parts(fx h, fx, double &oh, double &ol) {
-    const dd v = fx_to_dd(h);
-    oh = v.hi;
-    ol = v.lo;
-}
 
 // ---- shared-memory layout ----------------------------------------------------
 // X and Y alternate as source and destination of the breadth-first levels; the
@@ -476,6 +475,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     uint16_t *dec = (uint16_t *)(smem + Lay::off_dec);
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
+    __shared__ fx s_vred[kThreads / 32];    // fixed point: per-warp aligned sums
+    __shared__ float s_ared[kThreads / 32];
+    __shared__ int s_ered[kThreads / 32];
     T *Ub = (T *)(smem + Lay::off_U);
     T *Wb = (T *)(smem + Lay::off_W);
     T *Qb = (T *)(smem + Lay::off_Q);
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int i = f / d, j = f - i * d;
                     if (j >= i) X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
                 }
-                if (t == 0) tauX[0] = Node(1.0);
+                if (t == 0) tauX[0] = node_one<Node>();
             }
             __syncthreads();
             // breadth-first expansion of L_eff levels: node c at level l + 1 is child
@@ -654,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                         bad = pivot_bad(det);
                     }
                     tdst[2 * t] = tsrc[t];
-                    tdst[2 * t + 1] = tsrc[t] * to_node(rs);
+                    tdst[2 * t + 1] = node_times(tsrc[t], rs);
                     if (bad) atomicOr(&s_flag, bad);
                 }
                 __syncthreads();
@@ -702,7 +704,59 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 __syncthreads();
             }
             // register-resident bottom B levels, one node per thread
-            if (t < (1 << L_eff)) {
+            if constexpr (Prec<T>::fixed) {
+                // each thread's subtree sum relative to its prefactor m 2^e, then one
+                // exponent-aligned fixed-point sum over the CTA: a single conversion to
+                // double-double per sub-unit
+                fx v = fx_zero();
+                int e = -(1 << 20);
+                float ab = 0.0f;
+                if (t < (1 << L_eff)) {
+                    const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
+                    const Node tn = ((L_eff & 1) ? tauY : tauX)[t];
+                    const int nreal = n - (n_eff - B);
+                    Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
+                    SmemMat<T, B> A{node};
+                    dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc);
+                    const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
+                    v = fx_neg_if(fx_mul_su(acc.hi, tn.m), excl & 1);   // |v| < 2^11
+                    e = tn.e;
+                    ab = acc.abs * ((float)(int32_t)tn.m.w[3] * (1.0f / 65536.0f));
+                    if (acc.bad) atomicOr(&s_flag, acc.bad);
+                }
+                int em = __reduce_max_sync(0xffffffffu, e);
+                if ((t & 31) == 0) s_ered[t >> 5] = em;
+                __syncthreads();
+                em = s_ered[0];
+#pragma unroll
+                for (int w = 1; w < kThreads / 32; ++w) em = max(em, s_ered[w]);
+                // align to 2^(em + 4): the CTA sum of 128 terms stays below 2^14
+                v = fx_shr(v, em - e + 4);
+                ab = ldexpf(ab, max(e - em, -126));
+#pragma unroll
+                for (int off = 16; off; off >>= 1) {
+                    v = v + fx_shfl_xor(v, off);
+                    ab += __shfl_xor_sync(0xffffffffu, ab, off);
+                }
+                if ((t & 31) == 0) {
+                    s_vred[t >> 5] = v;
+                    s_ared[t >> 5] = ab;
+                }
+                __syncthreads();
+                if (t == 0) {
+                    fx S = s_vred[0];
+                    float AB = s_ared[0];
+#pragma unroll
+                    for (int w = 1; w < kThreads / 32; ++w) {
+                        S = S + s_vred[w];
+                        AB += s_ared[w];
+                    }
+                    const dd sv = fx_to_dd(S);
+                    const double sc = ldexp(1.0, em + 4);
+                    unit_add(u_hi, u_lo, tsub, sv.hi * sc, sv.lo * sc);
+                    u_abs += tau_abs(tsub) * ldexp((double)AB, em);
+                }
+            } else if (t < (1 << L_eff)) {
                 const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
                 const Node tau_node = ((L_eff & 1) ? tauY : tauX)[t];
                 const int nreal = n - (n_eff - B);
@@ -716,7 +770,6 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 unit_add(u_hi, u_lo, sc, sh, sl);
                 u_abs += tau_abs(sc) * to_hi(acc.abs);
                 if (is_nan(acc.abs) || is_nan(tau_node)) atomicOr(&s_flag, 1);
-                if (acc.bad) atomicOr(&s_flag, acc.bad);
             }
             __syncthreads();   // X / Y are rewritten by the next sub-unit
         }
