@@ -53,6 +53,28 @@ def schur_flops(n: int) -> float:
     return tot
 
 
+def approx_unit_flops(n: int, j: int) -> float:
+    """Algorithmic real flops of one (pattern, nu) unit of the approximation: the
+    sweep-operator inverse of the 2n x 2n complex symmetric I - t O_S (2n pivots, each a
+    complex multiply and multiply-subtract on (2n)^2 / 2 entries: 14 flops) and the group
+    minors det(G_WW)^{-1/2} for every |W| <= j (LDL^T with complex pivots and inverse
+    square roots: 60, 240 and 300 flops for w = 1, 2, 3; w = 4 reuses its triple's
+    factors through a 2x2 Schur block: 100)."""
+    N = 2 * n
+    f = 14.0 * N * N * N / 2
+    per = {1: 60, 2: 240, 3: 300, 4: 100}
+    for w in range(1, j + 1):
+        f += math.comb(n, w) * per[w]
+    return f
+
+
+def adjoint_flops(n: int) -> float:
+    """Algorithmic flops of the exact adjoint over the 2^n subsets Z of S: per subset a
+    Cholesky of A_Z ((2z)^3 / 3), its inverse from the factor (2 (2z)^3 / 3) and the
+    weighted accumulation into Gbar ((2z)^2)."""
+    return float(sum(math.comb(n, z) * ((2 * z) ** 3 + (2 * z) ** 2) for z in range(n + 1)))
+
+
 def workload(name: str, rank: int, world: int):
     c = g.CONFIGS[name]
     U, r = c.unitary(), c.squeezing()
@@ -330,12 +352,178 @@ def run_gpu(args):
         errs[pk] = {"max_abs_dlogP": float(d.max()) if d.size else None,
                     "median_abs_dlogP": float(np.median(d)) if d.size else None,
                     "status_ok_fraction_all_patterns": float((rv["status"] == 0).mean())}
+    if args.workloads == "all":
+        line["workloads"] = run_workloads(dev, stream, meas, fp32_peak)
     line["error_vs_oracle"] = {"reference": "double-double oracle",
                                "patterns_checked": int(sample.size),
                                "clicks_checked": [int(n[sample].min()), int(n[sample].max())] if sample.size else None,
                                "per_precision": errs}
     print(json.dumps(line))
     return 0
+
+
+def run_workloads(dev, stream, meas, fp32_peak):
+    """The other four workloads, one pass each (one GPU): timings with CUDA events on the
+    library's stream, the dominant kernel's roofline, accuracy against the oracle on a
+    bounded sample, and the approximation against the exact sum where the exact sum is
+    run (reported, not gated).  A context of its own (no reservation: workspaces grow)."""
+    import torch
+    import oracle
+    from oracle import approx as oap
+    from oracle import grad as ograd
+    from paper_2106_01445_gb300.api import Context, LogProbClements, patterns_tensor
+    ctx = Context(dev.index, stream)
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.timing(True)
+        ctx.timing_read(reset=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, launches = ctx.timing_read(reset=True)
+        ctx.timing(False)
+        return e0.elapsed_time(e1) / reps, kms / max(launches, 1), r
+
+    def host(out):
+        return {k: v.cpu().numpy() for k, v in out.items()}
+
+    def nclicks(pats):
+        return np.array([len(g.pattern_modes(p)) for p in pats])
+
+    res = {}
+    # ---- 8 modes, all 256 patterns: latency of one call; sum of P; every pattern vs the oracle
+    c = g.CONFIGS["m8_all"]
+    U, r, pats = c.unitary(), c.squeezing(), c.patterns()
+    st = ctx.build_state(U, r, c.eta)
+    pd = patterns_tensor(pats, dev)
+    ref = oracle.prob_exact(oracle.build_state(U, r, c.eta), pats, dd=True)["logP"]
+    e = {}
+    for prec in ("fx", "fp64"):
+        ms, _, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, precision=prec), reps=20)
+        lp = host(out)["logP"]
+        e[prec] = {"ms_per_call": ms, "sum_P_minus_1": float(np.exp(lp).sum() - 1.0),
+                   "max_abs_dlogP_vs_dd_oracle": float(np.abs(lp - ref).max())}
+    res["m8_all"] = {"patterns": len(pats), "subsets": 3 ** 8, **e}
+
+    # ---- 50 modes, 4096 patterns n = 10..40: approximation orders 2..4; exact on n <= 22
+    c = g.CONFIGS["m50_approx"]
+    U, r, pats = c.unitary(), c.squeezing(), c.patterns()
+    n = nclicks(pats)
+    st = ctx.build_state(U, r, c.eta)
+    pd = patterns_tensor(pats, dev)
+    exi = np.nonzero(n <= c.exact_n_max)[0]
+    ms_ex, kms_ex, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd[torch.as_tensor(exi, device=dev)],
+                                                precision="fx"))
+    ex = host(out)
+    sub_ex = float(sum(2.0 ** k for k in n[exi]))
+    entry = {"patterns": len(pats), "exact_fx_on_n_le_%d" % c.exact_n_max: {
+        "patterns": int(exi.size), "ms": ms_ex, "subsets_per_s": sub_ex / (ms_ex * 1e-3),
+        "status_ok_fraction": float((ex["status"] == 0).mean())}}
+    st_or = oracle.build_state(U, r, c.eta)
+    small = [i for i in np.argsort(n, kind="stable") if n[i] <= 12][:2]
+    for order in (2, 3, 4):
+        for prec in (("fp32", "fp64") if order == 2 else ("fp32",)):
+            ms, kms, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, order=order, precision=prec))
+            a = host(out)
+            units = (a["kappa"].astype(np.int64) + 1) // 2 + 1
+            fl = float(sum(u * approx_unit_flops(int(k), order) for u, k in zip(units, n)))
+            peak = fp32_peak if prec == "fp32" else meas["fp64"]
+            ok = (ex["status"] == 0) & np.isin(a["status"][exi], (0, 7))
+            rel = np.abs(np.expm1(a["logP"][exi][ok] - ex["logP"][ok]))
+            orc = []
+            for i in small:
+                lp_o, _ = oap.approx_logprob(st_or.O, st_or.logdet, c.M, g.pattern_modes(pats[i]), order)
+                orc.append(abs(a["logP"][i] - lp_o))
+            entry["order%d_%s" % (order, prec)] = {
+                "ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
+                "status_ok_fraction": float((a["status"] == 0).mean()),
+                "fit_fallback_fraction": float((a["status"] == 7).mean()),
+                "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<%s>" % (
+                    "float" if prec == "fp32" else "double"), "kernel_ms": kms, "flops": fl,
+                    "achieved_tflops": fl / (kms * 1e-3) / 1e12, "peak_tflops": peak / 1e12,
+                    "frac": fl / (kms * 1e-3) / peak},
+                "vs_exact_n_le_%d" % c.exact_n_max: {"median_rel_dP": float(np.median(rel)),
+                                                     "max_rel_dP": float(rel.max())},
+                "max_abs_dlogP_vs_oracle_approx": float(max(orc)), "oracle_patterns_n": [int(n[i]) for i in small]}
+    res["m50_approx"] = entry
+
+    # ---- 32-mode Clements mesh, 512 patterns n = 8..16: log P and its gradient
+    c = g.CONFIGS["m32_grad"]
+    th, ph = g.clements_phases(c.M, c.seed)
+    r, pats = c.squeezing(), c.patterns()
+    n = nclicks(pats)
+    pd = patterns_tensor(pats, dev)
+    rt = torch.tensor(r, device=dev, requires_grad=True)
+    et = torch.tensor(c.eta, dtype=torch.float64, device=dev, requires_grad=True)
+    tt = torch.tensor(th, device=dev, requires_grad=True)
+    pt = torch.tensor(ph, device=dev, requires_grad=True)
+    wts = torch.linspace(-1.0, 1.0, len(pats), dtype=torch.float64, device=dev)
+
+    def step():
+        lp = LogProbClements.apply(rt, et, tt, pt, pd, ctx)
+        return torch.autograd.grad((wts * lp).sum(), (rt, et, tt, pt))
+
+    step()
+    ms, _, _ = timed(step, reps=3)
+    Ud = ctx.clements_unitary(torch.as_tensor(th, device=dev), torch.as_tensor(ph, device=dev), c.M)
+    st = ctx.build_state(torch.view_as_complex(Ud.view(c.M, c.M, 2)), torch.as_tensor(r, device=dev), c.eta)
+    ms_adj, kms_adj, (dsq, _, _) = timed(lambda: ctx.grad(st["O"], st["logdet"], pd, wts))
+    fl = float(sum(adjoint_flops(int(k)) for k in n))
+    chk = [i for i in np.argsort(n, kind="stable")][:2]
+    U = g.clements_unitary(c.M, th, ph)
+    st_or = oracle.build_state(U, r, c.eta)
+    ds_gpu = ctx.grad(st["O"], st["logdet"], pd[torch.as_tensor(chk, device=dev)],
+                      torch.ones(len(chk), dtype=torch.float64, device=dev))[0].cpu().numpy()
+    ds_orc = ograd.grad_sigmaQ(st_or, pats[chk], np.ones(len(chk)))
+    res["m32_grad"] = {"patterns": len(pats), "params": 2 * len(th) + c.M + 1,
+                       "ms_forward_and_backward": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
+                       "roofline_adjoint": {"bound": "alu", "kernel": "grad_subsets_kernel (double-double)",
+                                            "kernel_ms": kms_adj, "flops": fl,
+                                            "achieved_tflops": fl / (kms_adj * 1e-3) / 1e12,
+                                            "peak_tflops": meas["dd"] / 1e12,
+                                            "frac": fl / (kms_adj * 1e-3) / meas["dd"]},
+                       "max_abs_d_dsigmaQ_vs_oracle": float(np.abs(ds_gpu - ds_orc).max()),
+                       "oracle_patterns_n": [int(n[i]) for i in chk]}
+
+    # ---- 100 modes: approximation on a slice of the 16384 patterns (n = 40..90); exact
+    # fixed point on 8 of the 64 n = 30 anchors and the approximation against it
+    c = g.CONFIGS["m100_approx"]
+    U, r = c.unitary(), c.squeezing()
+    pats = c.patterns()[:64]
+    anc = c.anchor_patterns()[:8]
+    n = nclicks(pats)
+    st = ctx.build_state(U, r, c.eta)
+    pd, ad = patterns_tensor(pats, dev), patterns_tensor(anc, dev)
+    ms_a, kms_a, out = timed(lambda: ctx.prob(st["O"], st["logdet"], ad, precision="fx"))
+    exa = host(out)
+    entry = {"slice_patterns": len(pats), "slice_clicks": [int(n.min()), int(n.max())],
+             "anchors_exact_fx": {"anchors": len(anc), "clicks": c.anchor_n, "ms": ms_a,
+                                  "subsets_per_s": len(anc) * 2.0 ** c.anchor_n / (ms_a * 1e-3),
+                                  "status_ok_fraction": float((exa["status"] == 0).mean()),
+                                  "max_err_bound": float(np.nanmax(exa["err_bound"]))}}
+    for order in (2, 3, 4):
+        ms, kms, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, order=order, precision="fp32"))
+        a = host(out)
+        units = (a["kappa"].astype(np.int64) + 1) // 2 + 1
+        fl = float(sum(u * approx_unit_flops(int(k), order) for u, k in zip(units, n)))
+        aa = host(ctx.prob(st["O"], st["logdet"], ad, order=order, precision="fp32"))
+        ok = (exa["status"] == 0) & np.isin(aa["status"], (0, 7))
+        rel = np.abs(np.expm1(aa["logP"][ok] - exa["logP"][ok]))
+        entry["order%d_fp32" % order] = {
+            "ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
+            "status_ok_fraction": float((a["status"] == 0).mean()),
+            "fit_fallback_fraction": float((a["status"] == 7).mean()),
+            "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<float>", "kernel_ms": kms,
+                                "flops": fl, "achieved_tflops": fl / (kms * 1e-3) / 1e12,
+                                "peak_tflops": fp32_peak / 1e12, "frac": fl / (kms * 1e-3) / fp32_peak},
+            "anchors_vs_exact": {"median_rel_dP": float(np.median(rel)), "max_rel_dP": float(rel.max())}}
+    res["m100_approx"] = entry
+    ctx.close()
+    return res
 
 
 def run_profile_case(args):
@@ -371,6 +559,8 @@ def main():
     ap.add_argument("--profile", choices=["sweep", "approx"], default=None,
                     help="run one kernel path twice (for ncu) instead of the benchmark")
     ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--workloads", choices=["all", "none"], default="all",
+                    help="also run one pass of the other four workloads (on rank 0)")
     ap.add_argument("--npat", type=int, default=128)
     args = ap.parse_args()
     if args.profile:

@@ -218,9 +218,10 @@ def patterns_numpy(t: torch.Tensor) -> np.ndarray:
 class LogProbClements(torch.autograd.Function):
     """log P of click patterns as a differentiable function of the squeezing r,
     the transmission eta and the mesh phases (theta, phi).  Forward: mesh
-    unitary, state build and the exact double-double sweep in libgbs; backward:
-    the double-double adjoint (gbs_grad), the state-build chain (gbs_grad_params)
-    and the reverse pass through the mesh (gbs_clements_grad).
+    unitary, state build and the exact sweep in libgbs (fixed point; double-double
+    for patterns outside its range); backward: the double-double adjoint
+    (gbs_grad), the state-build chain (gbs_grad_params) and the reverse pass
+    through the mesh (gbs_clements_grad).
 
         logP = LogProbClements.apply(r, eta, theta, phi, patterns, ctx)
     """
@@ -231,7 +232,13 @@ class LogProbClements(torch.autograd.Function):
         Ud = gbs.clements_unitary(theta, phi, M)
         rd = r.detach().to(device=gbs.device, dtype=torch.float64).contiguous()
         st = gbs.build_state(torch.view_as_complex(Ud.view(M, M, 2)), rd, float(eta), check=False)
-        out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="dd")
+        out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="fx")
+        bad = out["status"] == _lib.GBS_E_RANGE
+        if bool(bad.any()):
+            idx = torch.nonzero(bad).flatten()
+            sub = gbs.prob(st["O"], st["logdet"], patterns_tensor(patterns, gbs.device)[idx], order=0,
+                           precision="dd")
+            out["logP"][idx] = sub["logP"]
         fctx.save_for_backward(rd, theta.detach(), phi.detach(), Ud, st["O"], st["logdet"])
         fctx.gbs, fctx.eta, fctx.patterns = gbs, float(eta), patterns
         return out["logP"]
