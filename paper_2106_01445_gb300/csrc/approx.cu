@@ -28,7 +28,9 @@ namespace {
 
 constexpr int kMaxOrder = 4;
 constexpr int kMinorThreads = 256;
-constexpr int kFitThreads = 128;
+constexpr int kDftThreads = 128;
+constexpr int kSecThreads = 256;   // one warp per sector
+constexpr int kSumThreads = 128;   // one warp per pattern
 constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
 constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
@@ -54,15 +56,20 @@ template <typename R> __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> 
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 template <typename R> __device__ __forceinline__ cx<R> cinv(cx<R> a) {
-    R d = a.re * a.re + a.im * a.im;
-    return {a.re / d, -a.im / d};
+    const R d = R(1) / (a.re * a.re + a.im * a.im);
+    return {a.re * d, -a.im * d};
 }
-// principal p^{-1/2} for Re p > 0: sqrt(p) = s + i q with s = sqrt((|p| + Re p)/2), q = Im p/(2 s)
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+// principal p^{-1/2} for Re p > 0: with a = |p| and s = sqrt((a + Re p)/2) (no
+// cancellation: Re p > 0), sqrt(p) = s + i Im p / (2 s) and p^{-1/2} = (s - i Im p/(2 s)) / a;
+// two reciprocal square roots, no division
 template <typename R> __device__ __forceinline__ cx<R> crsqrt(cx<R> p) {
-    R a = hypot(p.re, p.im);
-    R s = sqrt((a + p.re) * R(0.5));
-    R q = p.im / (R(2) * s);
-    return {s / a, -q / a};
+    const R n2 = p.re * p.re + p.im * p.im;
+    const R ra = rsqrt_r(n2);
+    const R h = (n2 * ra + p.re) * R(0.5);
+    const R rh = rsqrt_r(h);
+    return {h * rh * ra, -p.im * ra * rh * R(0.5)};
 }
 __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
 __device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
@@ -77,6 +84,11 @@ struct ApproxPlan {
     int *overflow;
     double *unit_D;       // 2 (j + 1) doubles per unit: D_w(t_l), w = 0..j
     int *unit_flag;       // per pattern: non-positive pivot seen
+    long long *info;      // units, largest n, largest L, sectors (read back to size the launches)
+    long long *sec_off;   // n_pat + 1: sectors k = 0..L-1 of each pattern
+    double *pat_max;      // per pattern: largest tilted sector
+    double *sec_D;        // (kMaxOrder + 1) per sector: D_w^(k), w = 0..order
+    double *sec_part;     // per sector: fitted last point (negative: the fit fell back)
 };
 
 // log det(I - rho O_S) by Cholesky in shared memory (packed); +inf if not positive definite
@@ -188,29 +200,78 @@ __global__ void approx_scan_kernel(int n_pat, long long cap, ApproxPlan pl) {
     pl.unit_off[n_pat] = run;
     *pl.overflow = run > cap ? 1 : 0;
     *pl.total = run > cap ? 0 : run;
+    int nmax = 0, Lmax = 1;
+    long long secs = 0;
+    for (int p = 0; p < n_pat; ++p) {
+        nmax = pl.pat_n[p] > nmax ? pl.pat_n[p] : nmax;
+        Lmax = pl.pat_L[p] > Lmax ? pl.pat_L[p] : Lmax;
+        pl.sec_off[p] = secs;
+        secs += pl.pat_L[p] > 0 ? pl.pat_L[p] : 0;
+    }
+    pl.sec_off[n_pat] = secs;
+    pl.info[0] = run;
+    pl.info[1] = nmax;
+    pl.info[2] = Lmax;
+    pl.info[3] = secs;
 }
 
 // ---- minors at one nu point ------------------------------------------------------
-// unpivoted LDL^T pivots of a complex symmetric K x K matrix (packed, in registers);
-// returns prod p^{-1/2} (principal, Re p > 0 for accretive matrices)
+// unpivoted LDL^T pivots of a complex symmetric K x K matrix (packed, in registers,
+// K even); returns prod p^{-1/2}.  Every pivot of an accretive matrix has Re p > 0, so
+// |arg p| < pi/2 and the principal root of a product of two pivots is the product of
+// their principal roots: one root per pair of pivots.
 template <typename R, int K>
 __device__ __forceinline__ cx<R> ldl_rsqrt_prod(cx<R> (&a)[K * (K + 1) / 2], bool &bad) {
-    cx<R> f = mk<R>(R(1), R(0));
+    cx<R> f = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         cx<R> d = a[pidx(K, k, k)];
         if (!(d.re > R(0))) bad = true;
-        f = f * crsqrt(d);
-        cx<R> inv = cinv(d);
+        if (k & 1) f = f * crsqrt(prev * d);
+        prev = d;
+        if (k + 1 < K) {
+            cx<R> inv = cinv(d);
 #pragma unroll
-        for (int i = k + 1; i < K; ++i) {
-            cx<R> li = a[pidx(K, k, i)] * inv;
+            for (int i = k + 1; i < K; ++i) {
+                cx<R> li = a[pidx(K, k, i)] * inv;
 #pragma unroll
-            for (int j = i; j < K; ++j) a[pidx(K, i, j)] = a[pidx(K, i, j)] - li * a[pidx(K, k, j)];
+                for (int j = i; j < K; ++j) a[pidx(K, i, j)] = a[pidx(K, i, j)] - li * a[pidx(K, k, j)];
+            }
         }
     }
     return f;
 }
+
+// per-thread sums of the group terms: FP64 for FP64 minors; float-float (TwoSum) for
+// FP32 minors, which keeps the FP64 pipe out of the inner loop
+template <typename R> struct GroupAcc;
+template <> struct GroupAcc<double> {
+    double v[2 * (kMaxOrder + 1)];
+    __device__ void zero() {
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) v[w] = 0.0;
+    }
+    __device__ __forceinline__ void add(int w, cx<double> f) {
+        v[2 * w] += f.re;
+        v[2 * w + 1] += f.im;
+    }
+    __device__ __forceinline__ double get(int q) const { return v[q]; }
+};
+template <> struct GroupAcc<float> {
+    float hi[2 * (kMaxOrder + 1)], lo[2 * (kMaxOrder + 1)];
+    __device__ void zero() {
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) hi[w] = lo[w] = 0.0f;
+    }
+    __device__ __forceinline__ void two(int q, float x) {
+        const float s = hi[q] + x, bp = s - hi[q];
+        lo[q] += (hi[q] - (s - bp)) + (x - bp);
+        hi[q] = s;
+    }
+    __device__ __forceinline__ void add(int w, cx<float> f) {
+        two(2 * w, f.re);
+        two(2 * w + 1, f.im);
+    }
+    __device__ __forceinline__ double get(int q) const { return (double)hi[q] + (double)lo[q]; }
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, const double *__restrict__ O,
@@ -293,17 +354,14 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
         __syncthreads();
         // entries of G = (I - t O_S)^{-1} are minus the swept matrix
         auto g = [&](int i, int j) -> cx<R> { cx<R> v = G[pidx_any(N, i, j)]; return mk<R>(-v.re, -v.im); };
-        double acc[2 * (kMaxOrder + 1)];
-#pragma unroll
-        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) acc[w] = 0.0;
+        GroupAcc<R> acc;
+        acc.zero();
         bool bad = false;
-        // w = 1
+        // w = 1: det of the 2x2 block, one root
         if (order >= 1)
             for (int a = t; a < n; a += kMinorThreads) {
                 cx<R> m[3] = {g(2 * a, 2 * a), g(2 * a, 2 * a + 1), g(2 * a + 1, 2 * a + 1)};
-                cx<double> f = widen(ldl_rsqrt_prod<R, 2>(m, bad));
-                acc[2] += f.re;
-                acc[3] += f.im;
+                acc.add(1, ldl_rsqrt_prod<R, 2>(m, bad));
             }
         // w = 2
         if (order >= 2)
@@ -317,66 +375,53 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = i; j < 4; ++j) m[pidx(4, i, j)] = g(rr[i], rr[j]);
-                cx<double> f = widen(ldl_rsqrt_prod<R, 4>(m, bad));
-                acc[4] += f.re;
-                acc[5] += f.im;
+                acc.add(2, ldl_rsqrt_prod<R, 4>(m, bad));
             }
-        // w = 3 (and w = 4 from each triple's factorisation)
+        // w = 3, and w = 4 from each triple's factorisation.  Triples in order of their
+        // largest detector c (then b, a), so the lanes of a warp share c and with it the
+        // number n - 1 - c of fourth detectors d > c.
         if (order >= 3) {
             const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
             for (long long idx = t; idx < ntri; idx += kMinorThreads) {
-                int a = 0;
-                long long rem = idx;
-                for (;;) {
-                    long long c2 = (long long)(n - 1 - a) * (n - 2 - a) / 2;
-                    if (rem < c2) break;
-                    rem -= c2;
-                    ++a;
-                }
-                int b = a + 1;
-                for (;;) {
-                    long long c1 = n - 1 - b;
-                    if (rem < c1) break;
-                    rem -= c1;
-                    ++b;
-                }
-                int c = b + 1 + (int)rem;
+                // c: the largest with C(c, 3) <= idx; then b: the largest with C(b, 2) <= rem
+                // (FP32 estimates on the MUFU pipe, corrected exactly in integers)
+                int c = (int)cbrtf(6.0f * (float)idx);
+                while ((long long)(c + 1) * c * (c - 1) / 6 <= idx) ++c;
+                while ((long long)c * (c - 1) * (c - 2) / 6 > idx) --c;
+                const long long rem = idx - (long long)c * (c - 1) * (c - 2) / 6;
+                int b = (int)sqrtf(2.0f * (float)rem);
+                while ((long long)(b + 1) * b / 2 <= rem) ++b;
+                while ((long long)b * (b - 1) / 2 > rem) --b;
+                const int a = (int)(rem - (long long)b * (b - 1) / 2);
                 int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
-                cx<R> m[21];
+                cx<R> w6[21];
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
 #pragma unroll
-                    for (int j = i; j < 6; ++j) m[pidx(6, i, j)] = g(rr[i], rr[j]);
-                // keep the triple's LDL^T: after ldl_rsqrt_prod, m holds the updated
-                // trailing blocks; redo the factorisation explicitly to keep L and D
-                cx<R> Lf[15], Dv[6];
-                cx<R> f3 = mk<R>(R(1), R(0));
-                {
-                    cx<R> w6[21];
+                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = g(rr[i], rr[j]);
+                // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
+                cx<R> Lf[15], Dinv[6];
+                cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
 #pragma unroll
-                    for (int i = 0; i < 21; ++i) w6[i] = m[i];
+                for (int k = 0; k < 6; ++k) {
+                    cx<R> d = w6[pidx(6, k, k)];
+                    if (!(d.re > R(0))) bad = true;
+                    if (k & 1) f3 = f3 * crsqrt(prev * d);
+                    prev = d;
+                    cx<R> inv = cinv(d);
+                    Dinv[k] = inv;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        cx<R> d = w6[pidx(6, k, k)];
-                        if (!(d.re > R(0))) bad = true;
-                        Dv[k] = d;
-                        f3 = f3 * crsqrt(d);
-                        cx<R> inv = cinv(d);
+                    for (int i = k + 1; i < 6; ++i) {
+                        cx<R> li = w6[pidx(6, k, i)] * inv;
+                        Lf[pidx(5, k, i - 1)] = li;
 #pragma unroll
-                        for (int i = k + 1; i < 6; ++i) {
-                            cx<R> li = w6[pidx(6, k, i)] * inv;
-                            Lf[pidx(5, k, i - 1)] = li;  // L[i][k], k < i
-#pragma unroll
-                            for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = w6[pidx(6, i, j)] - li * w6[pidx(6, k, j)];
-                        }
+                        for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = w6[pidx(6, i, j)] - li * w6[pidx(6, k, j)];
                     }
                 }
-                cx<double> f3d = widen(f3);
-                acc[6] += f3d.re;
-                acc[7] += f3d.im;
+                acc.add(3, f3);
                 if (order >= 4)
                     for (int d4 = c + 1; d4 < n; ++d4) {
-                        // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2)
+                        // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2); det S^{-1/2}
                         cx<R> y0[6], y1[6];
 #pragma unroll
                         for (int i = 0; i < 6; ++i) {
@@ -392,27 +437,29 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
                         cx<R> s00 = g(2 * d4, 2 * d4), s01 = g(2 * d4, 2 * d4 + 1), s11 = g(2 * d4 + 1, 2 * d4 + 1);
 #pragma unroll
                         for (int k = 0; k < 6; ++k) {
-                            cx<R> di = cinv(Dv[k]);
-                            cx<R> z0 = y0[k] * di, z1 = y1[k] * di;
+                            const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
                             s00 = s00 - z0 * y0[k];
                             s01 = s01 - z0 * y1[k];
                             s11 = s11 - z1 * y1[k];
                         }
-                        cx<R> m2[3] = {s00, s01, s11};
-                        cx<double> f4 = widen(f3 * ldl_rsqrt_prod<R, 2>(m2, bad));
-                        acc[8] += f4.re;
-                        acc[9] += f4.im;
+                        // pivots s00 and det / s00 of the accretive block: Re > 0 each
+                        const cx<R> det = s00 * s11 - s01 * s01;
+                        if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
+                        acc.add(4, f3 * crsqrt(det));
                     }
             }
         }
         if (bad) s_bad = 1;
         // deterministic block reduction of the (j + 1) complex sums
+        double accd[2 * (kMaxOrder + 1)];
+#pragma unroll
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) accd[w] = w < 2 ? 0.0 : acc.get(w);
 #pragma unroll
         for (int w = 2; w < 2 * (kMaxOrder + 1); ++w)
-            for (int off = 16; off; off >>= 1) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], off);
+            for (int off = 16; off; off >>= 1) accd[w] += __shfl_xor_sync(0xffffffffu, accd[w], off);
         if ((t & 31) == 0)
 #pragma unroll
-            for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) red[t >> 5][w] = acc[w];
+            for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) red[t >> 5][w] = accd[w];
         __syncthreads();
         if (t == 0) {
             const cx<double> z = mk<double>(s_zs[0], s_zs[1]);
@@ -436,21 +483,30 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
 }
 
 // ---- per-sector fit (maximum-entropy dual, damped Newton) ----------------------------
+// One warp per sector: the lanes share the support points of the sums; every lane then
+// takes the same Newton step from the same (broadcast) sums.
+__device__ __forceinline__ double warp_sum_bcast(double v) {
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
 // support x_s = v_s / n for v in [v0, n-1]; moments m (m_0 = 1); J + 1 coefficients
-__device__ bool maxent_fit(int v0, int n, int J, const double *m, double *a) {
+__device__ bool maxent_fit_warp(int v0, int n, int J, const double *m, double *a, int lane) {
     const int S = n - v0;
     auto phi_grad = [&](const double *aa, double *g, double *H, double &phi) {
         double pw[2 * kMaxOrder + 1];
         for (int q = 0; q <= 2 * J; ++q) pw[q] = 0.0;
-        phi = 0.0;
-        for (int s = 0; s < S; ++s) {
+        double ph = 0.0;
+        for (int s = lane; s < S; s += 32) {
             double x = (double)(v0 + s) / n, f = 0.0, xp = 1.0;
             for (int i = 0; i <= J; ++i) { f += aa[i] * xp; xp *= x; }
             double q = exp(-f);
-            phi += q;
+            ph += q;
             xp = 1.0;
             for (int i = 0; i <= 2 * J; ++i) { pw[i] += xp * q; xp *= x; }
         }
+        phi = warp_sum_bcast(ph);
+        for (int i = 0; i <= 2 * J; ++i) pw[i] = warp_sum_bcast(pw[i]);
         for (int i = 0; i <= J; ++i) {
             phi += aa[i] * m[i];
             if (g) g[i] = m[i] - pw[i];
@@ -531,60 +587,68 @@ __device__ __forceinline__ double stirling2(int i, int w) {
     return tab[i][w];
 }
 
-__global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int order, double sector_eps,
-                                                               const double *__restrict__ logdet,
-                                                               ApproxPlan pl, double *__restrict__ logP,
-                                                               double *__restrict__ kappa,
-                                                               double *__restrict__ err_bound,
-                                                               int32_t *__restrict__ status) {
-    extern __shared__ double fsm[];
+// inverse DFT of one pattern's tables (real: O is real, so D(conj t) = conj D(t)):
+//   D_w^(k) = (1/L) sum_l D_w(t_l) e^{-2 pi i k l / L},  one CTA per pattern
+__global__ void __launch_bounds__(kDftThreads) approx_dft_kernel(int order, ApproxPlan pl) {
+    extern __shared__ double tw[];  // cos, sin (2 pi m / L), m < L
+    __shared__ double red[kDftThreads / 32];
     const int p = blockIdx.x, t = threadIdx.x;
     const int n = pl.pat_n[p], L = pl.pat_L[p];
-    __shared__ double s_max;
-    __shared__ int s_fallback;
-    if (n < 0 || *pl.overflow) {
-        if (t == 0) {
-            logP[p] = nan("");
-            if (kappa) kappa[p] = nan("");
-            if (err_bound) err_bound[p] = nan("");
-            if (status) status[p] = n < 0 ? GBS_E_INVALID : GBS_E_NOMEM;
-        }
-        return;
-    }
-    const int K = L - 1, H = L / 2;
-    double *D = fsm;                       // (order + 1) x (K + 1) sector tables
-    double *part = fsm + (order + 1) * (K + 1);  // K + 1 fitted last points
+    if (n < 0 || L <= 0 || *pl.overflow) return;
+    const int H = L / 2;
+    for (int m = t; m < L; m += kDftThreads) sincospi(2.0 * (double)m / (double)L, &tw[2 * m + 1], &tw[2 * m]);
+    __syncthreads();
     const double *U = pl.unit_D + (size_t)pl.unit_off[p] * 2 * (kMaxOrder + 1);
-    // inverse DFT (real coefficients; conjugate symmetry of the real matrix O)
-    for (int idx = t; idx < (order + 1) * (K + 1); idx += kFitThreads) {
-        int w = idx / (K + 1), k = idx - w * (K + 1);
+    double *D = pl.sec_D + (size_t)pl.sec_off[p] * (kMaxOrder + 1);
+    double mx = 0.0;
+    for (int idx = t; idx < (order + 1) * L; idx += kDftThreads) {
+        const int k = idx / (order + 1), w = idx - k * (order + 1);
         double s = U[2 * w];  // l = 0
+        int m = 0;            // k l mod L
         for (int l = 1; l <= H; ++l) {
-            double sn, cs;
-            sincospi(2.0 * (double)(((long long)k * l) % L) / (double)L, &sn, &cs);
+            m += k;
+            if (m >= L) m -= L;
             const double re = U[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w];
             const double im = U[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w + 1];
-            double term = re * cs + im * sn;       // Re(D(t_l) e^{-i 2 pi k l / L})
+            const double term = re * tw[2 * m] + im * tw[2 * m + 1];  // Re(D(t_l) e^{-i 2 pi k l / L})
             s += (2 * l == L) ? term : 2.0 * term;
         }
-        D[w * (K + 1) + k] = s / L;
+        D[(size_t)k * (kMaxOrder + 1) + w] = s / L;
+        if (w == 0) mx = fmax(mx, s / L);
     }
+    for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((t & 31) == 0) red[t >> 5] = mx;
     __syncthreads();
     if (t == 0) {
-        double mx = 0.0;
-        for (int k = 0; k <= K; ++k) mx = fmax(mx, D[k]);
-        s_max = mx;
-        s_fallback = 0;
+        for (int w = 1; w < kDftThreads / 32; ++w) mx = fmax(mx, red[w]);
+        pl.pat_max[p] = mx;
     }
-    __syncthreads();
-    const double floor_ = sector_eps * s_max;
-    for (int k = t; k <= K; k += kFitThreads) {
+}
+
+// one warp per (pattern, sector k): factorial moments -> raw moments (Stirling numbers)
+// -> maximum-entropy fit on the support v in [max(0, n - k), n - 1] -> the last point
+__global__ void __launch_bounds__(kSecThreads) approx_sector_fit_kernel(int n_pat, int order, double sector_eps,
+                                                                      ApproxPlan pl) {
+    const int lane = threadIdx.x & 31;
+    const long long nsec = pl.sec_off[n_pat];
+    const long long nwarps = (long long)gridDim.x * (kSecThreads / 32);
+    if (*pl.overflow) return;
+    for (long long gs = (long long)blockIdx.x * (kSecThreads / 32) + (threadIdx.x >> 5); gs < nsec; gs += nwarps) {
+        // the pattern whose sector range holds gs (the last with sec_off <= gs)
+        int lo = 0, hi = n_pat;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pl.sec_off[mid] <= gs) lo = mid; else hi = mid;
+        }
+        const int p = lo, n = pl.pat_n[p];
+        const int k = (int)(gs - pl.sec_off[p]);
+        const double *Dk = pl.sec_D + (size_t)gs * (kMaxOrder + 1);
+        const double D0 = Dk[0];
         double val = 0.0;
         bool fell = false;
-        const double D0 = D[k];
         if (n == 0) {
             val = (k == 0) ? D0 : 0.0;
-        } else if (k >= n && D0 >= floor_ && D0 > 0.0) {
+        } else if (k >= n && D0 >= sector_eps * pl.pat_max[p] && D0 > 0.0) {
             const int v0 = n - k > 0 ? n - k : 0;
             const int S = n - v0;
             const int Jmax = order < S - 1 ? order : S - 1;
@@ -592,7 +656,7 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
             for (int i = 0; i <= Jmax; ++i) {
                 double s = 0.0, fw = 1.0;
                 for (int w = 0; w <= i; ++w) {
-                    s += stirling2(i, w) * fw * D[w * (K + 1) + k];
+                    s += stirling2(i, w) * fw * Dk[w];
                     fw *= (w + 1);
                 }
                 mu[i] = s;
@@ -602,7 +666,7 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
                 double m[kMaxOrder + 1], a[kMaxOrder + 1];
                 double np = 1.0;
                 for (int i = 0; i <= J; ++i) { m[i] = mu[i] / np / mu[0]; np *= n; }
-                if (maxent_fit(v0, n, J, m, a)) {
+                if (maxent_fit_warp(v0, n, J, m, a, lane)) {
                     val = mu[0] * exp(-a[0]);
                     done = true;
                     if (J != Jmax) fell = true;
@@ -610,29 +674,50 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
             }
             if (!done) fell = true;
         }
-        part[k] = fell ? -val : val;   // the sign marks a sector that fell back
+        if (lane == 0) pl.sec_part[gs] = fell ? -val : val;   // the sign marks a fallback
     }
-    __syncthreads();
-    if (t == 0) {
-        // sum_k part_k rho^{-k} in logs (the tables are tilted by rho^k)
-        const double lr = log(pl.pat_rho[p]);
-        double top = -INFINITY;
-        for (int k = 0; k <= K; ++k)
-            if (part[k] != 0.0) top = fmax(top, log(fabs(part[k])) - k * lr);
-        double s = 0.0, sf = 0.0;
-        for (int k = 0; k <= K; ++k)
-            if (part[k] != 0.0) {
-                double w = exp(log(fabs(part[k])) - k * lr - top);
-                s += w;
-                if (part[k] < 0.0) sf += w;
-            }
-        s_fallback = sf >= kFlagShare * s;
+}
+
+// per pattern (one warp): sum_k part_k rho^{-k} in logs (the tables are tilted by rho^k)
+__global__ void __launch_bounds__(kSumThreads) approx_sum_kernel(int n_pat, const double *__restrict__ logdet,
+                                                               ApproxPlan pl, double *__restrict__ logP,
+                                                               double *__restrict__ kappa,
+                                                               double *__restrict__ err_bound,
+                                                               int32_t *__restrict__ status) {
+    const int p = blockIdx.x * (kSumThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (p >= n_pat) return;
+    const int n = pl.pat_n[p], L = pl.pat_L[p];
+    if (n < 0 || *pl.overflow) {
+        if (lane == 0) {
+            logP[p] = nan("");
+            if (kappa) kappa[p] = nan("");
+            if (err_bound) err_bound[p] = nan("");
+            if (status) status[p] = n < 0 ? GBS_E_INVALID : GBS_E_NOMEM;
+        }
+        return;
+    }
+    const double *part = pl.sec_part + pl.sec_off[p];
+    const double lr = log(pl.pat_rho[p]);
+    double top = -INFINITY;
+    for (int k = lane; k < L; k += 32)
+        if (part[k] != 0.0) top = fmax(top, log(fabs(part[k])) - k * lr);
+    for (int off = 16; off; off >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, off));
+    double s = 0.0, sf = 0.0;
+    for (int k = lane; k < L; k += 32)
+        if (part[k] != 0.0) {
+            const double w = exp(log(fabs(part[k])) - k * lr - top);
+            s += w;
+            if (part[k] < 0.0) sf += w;
+        }
+    s = warp_sum_bcast(s);
+    sf = warp_sum_bcast(sf);
+    if (lane == 0) {
         logP[p] = s > 0.0 ? -0.5 * (*logdet) + top + log(s) : -INFINITY;
-        if (kappa) kappa[p] = (double)K;
+        if (kappa) kappa[p] = (double)(L - 1);
         if (err_bound) err_bound[p] = nan("");
         int st = GBS_OK;
         if (pl.unit_flag[p]) st = GBS_E_NOT_SPD;
-        else if (s_fallback) st = GBS_E_FIT;
+        else if (sf >= kFlagShare * s) st = GBS_E_FIT;
         if (status) status[p] = st;
     }
 }
@@ -640,26 +725,32 @@ __global__ void __launch_bounds__(kFitThreads) approx_fit_kernel(int n_pat, int 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct ApproxOffsets {
-    size_t counter, total, overflow, pat_n, pat_L, pat_rho, unit_off, unit_flag, unit_D, end;
+    size_t counter, total, overflow, info, pat_n, pat_L, pat_rho, unit_off, unit_flag, sec_off, pat_max,
+        unit_D, sec_D, sec_part, end;
 };
 
-ApproxOffsets approx_offsets(int n_pat, long long units) {
+ApproxOffsets approx_offsets(int n_pat, long long units, long long secs = 0) {
     ApproxOffsets o;
     o.counter = 0;
     o.total = 8;
     o.overflow = 16;
-    o.pat_n = align256(20);
+    o.info = 24;
+    o.pat_n = align256(56);
     o.pat_L = align256(o.pat_n + 4 * (size_t)n_pat);
     o.pat_rho = align256(o.pat_L + 4 * (size_t)n_pat);
     o.unit_off = align256(o.pat_rho + 8 * (size_t)n_pat);
     o.unit_flag = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
-    o.unit_D = align256(o.unit_flag + 4 * (size_t)n_pat);
-    o.end = o.unit_D + 8 * 2 * (kMaxOrder + 1) * (size_t)units;
+    o.sec_off = align256(o.unit_flag + 4 * (size_t)n_pat);
+    o.pat_max = align256(o.sec_off + 8 * ((size_t)n_pat + 1));
+    o.unit_D = align256(o.pat_max + 8 * (size_t)n_pat);
+    o.sec_D = align256(o.unit_D + 8 * 2 * (kMaxOrder + 1) * (size_t)units);
+    o.sec_part = align256(o.sec_D + 8 * (kMaxOrder + 1) * (size_t)secs);
+    o.end = o.sec_part + 8 * (size_t)secs;
     return o;
 }
 
-ApproxPlan approx_plan_from(void *ws, int n_pat) {
-    ApproxOffsets o = approx_offsets(n_pat, 0);
+ApproxPlan approx_plan_from(void *ws, int n_pat, long long units = 0, long long secs = 0) {
+    ApproxOffsets o = approx_offsets(n_pat, units, secs);
     char *b = (char *)ws;
     ApproxPlan pl;
     pl.total = (long long *)(b + o.total);
@@ -670,15 +761,19 @@ ApproxPlan approx_plan_from(void *ws, int n_pat) {
     pl.unit_off = (long long *)(b + o.unit_off);
     pl.unit_flag = (int *)(b + o.unit_flag);
     pl.unit_D = (double *)(b + o.unit_D);
+    pl.info = (long long *)(b + o.info);
+    pl.sec_off = (long long *)(b + o.sec_off);
+    pl.pat_max = (double *)(b + o.pat_max);
+    pl.sec_D = (double *)(b + o.sec_D);
+    pl.sec_part = (double *)(b + o.sec_part);
     return pl;
 }
 
 template <typename R>
 int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status) {
-    // shared memory: the packed complex inverse of the largest pattern allowed
+    // patterns up to this size are taken
     const int nmax_smem = sizeof(R) == 8 ? 79 : kApproxMaxN;
-    const size_t minor_smem = sizeof(cx<R>) * (size_t)sym(2 * nmax_smem);
     static_assert(kMaxK + 1 <= 4096, "sector table");
     if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
         int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
@@ -688,27 +783,31 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     const size_t plan_smem = sizeof(double) * (size_t)sym(2 * kApproxMaxN);
     GBS_CUDA(ctx, cudaFuncSetAttribute(approx_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)plan_smem));
+    const long long nocap = 1ll << 62;  // sized on the host below
     approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
                                                                         nmax_smem, pl);
     GBS_CUDA(ctx, cudaGetLastError());
-    long long cap = (long long)((ctx->ws_bytes - approx_offsets(n_pat, 0).unit_D) / (8 * 2 * (kMaxOrder + 1)));
-    approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, cap, pl);
+    approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, pl);
     GBS_CUDA(ctx, cudaGetLastError());
-    // size the per-unit results (one readback), then re-plan if the workspace grew
-    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.unit_off + n_pat, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    // size the workspace and the kernels' shared memory from one readback (units,
+    // largest n, largest L, sectors); re-plan if the workspace had to grow
+    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.info, 32, cudaMemcpyDeviceToHost, ctx->stream));
     GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    long long need = *(long long *)ctx->pinned;
-    if (need > cap) {
-        int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, need).end);
+    const long long units = ((long long *)ctx->pinned)[0], secs = ((long long *)ctx->pinned)[3];
+    const int nmax = (int)((long long *)ctx->pinned)[1], Lmax = (int)((long long *)ctx->pinned)[2];
+    const size_t need = approx_offsets(n_pat, units, secs).end;
+    if (need > ctx->ws_bytes) {
+        int st = gbs_ws_ensure(ctx, need);
         if (st) return st;
         pl = approx_plan_from(ctx->ws, n_pat);
         approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
                                                                             nmax_smem, pl);
-        cap = (long long)((ctx->ws_bytes - approx_offsets(n_pat, 0).unit_D) / (8 * 2 * (kMaxOrder + 1)));
-        approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, cap, pl);
+        approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, pl);
         GBS_CUDA(ctx, cudaGetLastError());
     }
+    pl = approx_plan_from(ctx->ws, n_pat, units, secs);
     GBS_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, 8, ctx->stream));  // work counter
+    const size_t minor_smem = sizeof(cx<R>) * (size_t)sym(2 * (nmax > 0 ? nmax : 1));
     GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)minor_smem));
     int nb = 0;
@@ -722,11 +821,18 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     GBS_CUDA(ctx, cudaGetLastError());
     st = gbs_timing_end(ctx);
     if (st) return st;
-    const size_t fit_smem = sizeof(double) * (size_t)(kMaxOrder + 2) * (kMaxK + 1);
-    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fit_smem));
-    approx_fit_kernel<<<n_pat, kFitThreads, fit_smem, ctx->stream>>>(
-        n_pat, order, sizeof(R) == 8 ? kSectorEps : kSectorEpsF32, logdet, pl, logP, kappa, err_bound, status);
+    const size_t dft_smem = sizeof(double) * 2 * (size_t)Lmax;
+    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dft_smem));
+    approx_dft_kernel<<<n_pat, kDftThreads, dft_smem, ctx->stream>>>(order, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    const long long want = (secs + kSecThreads / 32 - 1) / (kSecThreads / 32);
+    const int fit_blocks = (int)(want < (long long)ctx->num_sms * 16 ? (want > 0 ? want : 1) : ctx->num_sms * 16);
+    approx_sector_fit_kernel<<<fit_blocks, kSecThreads, 0, ctx->stream>>>(
+        n_pat, order, sizeof(R) == 8 ? kSectorEps : kSectorEpsF32, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    approx_sum_kernel<<<(n_pat + kSumThreads / 32 - 1) / (kSumThreads / 32), kSumThreads, 0, ctx->stream>>>(
+        n_pat, logdet, pl, logP, kappa, err_bound, status);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }
