@@ -330,22 +330,55 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
         }
         __syncthreads();
         // symmetric sweep operator on every pivot: G <- -(I - t O_S)^{-1};
-        // Z_S(t) = prod of principal pivot^{-1/2} (pivots are the LDL^T pivots)
+        // Z_S(t) = prod of principal pivot^{-1/2} (pivots are the LDL^T pivots).
+        // Pivot k's column is staged in cb (and cb / pivot in cu) by the previous pivot's
+        // second phase, so an entry update is one complex product of staged values.
+        cx<R> *const cb0 = G + sym(N), *const cb1 = cb0 + N, *const cu0 = cb0 + 2 * N, *const cu1 = cb0 + 3 * N;
+        {
+            const cx<R> inv0 = cinv(G[0]);
+            for (int i = t; i < N; i += kMinorThreads) {
+                const cx<R> v = G[pidx(N, 0, i)];
+                cb0[i] = v;
+                cu0[i] = v * inv0;
+            }
+        }
+        __syncthreads();
         cx<double> zs = mk<double>(1.0, 0.0);
+        cx<R> dprev = mk<R>(R(1), R(0));
+        const int fw = N + 1, fE = (N >> 1) * fw;  // rows p and N - 1 - p folded: N + 1 entries
         for (int k = 0; k < N; ++k) {
-            const cx<R> d = G[pidx(N, k, k)];
+            const cx<R> *cb = (k & 1) ? cb1 : cb0, *cu = (k & 1) ? cu1 : cu0;
+            const cx<R> d = cb[k];
             if (!(d.re > R(0)) && t == 0) s_bad = 1;
-            if (t == 0) zs = zs * widen(crsqrt(d));
+            if ((k & 1) && t == 0) zs = zs * widen(crsqrt(dprev * d));
+            dprev = d;
             const cx<R> inv = cinv(d);
-            for (int f = t; f < N * N; f += kMinorThreads) {
-                int i = f / N, j = f - i * N;
-                if (j < i || i == k || j == k) continue;
-                G[pidx(N, i, j)] = G[pidx(N, i, j)] - G[pidx_any(N, i, k)] * G[pidx_any(N, k, j)] * inv;
+            int fp = t / fw, fq = t - fp * fw;
+            const int sp = kMinorThreads / fw, sq = kMinorThreads - sp * fw;
+            for (int f = t; f < fE; f += kMinorThreads) {
+                int i, j;
+                if (fq < N - fp) { i = fp; j = fp + fq; } else { i = N - 1 - fp; j = i + (fq - (N - fp)); }
+                if (i != k && j != k) {
+                    cx<R> &e = G[i * N - (i * (i - 1)) / 2 + (j - i)];
+                    e = e - cb[i] * cu[j];
+                }
+                fq += sq;
+                fp += sp;
+                if (fq >= fw) { fq -= fw; ++fp; }
             }
             __syncthreads();
+            // scale pivot k's row and column; stage pivot k + 1's column
+            cx<R> *cbn = (k & 1) ? cb0 : cb1, *cun = (k & 1) ? cu0 : cu1;
+            const bool more = k + 1 < N;
+            const cx<R> invn = more ? cinv(G[pidx(N, k + 1, k + 1)]) : mk<R>(R(0), R(0));
             for (int i = t; i < N; i += kMinorThreads) {
-                if (i == k) continue;
-                G[pidx_any(N, i, k)] = G[pidx_any(N, i, k)] * inv;
+                if (i != k) G[pidx_any(N, i, k)] = cu[i];
+                if (more) {
+                    // entry (k, k + 1) is the one just scaled: cu[k + 1]
+                    const cx<R> v = i == k ? cu[k + 1] : G[pidx_any(N, i, k + 1)];
+                    cbn[i] = v;
+                    cun[i] = v * invn;
+                }
             }
             if (t == 0) G[pidx(N, k, k)] = mk<R>(R(0), R(0)) - inv;
             __syncthreads();
@@ -393,12 +426,17 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
                 while ((long long)(b + 1) * b / 2 <= rem) ++b;
                 while ((long long)b * (b - 1) / 2 > rem) --b;
                 const int a = (int)(rem - (long long)b * (b - 1) / 2);
-                int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
+                const int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
+                // row offsets: entry (rr[i], col) with rr[i] <= col sits at ro[i] + col
+                int ro[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) ro[i] = rr[i] * N - (rr[i] * (rr[i] - 1)) / 2 - rr[i];
+                auto gr = [&](int i, int col) -> cx<R> { const cx<R> v = G[ro[i] + col]; return mk<R>(-v.re, -v.im); };
                 cx<R> w6[21];
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
 #pragma unroll
-                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = g(rr[i], rr[j]);
+                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = gr(i, rr[j]);
                 // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
                 cx<R> Lf[15], Dinv[6];
                 cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
@@ -425,7 +463,7 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
                         cx<R> y0[6], y1[6];
 #pragma unroll
                         for (int i = 0; i < 6; ++i) {
-                            cx<R> v0 = g(rr[i], 2 * d4), v1 = g(rr[i], 2 * d4 + 1);
+                            cx<R> v0 = gr(i, 2 * d4), v1 = gr(i, 2 * d4 + 1);
 #pragma unroll
                             for (int k = 0; k < i; ++k) {
                                 v0 = v0 - Lf[pidx(5, k, i - 1)] * y0[k];
@@ -434,7 +472,10 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
                             y0[i] = v0;
                             y1[i] = v1;
                         }
-                        cx<R> s00 = g(2 * d4, 2 * d4), s01 = g(2 * d4, 2 * d4 + 1), s11 = g(2 * d4 + 1, 2 * d4 + 1);
+                        const int dg = 2 * d4 * N - (2 * d4 * (2 * d4 - 1)) / 2;  // (2 d4, 2 d4)
+                        const cx<R> e00 = G[dg], e01 = G[dg + 1], e11 = G[dg + N - 2 * d4];
+                        cx<R> s00 = mk<R>(-e00.re, -e00.im), s01 = mk<R>(-e01.re, -e01.im),
+                              s11 = mk<R>(-e11.re, -e11.im);
 #pragma unroll
                         for (int k = 0; k < 6; ++k) {
                             const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
@@ -807,7 +848,8 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     }
     pl = approx_plan_from(ctx->ws, n_pat, units, secs);
     GBS_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, 8, ctx->stream));  // work counter
-    const size_t minor_smem = sizeof(cx<R>) * (size_t)sym(2 * (nmax > 0 ? nmax : 1));
+    // the packed inverse and four staged pivot columns
+    const size_t minor_smem = sizeof(cx<R>) * ((size_t)sym(2 * (nmax > 0 ? nmax : 1)) + 8 * (size_t)(nmax > 0 ? nmax : 1));
     GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)minor_smem));
     int nb = 0;
