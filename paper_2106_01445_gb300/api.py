@@ -11,10 +11,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF
 
-PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, "fx": GBS_FX, GBS_FP64: GBS_FP64,
-              GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX}
+PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, "fx": GBS_FX, "ff": GBS_FF,
+              GBS_FP64: GBS_FP64, GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX, GBS_FF: GBS_FF}
 
 
 def _ptr(t) -> ctypes.c_void_p:

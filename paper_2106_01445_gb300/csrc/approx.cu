@@ -22,6 +22,7 @@
 // symmetry), approx_fit (one CTA per pattern: inverse DFT, fits, sum).
 #include <math.h>
 
+#include "ff.cuh"
 #include "gbs_internal.cuh"
 
 namespace {
@@ -33,8 +34,6 @@ constexpr int kSecThreads = 256;   // one warp per sector
 constexpr int kSumThreads = 128;   // one warp per pattern
 constexpr int kPlanThreads = 256;
 constexpr double kTailEps = 1e-14;
-constexpr double kSectorEps = 1e-12;  // tilted sectors below this share of the largest: noise
-constexpr double kSectorEpsF32 = 1e-6;  // the same for FP32 minors (moments resolved to ~1e-7 K)
 constexpr double kFlagShare = 1e-4;     // fallback reported when such sectors carry this share of P
 constexpr int kNumRho = 15;
 __constant__ double kRhos[kNumRho] = {1.0, 1.02, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.4, 1.5, 1.7, 2.0, 2.5, 3.0, 4.0};
@@ -61,6 +60,7 @@ template <typename R> __device__ __forceinline__ cx<R> cinv(cx<R> a) {
 }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ ff rsqrt_r(ff x) { return ff_rsqrt(x); }
 // principal p^{-1/2} for Re p > 0: with a = |p| and s = sqrt((a + Re p)/2) (no
 // cancellation: Re p > 0), sqrt(p) = s + i Im p / (2 s) and p^{-1/2} = (s - i Im p/(2 s)) / a;
 // two reciprocal square roots, no division
@@ -73,6 +73,23 @@ template <typename R> __device__ __forceinline__ cx<R> crsqrt(cx<R> p) {
 }
 __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
 __device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
+__device__ __forceinline__ cx<double> widen(cx<ff> a) { return {ff_to_double(a.re), ff_to_double(a.im)}; }
+
+// per precision of the minors: largest pattern (the packed inverse must fit in shared
+// memory) and the tilted-sector share below which a sector counts as rounding noise
+template <typename R> struct MinorPrec;
+template <> struct MinorPrec<double> {
+    static constexpr int nmax = 79;
+    static constexpr double sector_eps = 1e-12;  // tilted sectors below this share of the largest: noise
+};
+template <> struct MinorPrec<ff> {
+    static constexpr int nmax = 79;
+    static constexpr double sector_eps = 1e-12;
+};
+template <> struct MinorPrec<float> {
+    static constexpr int nmax = 112;
+    static constexpr double sector_eps = 1e-6;  // moments resolved to ~1e-7 K
+};
 
 // ---- plan: sector bound and DFT length per pattern ---------------------------------
 struct ApproxPlan {
@@ -253,6 +270,17 @@ template <> struct GroupAcc<double> {
     __device__ __forceinline__ void add(int w, cx<double> f) {
         v[2 * w] += f.re;
         v[2 * w + 1] += f.im;
+    }
+    __device__ __forceinline__ double get(int q) const { return v[q]; }
+};
+template <> struct GroupAcc<ff> {
+    double v[2 * (kMaxOrder + 1)];
+    __device__ void zero() {
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) v[w] = 0.0;
+    }
+    __device__ __forceinline__ void add(int w, cx<ff> f) {
+        v[2 * w] += ff_to_double(f.re);
+        v[2 * w + 1] += ff_to_double(f.im);
     }
     __device__ __forceinline__ double get(int q) const { return v[q]; }
 };
@@ -814,7 +842,7 @@ template <typename R>
 int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status) {
     // patterns up to this size are taken
-    const int nmax_smem = sizeof(R) == 8 ? 79 : kApproxMaxN;
+    const int nmax_smem = MinorPrec<R>::nmax;
     static_assert(kMaxK + 1 <= 4096, "sector table");
     if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
         int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
@@ -871,7 +899,7 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     const long long want = (secs + kSecThreads / 32 - 1) / (kSecThreads / 32);
     const int fit_blocks = (int)(want < (long long)ctx->num_sms * 16 ? (want > 0 ? want : 1) : ctx->num_sms * 16);
     approx_sector_fit_kernel<<<fit_blocks, kSecThreads, 0, ctx->stream>>>(
-        n_pat, order, sizeof(R) == 8 ? kSectorEps : kSectorEpsF32, pl);
+        n_pat, order, MinorPrec<R>::sector_eps, pl);
     GBS_CUDA(ctx, cudaGetLastError());
     approx_sum_kernel<<<(n_pat + kSumThreads / 32 - 1) / (kSumThreads / 32), kSumThreads, 0, ctx->stream>>>(
         n_pat, logdet, pl, logP, kappa, err_bound, status);
@@ -890,5 +918,7 @@ int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
         return run_approx<double>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
     if (precision == GBS_FP32_SPLIT)
         return run_approx<float>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
-    return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: the approximation runs in FP64 or the FP32 split");
+    if (precision == GBS_FF)
+        return run_approx<ff>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
+    return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: the approximation runs in FP64, float-float or the FP32 split");
 }

@@ -1,8 +1,8 @@
 """GPU parity of the moment approximation (orders 2..4) against the oracle's
 step-by-step version (exact eigenvalue power series instead of the DFT).
 
-Tolerances: the FP64 path and the oracle solve the same convex fits from the
-same moments; their moments differ by the DFT's rounding (~1e-15 of the largest
+Tolerances: the FP64 and float-float paths and the oracle solve the same convex
+fits from the same moments; their moments differ by the DFT's rounding (~1e-15 of the largest
 sector), so log P agrees to 1e-8.  The FP32 split computes the minors with FP32
 complex arithmetic: moments carry ~1e-6 relative error, and log P agrees to
 2e-3 (measured margin in the test).  With at most j + 1 points in every
@@ -46,10 +46,13 @@ def small_case():
     return M, U, r, eta, mode_sets, pats, st
 
 
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
 @pytest.mark.parametrize("order", [2, 3, 4])
-def test_fp64_matches_oracle(ctx, small_case, order):
+def test_fp64_matches_oracle(ctx, small_case, order, precision):
+    # FP64 minors and float-float minors (~48 bits) both resolve the moments far
+    # below the fits' 1e-13 residual target
     M, U, r, eta, mode_sets, pats, st = small_case
-    res = run(ctx, U, r, eta, pats, order, "fp64")
+    res = run(ctx, U, r, eta, pats, order, precision)
     for i, modes in enumerate(mode_sets):
         ref, info = ap.approx_logprob(st.O, st.logdet, M, modes, order)
         assert res["status"][i] in (0, 7), res["status"][i]
@@ -116,6 +119,25 @@ def test_m50_workload_sample(ctx):
     for i in idx:
         ref, _ = ap.approx_logprob(st.O, st.logdet, c.M, g.pattern_modes(pats[i]), 4)
         assert abs(res["logP"][i] - ref) < (1e-8 if n[i] <= 13 else 1e-5), (i, n[i])
+
+
+def test_ff_m50_sample_and_exact_only_rejects_ff(ctx):
+    from paper_2106_01445_gb300 import GbsError
+    c = g.CONFIGS["m50_approx"]
+    U, r = c.unitary(), c.squeezing()
+    pats = c.patterns()[:128]
+    n = np.array([len(g.pattern_modes(p)) for p in pats])
+    ff = run(ctx, U, r, c.eta, pats, 4, "ff")
+    f64 = run(ctx, U, r, c.eta, pats, 4, "fp64")
+    # same fits, no extra fallbacks; the far-tail sectors of these improbable patterns sit
+    # ~1e-10 below the largest, where 48-bit minors resolve the moments to ~1e-5 of
+    # themselves: log P to 1e-6 (measured 7e-8)
+    assert (ff["status"] == f64["status"]).all()
+    ok = f64["status"] == 0
+    assert np.abs(ff["logP"][ok] - f64["logP"][ok]).max() < 1e-6
+    st = ctx.build_state(U, r, c.eta)
+    with pytest.raises(GbsError):
+        ctx.prob(st["O"], st["logdet"], pats[:4], order=0, precision="ff")
 
 
 def test_approx_invalid_patterns(ctx):
