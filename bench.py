@@ -214,6 +214,13 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = Context(local, stream)
+    # the autotuner picks the work split of the headline precision on this batch, then
+    # the reservation sizes the workspace for it (no allocation or sync in the steps)
+    st0 = ctx.build_state(U, r, c.eta)
+    tuned = {}
+    for pk in ("fx", "dd", "fp64", "fp32"):
+        sp, tms = ctx.autotune(st0["O"], st0["logdet"], pats, precision=pk)
+        tuned[pk] = {"split": sp, "sweep_ms": tms}
     ctx.reserve(len(pats), int(n.max()))
     Ud = _complex_interleaved(U, dev)
     rd = torch.as_tensor(r, device=dev)
@@ -295,6 +302,7 @@ def run_gpu(args):
                        "subsets_per_step": subsets, "precision": prec,
                        "l2": "flushed between timed steps (512 MB write)"},
             "patterns_per_s": len(pats) * world * args.steps / (ms * 1e-3),
+            "autotune": tuned,
             "gpu_launches": 4 * args.steps}
     if rank != 0:
         return 0

@@ -77,6 +77,17 @@ int gbs_version(void);
  * synchronise (needed for CUDA-graph capture).  Synchronous. */
 int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max);
 
+/* Autotuner (not in the paper): runs the exact sweep of these patterns with every
+ * split s = 0..3 of a work unit (the prefix modes a CTA loops over inside one unit:
+ * 2^(s + 9 or 10) subsets per unit) and keeps the fastest for this precision in the
+ * context; later gbs_prob, gbs_reserve and gbs_prob_noalloc calls use it.  Choose
+ * it before gbs_reserve (a reservation sized for one split may not hold a finer
+ * one: such splits are skipped).  Allocates scratch for its outputs and
+ * synchronises: not for use under stream capture.  best_split / best_ms (mean ms of
+ * one sweep) may be NULL.  Errors: GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
+int gbs_autotune(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                 const uint64_t *patterns, int n_pat, int precision, int *best_split, double *best_ms);
+
 /* ---- state build (Methods, "Model" and "Partition function") ------------
  * From U (M x M complex, unitary), squeezing r (M, r_j = 0 for vacuum
  * inputs) and uniform transmission eta in (0, 1]:

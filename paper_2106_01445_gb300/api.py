@@ -80,6 +80,17 @@ class Context:
     def reserve(self, n_pat: int, n_max: int):
         self._check(self.lib.gbs_reserve(self.h, n_pat, n_max))
 
+    def autotune(self, O: torch.Tensor, logdet: torch.Tensor, patterns, precision="fx"):
+        """Pick the exact sweep's work split for this precision on these patterns
+        (kept in the context); returns (split, ms of one sweep).  Synchronous; call it
+        before reserve()."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        s, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.gbs_autotune(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), pats.shape[0],
+                                          PRECISIONS[precision], ctypes.byref(s), ctypes.byref(ms)))
+        return s.value, ms.value
+
     def build_state(self, U, r, eta: float, want_sigma: bool = False, check: bool = True):
         """Device O (2M x 2M), log det sigma_Q (1,), sigma (or None), status (1,) int32."""
         Ud = _complex_interleaved(U, self.device)

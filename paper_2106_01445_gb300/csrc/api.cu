@@ -144,8 +144,8 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_reserve: bad n_pat %d / n_max %d", n_pat, n_max);
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     long long units = 0;
-    for (int prec = 0; prec < 3; ++prec) {
-        long long u = sweep_units_upper_bound(n_pat, n_max, prec);
+    for (int prec = 0; prec < 4; ++prec) {
+        long long u = sweep_units_upper_bound(n_pat, n_max, prec, sweep_split_of(ctx, prec));
         if (u > units) units = u;
     }
     int st = gbs_ws_ensure(ctx, sweep_workspace_bytes(n_pat, units));
@@ -153,6 +153,69 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
     ctx->reserved = true;
     ctx->cap_pat = n_pat;
     ctx->cap_units = units;
+    return GBS_OK;
+}
+
+int gbs_autotune(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                 const uint64_t *patterns, int n_pat, int precision, int *best_split, double *best_ms) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 1 || !O || !logdet_sigmaQ || !patterns ||
+        (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_autotune: bad arguments (M=%d, n_pat=%d, precision=%d)", M,
+                        n_pat, precision);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    double *lp = nullptr;
+    int32_t *st = nullptr;
+    GBS_CUDA(ctx, cudaMalloc(&lp, sizeof(double) * (size_t)n_pat));
+    if (cudaMalloc(&st, sizeof(int32_t) * (size_t)n_pat) != cudaSuccess) {
+        cudaFree(lp);
+        return gbs_fail(ctx, GBS_E_NOMEM, "gbs_autotune: cannot allocate %d statuses", n_pat);
+    }
+    int32_t *hst = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_pat);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int code = GBS_OK, best = -1;
+    float best_t = 0.0f;
+    const int saved = ctx->sweep_split[precision];
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    if (!hst || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        code = gbs_fail(ctx, GBS_E_NOMEM, "gbs_autotune: setup failed");
+    } else {
+        for (int s = 0; s <= 3 && code == GBS_OK; ++s) {
+            ctx->sweep_split[precision] = s;
+            code = sweep_exact(ctx, M, O, logdet_sigmaQ, patterns, n_pat, precision, lp, nullptr, nullptr, st);
+            if (code) break;
+            cudaEventRecord(e0, ctx->stream);
+            for (int rep = 0; rep < 2 && code == GBS_OK; ++rep)
+                code = sweep_exact(ctx, M, O, logdet_sigmaQ, patterns, n_pat, precision, lp, nullptr, nullptr, st);
+            if (code) break;
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaMemcpy(hst, st, sizeof(int32_t) * (size_t)n_pat, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                code = gbs_fail(ctx, GBS_E_CUDA, "gbs_autotune: timing failed");
+                break;
+            }
+            bool fits = true;  // a reservation too small for this split reports GBS_E_NOMEM
+            for (int p = 0; p < n_pat; ++p) fits = fits && hst[p] != GBS_E_NOMEM;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (fits && (best < 0 || ms < best_t)) {
+                best = s;
+                best_t = ms;
+            }
+        }
+    }
+    ctx->sweep_split[precision] = code == GBS_OK && best >= 0 ? best : saved;
+    ctx->timing = timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    free(hst);
+    cudaFree(lp);
+    cudaFree(st);
+    if (code) return code;
+    if (best < 0) return gbs_fail(ctx, GBS_E_NOMEM, "gbs_autotune: no split fits the reserved workspace");
+    if (best_split) *best_split = best;
+    if (best_ms) *best_ms = best_t / 2.0;
     return GBS_OK;
 }
 

@@ -26,6 +26,9 @@ struct gbs_ctx {
     size_t host_io_bytes = 0;
     // persistent-grid sizes of the sweep kernels (CTAs per SM), by precision
     int sweep_blocks_per_sm[4] = {0, 0, 0, 0};
+    // prefix levels looped inside one sweep unit, by precision (-1: the default);
+    // set by gbs_autotune
+    int sweep_split[4] = {-1, -1, -1, -1};
     // optional event timing of the sweep kernel launches
     static const int kTimingRing = 4096;
     bool timing = false;
@@ -65,7 +68,8 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
                    const double *logdet, const uint64_t *patterns, int n_pat, int precision,
                    double *logP, double *kappa, double *err_bound, int32_t *status);
 size_t sweep_workspace_bytes(int n_pat, long long units);
-long long sweep_units_upper_bound(int n_pat, int n_max, int precision);
+long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split);
+int sweep_split_of(const gbs_ctx *ctx, int precision);
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);

@@ -58,7 +58,7 @@ extern "C" int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const doub
         return gbs_fail(ctx, GBS_E_INVALID,
                         "gbs_prob_noalloc: %d patterns exceed the fixed scratch limit of %d", n_pat,
                         kNoAllocMaxPatterns);
-    const long long units = sweep_units_upper_bound(n_pat, n_max, precision);
+    const long long units = sweep_units_upper_bound(n_pat, n_max, precision, sweep_split_of(ctx, precision));
     const size_t need = sweep_workspace_bytes(n_pat, units);
     if (need > kNoAllocBytes)
         return gbs_fail(ctx, GBS_E_INVALID,

@@ -320,14 +320,16 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 
 // ---- plan: order patterns by click count, one unit per prefix choice -----------------
 // n_eff = clicks padded to >= B; L_eff breadth-first levels; q prefix levels of
-// which the first q - s index units and the last s are looped over in the CTA.
+// which the first q - s index units and the last s (s <= split <= kS) are looped over
+// in the CTA.  The split sets the work per unit (2^(s + L + B) subsets): the autotuner
+// picks it per precision.
 template <typename T>
-__host__ __device__ inline void unit_shape(int n, int &n_eff, int &L_eff, int &q, int &s) {
+__host__ __device__ inline void unit_shape(int n, int &n_eff, int &L_eff, int &q, int &s, int split) {
     constexpr int B = Prec<T>::B;
     n_eff = n > B ? n : B;
     L_eff = n_eff - B < kL ? n_eff - B : kL;
     q = n_eff - B - L_eff;
-    s = q < kS ? q : kS;
+    s = q < split ? q : split;
 }
 
 struct Plan {
@@ -339,6 +341,7 @@ struct Plan {
     long long *unit_off;  // n_pat + 1, in sorted order
     int *pflags;        // per sorted position: status bits
     double *partials;   // 3 per unit
+    int split;          // prefix levels looped inside a unit (0..kS)
 };
 
 template <typename T>
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
     for (int i = t * per; i < n_pat && i < (t + 1) * per; ++i) {
         int n = pl.pat_n[pl.perm[i]];
         int n_eff, L_eff, q, ss;
-        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss);
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss, pl.split);
         s += n < 0 ? 0 : (1ll << (q - ss));
     }
     chunk[t] = s;
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
         pl.pflags[i] = 0;
         int n = pl.pat_n[pl.perm[i]];
         int n_eff, L_eff, q, ss;
-        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss);
+        unit_shape<T>(n < 0 ? 0 : n, n_eff, L_eff, q, ss, pl.split);
         run += n < 0 ? 0 : (1ll << (q - ss));
     }
     if (t == kPlanThreads - 1) {
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         __syncthreads();
         const int n = s_n;
         int n_eff, L_eff, q, ss;
-        unit_shape<T>(n, n_eff, L_eff, q, ss);
+        unit_shape<T>(n, n_eff, L_eff, q, ss, pl.split);
         const int r = L_eff + B;           // modes of a sub-unit's level-0 matrix
         const int qs = q - ss;             // prefix levels fixed by the unit index
         const int rp = ss + r;             // modes after the unit's prefix elimination
@@ -938,6 +941,7 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
         cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
     }
     Plan pl = plan_from(ctx->ws, n_pat);
+    pl.split = sweep_split_of(ctx, pi);
     plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
     GBS_CUDA(ctx, cudaGetLastError());
     if (!ctx->reserved) {
@@ -951,6 +955,7 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
             if (st) return st;
             cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
             pl = plan_from(ctx->ws, n_pat);
+            pl.split = sweep_split_of(ctx, pi);
             plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
             GBS_CUDA(ctx, cudaGetLastError());
         }
@@ -991,6 +996,7 @@ int run_sweep_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O
         return gbs_fail(ctx, GBS_E_INVALID, "workspace of %zu bytes cannot hold %d patterns", ws_bytes, n_pat);
     const long long cap = (long long)((ws_bytes - base) / 24);
     Plan pl = plan_from(ws, n_pat);
+    pl.split = sweep_split_of(ctx, pi);
     plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
     GBS_CUDA(ctx, cudaGetLastError());
     const int grid = ctx->num_sms * ctx->sweep_blocks_per_sm[pi];
@@ -1023,12 +1029,17 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
 
 size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_pat, units).end; }
 
-long long sweep_units_upper_bound(int n_pat, int n_max, int precision) {
+int sweep_split_of(const gbs_ctx *ctx, int precision) {
+    const int v = ctx->sweep_split[precision & 3];
+    return v < 0 || v > kS ? kS : v;
+}
+
+long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split) {
     int n_eff, L_eff, q, ss;
-    if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss);
-    else if (precision == GBS_DD) unit_shape<dd>(n_max, n_eff, L_eff, q, ss);
-    else if (precision == GBS_FX) unit_shape<fx>(n_max, n_eff, L_eff, q, ss);
-    else unit_shape<float>(n_max, n_eff, L_eff, q, ss);
+    if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss, split);
+    else if (precision == GBS_DD) unit_shape<dd>(n_max, n_eff, L_eff, q, ss, split);
+    else if (precision == GBS_FX) unit_shape<fx>(n_max, n_eff, L_eff, q, ss, split);
+    else unit_shape<float>(n_max, n_eff, L_eff, q, ss, split);
     return (long long)n_pat << (q - ss);
 }
 

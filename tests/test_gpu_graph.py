@@ -1,0 +1,82 @@
+"""Batching features of the exact path: one persistent launch for uneven patterns
+captured in a CUDA graph (gbs_reserve makes gbs_prob allocation- and sync-free),
+and the autotuner's split choice (results are the same for every split)."""
+import numpy as np
+import pytest
+import torch
+
+import gbs_inputs as g
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(cuda_ok):
+    from paper_2106_01445_gb300 import build
+    build.build()
+    from paper_2106_01445_gb300.api import Context, patterns_tensor, _complex_interleaved
+    return Context, patterns_tensor, _complex_interleaved
+
+
+@pytest.mark.parametrize("precision", ["fx", "fp64"])
+def test_cuda_graph_capture_and_replay(setup, precision):
+    Context, patterns_tensor, _complex_interleaved = setup
+    dev = torch.device("cuda", 0)
+    c = g.CONFIGS["m24_exact"]
+    pats = c.patterns()
+    n = np.array([len(g.pattern_modes(p)) for p in pats])
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        ctx = Context(0, s)
+        ctx.reserve(len(pats), int(n.max()))
+        Ud = _complex_interleaved(c.unitary(), dev)
+        rd = torch.as_tensor(c.squeezing(), device=dev)
+        pd = patterns_tensor(pats, dev)
+        M = c.M
+        O = torch.empty((2 * M, 2 * M), dtype=torch.float64, device=dev)
+        logdet = torch.empty(1, dtype=torch.float64, device=dev)
+        sst = torch.zeros(1, dtype=torch.int32, device=dev)
+        out = {k: torch.empty(len(pats), dtype=torch.float64, device=dev) for k in ("logP", "kappa", "err_bound")}
+        out["status"] = torch.empty(len(pats), dtype=torch.int32, device=dev)
+        # eager reference (also warms the kernels' attributes up before capture)
+        ctx.build_state_into(Ud, rd, c.eta, O, logdet, sst)
+        ref = ctx.prob(O, logdet, pd, precision=precision)
+        ref = {k: v.clone() for k, v in ref.items()}
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            ctx.build_state_into(Ud, rd, c.eta, O, logdet, sst)
+            ctx.prob(O, logdet, pd, precision=precision, out=out)
+        for _ in range(2):
+            out["logP"].fill_(0.0)
+            graph.replay()
+            s.synchronize()
+            assert torch.equal(out["status"], ref["status"])
+            assert torch.equal(out["logP"], ref["logP"])      # deterministic: bit for bit
+        # new inputs through the captured buffers: another interferometer
+        Ud.copy_(_complex_interleaved(g.haar_unitary(M, 99), dev))
+        graph.replay()
+        s.synchronize()
+        ctx.build_state_into(Ud, rd, c.eta, O, logdet, sst)
+        ref2 = ctx.prob(O, logdet, pd, precision=precision)
+        s.synchronize()
+        assert torch.equal(out["logP"], ref2["logP"])
+        assert not torch.equal(out["logP"], ref["logP"])
+        ctx.close()
+
+
+def test_autotune_picks_a_split_with_equal_results(setup):
+    Context, patterns_tensor, _ = setup
+    c = g.CONFIGS["m24_exact"]
+    ctx = Context(0)
+    st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
+    pats = c.patterns()[:256]
+    before = ctx.prob(st["O"], st["logdet"], pats, precision="fx")
+    split, ms = ctx.autotune(st["O"], st["logdet"], pats, precision="fx")
+    assert 0 <= split <= 3 and ms > 0.0
+    after = ctx.prob(st["O"], st["logdet"], pats, precision="fx")
+    torch.cuda.synchronize()
+    assert torch.equal(before["status"], after["status"])
+    # a different split changes only the order of the double-double unit sums
+    ok = before["status"] == 0
+    assert (before["logP"][ok] - after["logP"][ok]).abs().max().item() < 1e-13
