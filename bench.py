@@ -562,7 +562,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fx", choices=["fp32", "fp64", "dd", "fx"])
+    ap.add_argument("--precision", default="fx", choices=["fp32", "fp64", "dd", "fx", "ff"],
+                    help="ff (float-float minors) serves --profile approx only")
     ap.add_argument("--dd-sample", type=int, default=24)
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")

@@ -75,6 +75,12 @@ __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re,
 __device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
 __device__ __forceinline__ cx<double> widen(cx<ff> a) { return {ff_to_double(a.re), ff_to_double(a.im)}; }
 
+// an entry of I - t O_S, t = cs + i sn, from the FP64 products (forming it in FP32 was
+// measured no faster and raised the FP32 path's fit fallbacks)
+template <typename R> __device__ __forceinline__ cx<R> init_entry(bool diag, double cs, double sn, double o) {
+    return mk<R>(R((diag ? 1.0 : 0.0) - cs * o), R(-sn * o));
+}
+
 // per precision of the minors: largest pattern (the packed inverse must fit in shared
 // memory) and the tilted-sector share below which a sector counts as rounding noise
 template <typename R> struct MinorPrec;
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, con
             if (j < i) continue;
             int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
             double o = O[(size_t)si * N2 + sj];
-            G[pidx(N, i, j)] = mk<R>((R)((i == j ? 1.0 : 0.0) - cs * o), (R)(-sn * o));
+            G[pidx(N, i, j)] = init_entry<R>(i == j, cs, sn, o);
         }
         __syncthreads();
         // symmetric sweep operator on every pivot: G <- -(I - t O_S)^{-1};
