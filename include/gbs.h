@@ -153,16 +153,17 @@ int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const double *logdet_
                      double *kappa, double *err_bound, int32_t *status);
 
 /* ---- gradients (not in the paper) ---------------------------------------
- * L = sum_p w[p] log P(S_p) (exact probabilities, n <= 16 clicks per pattern).
+ * L = sum_p w[p] log P(S_p) (exact probabilities, n <= 24 clicks per pattern).
  * With A = sigma_Q^{-1}, dT = tr(Gbar dA_S), Gbar = sum_Z (-1)^{n-|Z|} (-1/2)
  * det(A_Z)^{-1/2} A_Z^{-1} (the trace formula d det^{-1/2} = -1/2 det^{-1/2}
- * tr(A^{-1} dA)), computed per subset in double-double because Gbar and T
- * cancel alike:
+ * tr(A^{-1} dA)), i.e. Gbar = dT/dA_S, computed in double-double (Gbar and T
+ * cancel alike) by reverse mode through the include/exclude Schur recursion that
+ * evaluates T (O(2^n) work per pattern):
  *   dL/dsigma_Q = -1/2 (sum w) A - A H A,  H = sum_p (w_p / T_p) Gbar_p (embedded).
  * w: n_pat doubles (device).  dsigmaQ: 2M x 2M out (device).  logP, status:
  * optional per-pattern outputs (the double-double log P).  Synchronises once
  * (pattern sizes are checked on the host); GBS_E_INVALID for a pattern with
- * more than 16 clicks or a detector >= M. */
+ * more than 24 clicks or a detector >= M. */
 int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
              const uint64_t *patterns, int n_pat, const double *w, double *dsigmaQ, double *logP,
              int32_t *status);

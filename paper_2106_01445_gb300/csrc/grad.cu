@@ -6,10 +6,11 @@
 //     dT = tr(Gbar dA_S),  Gbar = sum_Z (-1)^{n-|Z|} (-1/2) tau_Z A_Z^{-1},
 //     dL/dsigma_Q = -1/2 (sum_p w_p) A - A H A,   H = sum_p (w_p / T_p) embed(Gbar_p).
 // Gbar and T cancel together by the condition number kappa of the signed sum
-// (1e14..1e19 on improbable patterns), so every subset Cholesky, inverse and
-// sum is double-double; after the division by T the result is an ordinary
-// FP64 number.  One warp per subset; chunks of subsets per CTA; chunk partials
-// summed per pattern in order (deterministic).
+// (1e14..1e19 on improbable patterns), so the whole computation is double-double;
+// after the division by T the result is an ordinary FP64 number.  Gbar = dT/dA_S is
+// computed in reverse mode through the same include/exclude Schur recursion that
+// evaluates T (O(2^n) work instead of a factorisation and inverse per subset); one
+// CTA per pattern, its units in order (deterministic).
 //
 // Then the chain through sigma_Q = eta R diag(d) R^T + (1 - eta/2) I (R the xp
 // form of U, d = e^{-2r}/2 on x, e^{2r}/2 on p) and through the rectangular
@@ -19,141 +20,342 @@
 
 namespace {
 
-constexpr int kGradMaxN = 16;            // clicks per pattern on the gradient path
-constexpr int kGD = 2 * kGradMaxN;       // largest subset matrix (32 x 32)
-constexpr int kGradWarps = 2;            // warps per CTA
-constexpr int kChunkLog = 11;            // 2048 subsets per CTA
+constexpr int kGradMaxN = 24;            // clicks per pattern on the gradient path
+constexpr int kGD = 2 * kGradMaxN;       // largest pattern matrix (48 x 48)
+constexpr int kTM = 7;                   // modes of a unit's subtree (2^7 leaves)
+constexpr int kTreeThreads = 128;
 
-struct GradWarpSmem {
-    dd L[kGD * kGD];     // Cholesky factor (lower)
-    dd X[kGD * kGD];     // columns of A_Z^{-1}
-    dd acc[kGD * kGD];   // this warp's share of Gbar (2n x 2n, S-local rows 2a + alpha)
-};
+__host__ __device__ constexpr int gsym(int d) { return d * (d + 1) / 2; }
+// packed upper-triangle index of (i, j), i <= j
+__host__ __device__ constexpr int gpidx(int d, int i, int j) { return i * d - (i * (i - 1)) / 2 + (j - i); }
+__device__ __forceinline__ int gpany(int d, int i, int j) { return i <= j ? gpidx(d, i, j) : gpidx(d, j, i); }
+// level l of a unit's subtree: 2^l nodes of dimension 2 (kTM - l), packed, back to back
+__host__ __device__ constexpr int lvl_off(int l) {
+    int s = 0;
+    for (int q = 0; q < l; ++q) s += (1 << q) * gsym(2 * (kTM - q));
+    return s;
+}
+constexpr int lvl_cap() {
+    int m = 0;
+    for (int l = 0; l < kTM; ++l) m = (1 << l) * gsym(2 * (kTM - l)) > m ? (1 << l) * gsym(2 * (kTM - l)) : m;
+    return m;
+}
+constexpr int y_cap() {
+    int m = 2 * (kGD - 2);
+    for (int l = 0; l < kTM; ++l) m = (1 << l) * 4 * (kTM - l - 1) > m ? (1 << l) * 4 * (kTM - l - 1) : m;
+    return m;
+}
+constexpr int kNodes = (1 << kTM) - 1;   // nodes of levels 0..kTM-1
+// shared memory (double-double elements)
+constexpr int kOffUM = gsym(kGD), kOffGf = 2 * gsym(kGD), kOffLv = 3 * gsym(kGD);
+constexpr int kOffAdjA = kOffLv + lvl_off(kTM), kOffAdjB = kOffAdjA + lvl_cap();
+constexpr int kOffQ = kOffAdjB + lvl_cap(), kOffRs = kOffQ + 3 * kNodes, kOffS = kOffRs + kNodes;
+constexpr int kOffY = kOffS + kNodes, kOffPreQ = kOffY + y_cap(), kOffPreRs = kOffPreQ + 3 * kGradMaxN;
+constexpr int kTreeSmem = kOffPreRs + kGradMaxN;
 
-__global__ void __launch_bounds__(32 * kGradWarps) grad_subsets_kernel(
-    int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int n_pat,
-    const long long *__restrict__ chunk_off, double *__restrict__ part_hi, double *__restrict__ part_lo,
-    double *__restrict__ part_T, int *__restrict__ flags) {
+// (i, j), i <= j, of packed entry f of an even dimension d: rows p and d - 1 - p folded
+__device__ __forceinline__ void fold_ij(int f, int d, int &i, int &j) {
+    const int w = d + 1, p = f / w, k = f - p * w;
+    if (k < d - p) {
+        i = p;
+        j = p + k;
+    } else {
+        i = d - 1 - p;
+        j = i + (k - (d - p));
+    }
+}
+
+// One 2x2 pivot of the packed D x D unit matrix, eliminated by the CTA: rows and
+// columns >= c0 + 2 receive C - W B^T (W = B P^{-1}); the pivot rows stay as they were
+// (the reverse pass reads them).  Returns det^{-1/2}; stores P^{-1} and det^{-1/2}.
+__device__ dd tree_pivot(dd *UM, int D, int c0, dd *Wb, dd *Qout, dd *rsout, int *bad) {
+    const int t = threadIdx.x;
+    const dd p00 = UM[gpidx(D, c0, c0)], p01 = UM[gpidx(D, c0, c0 + 1)], p11 = UM[gpidx(D, c0 + 1, c0 + 1)];
+    const dd det = dd_dot2(p00, p11, -p01, p01);
+    const dd rs = dd_rsqrt(det), inv = rs * rs;
+    const dd q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+    if (t == 0) {
+        Qout[0] = q00;
+        Qout[1] = q01;
+        Qout[2] = q11;
+        *rsout = rs;
+        if (!(det.hi > 0.0)) atomicOr(bad, 1);
+    }
+    const int Dt = D - c0 - 2;
+    for (int i = t; i < Dt; i += kTreeThreads) {
+        const dd b0 = UM[gpidx(D, c0, c0 + 2 + i)], b1 = UM[gpidx(D, c0 + 1, c0 + 2 + i)];
+        Wb[2 * i] = dd_dot2(q00, b0, q01, b1);
+        Wb[2 * i + 1] = dd_dot2(q01, b0, q11, b1);
+    }
+    __syncthreads();
+    for (int f = t; f < gsym(Dt); f += kTreeThreads) {
+        int i, j;
+        fold_ij(f, Dt, i, j);
+        dd &c = UM[gpidx(D, c0 + 2 + i, c0 + 2 + j)];
+        c = dd_fms2(c, Wb[2 * i], UM[gpidx(D, c0, c0 + 2 + j)], Wb[2 * i + 1], UM[gpidx(D, c0 + 1, c0 + 2 + j)]);
+    }
+    __syncthreads();
+    return rs;
+}
+
+// Gbar_p = dT/dA_S by reverse mode through the include/exclude Schur recursion.
+// Units = (pattern, include/exclude choice of the first q = n - m modes), m = min(n, 7).
+// A unit's value V = (-1)^{q-k} tau_prefix S(root): its k included prefix modes are
+// eliminated (pivot rows kept), then the subtree over the last m modes is expanded
+// breadth first with every level kept, S(node) = rs S(include child) - S(exclude child)
+// (S = 1 at a leaf).  Reverse, with Gamma(node) = dS(node)/dC_node:
+//   rest block:  rs Gamma(inc) - Gamma(exc)
+//   pivot rows:  -rs Y,  Y = P^{-1} B Gamma(inc)
+//   pivot block: rs (Y B^T P^{-1} - S(inc) P^{-1} / 2)
+// then back through the prefix pivots the same way (with -V P^{-1} / 2 from tau_prefix),
+// added into the pattern's Gbar at the unit's rows.  One CTA per pattern; units in order.
+__global__ void __launch_bounds__(kTreeThreads) grad_tree_kernel(int M, const double *__restrict__ O,
+                                                               const uint64_t *__restrict__ pats, int n_pat,
+                                                               double *__restrict__ part_hi,
+                                                               double *__restrict__ part_lo,
+                                                               double *__restrict__ part_T, int *__restrict__ flags) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    GradWarpSmem *ws = (GradWarpSmem *)gsm;
+    dd *const base = (dd *)gsm;
+    dd *const Gacc = base, *const UM = base + kOffUM, *const Gf = base + kOffGf, *const Lv = base + kOffLv;
+    dd *const nQ = base + kOffQ, *const nrs = base + kOffRs, *const nS = base + kOffS, *const Yb = base + kOffY;
+    dd *const preQ = base + kOffPreQ, *const prers = base + kOffPreRs;
     __shared__ int modes[128];
-    __shared__ int s_n, s_p;
-    __shared__ double s_T[kGradWarps][2];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long cid = blockIdx.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n_pat;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (chunk_off[mid] <= cid) lo = mid; else hi = mid;
-        }
-        int p = lo;
-        while (p + 1 < n_pat && chunk_off[p + 1] <= cid) ++p;
-        s_p = p;
+    __shared__ int rowmode[kGD];
+    __shared__ int s_n, s_k, s_bad;
+    __shared__ dd s_T, s_V;
+    const int t = threadIdx.x, p = blockIdx.x, N2 = 2 * M;
+    if (t == 0) {
         int n = 0;
         for (int i = 0; i < M; ++i) {
-            uint64_t w = i < 64 ? pats[2 * p] : pats[2 * p + 1];
+            const uint64_t w = i < 64 ? pats[2 * p] : pats[2 * p + 1];
             if (w >> (i & 63) & 1ull) modes[n++] = i;
         }
         s_n = n;
+        s_bad = 0;
+        s_T = dd(n == 0 ? 1.0 : 0.0);
     }
     __syncthreads();
-    const int p = s_p, n = s_n, D = 2 * n, N2 = 2 * M;
-    const long long chunk = cid - chunk_off[p];
-    GradWarpSmem &S = ws[wid];
-    for (int f = lane; f < D * D; f += 32) S.acc[f] = dd(0.0);
-    dd tsum = dd(0.0);
-    bool bad = false;
-    const long long z0 = chunk << kChunkLog;
-    long long z1 = z0 + (1ll << kChunkLog);
-    if (z1 > (1ll << n)) z1 = 1ll << n;
-    __syncwarp();
-    for (long long z = z0 + wid; z < z1; z += kGradWarps) {
-        const int k = __popcll((unsigned long long)z), d = 2 * k;
-        // the lane's row: mode (i/2)-th set bit of z, quadrature i & 1
-        int gi = 0, li = 0;
-        if (lane < d) {
-            int c = lane >> 1, a = 0;
-            for (; a < n; ++a)
-                if (z >> a & 1) { if (c == 0) break; --c; }
-            gi = modes[a] + (lane & 1) * M;
-            li = 2 * a + (lane & 1);
-        }
-        // lower triangle of A_Z = (I - O)_Z, exact in double-double
-        for (int j = 0; j < d; ++j) {
-            int gj = __shfl_sync(0xffffffffu, gi, j);
-            if (lane < d && lane >= j) S.L[lane * kGD + j] = dd_two_sum(lane == j ? 1.0 : 0.0, -O[(size_t)gi * N2 + gj]);
-        }
-        __syncwarp();
-        // left-looking Cholesky, lane = row
-        for (int j = 0; j < d; ++j) {
-            if (lane == j) {
-                dd s = S.L[j * kGD + j];
-                for (int m = 0; m < j; ++m) s = s - S.L[j * kGD + m] * S.L[j * kGD + m];
-                if (!(s.hi > 0.0)) bad = true;
-                // sqrt by one Newton step from the double root
-                double x = sqrt(s.hi);
-                dd r = s - dd(x) * dd(x);
-                S.L[j * kGD + j] = dd_two_sum(x, r.hi / (2.0 * x));
+    const int n = s_n, m = n < kTM ? n : kTM, q = n - m, Dn = 2 * n;
+    for (int f = t; f < gsym(Dn); f += kTreeThreads) Gacc[f] = dd(0.0);
+    for (long long u = 0; n > 0 && u < (1ll << q); ++u) {
+        if (t == 0) {
+            int k = 0;
+            for (int a = 0; a < q; ++a)
+                if (u >> a & 1) {
+                    rowmode[2 * k] = 2 * a;
+                    rowmode[2 * k + 1] = 2 * a + 1;
+                    ++k;
+                }
+            for (int a = q; a < n; ++a) {
+                rowmode[2 * (k + a - q)] = 2 * a;
+                rowmode[2 * (k + a - q) + 1] = 2 * a + 1;
             }
-            __syncwarp();
-            if (lane > j && lane < d) {
-                dd s = S.L[lane * kGD + j];
-                for (int m = 0; m < j; ++m) s = s - S.L[lane * kGD + m] * S.L[j * kGD + m];
-                S.L[lane * kGD + j] = s / S.L[j * kGD + j];
-            }
-            __syncwarp();
+            s_k = k;
         }
-        // tau = prod 1/L_ii; sign (-1)^{n - k}
+        __syncthreads();
+        const int k = s_k, D0 = 2 * (k + m);
+        // the unit's rows of A = I - O (exact in double-double)
+        for (int f = t; f < gsym(D0); f += kTreeThreads) {
+            int i, j;
+            fold_ij(f, D0, i, j);
+            const int ri = rowmode[i], rj = rowmode[j];
+            const int gi = modes[ri >> 1] + (ri & 1) * M, gj = modes[rj >> 1] + (rj & 1) * M;
+            UM[gpidx(D0, i, j)] = dd_two_sum(i == j ? 1.0 : 0.0, -O[(size_t)gi * N2 + gj]);
+        }
+        __syncthreads();
         dd tau = dd(1.0);
-        for (int i = 0; i < d; ++i) tau = tau / S.L[i * kGD + i];
-        if ((n - k) & 1) tau = -tau;
-        tsum += tau;
-        // column `lane` of A_Z^{-1}: L y = e_lane, L^T x = y
-        if (lane < d) {
-            const int j = lane;
-            for (int i = 0; i < j; ++i) S.X[i * kGD + j] = dd(0.0);
-            S.X[j * kGD + j] = dd(1.0) / S.L[j * kGD + j];
-            for (int i = j + 1; i < d; ++i) {
-                dd s = dd(0.0);
-                for (int m = j; m < i; ++m) s += S.L[i * kGD + m] * S.X[m * kGD + j];
-                S.X[i * kGD + j] = -(s / S.L[i * kGD + i]);
+        for (int e = 0; e < k; ++e) tau = tau * tree_pivot(UM, D0, 2 * e, Yb, preQ + 3 * e, prers + e, &s_bad);
+        // level 0 of the subtree: the trailing 2m x 2m block
+        for (int f = t; f < gsym(2 * m); f += kTreeThreads) {
+            int i, j;
+            fold_ij(f, 2 * m, i, j);
+            Lv[gpidx(2 * m, i, j)] = UM[gpidx(D0, 2 * k + i, 2 * k + j)];
+        }
+        __syncthreads();
+        // forward: pivots of every level, children of every level but the last
+        for (int l = 0; l < m; ++l) {
+            const int d = 2 * (m - l), dc = d - 2, np = 1 << l, st = gsym(d), stc = gsym(dc);
+            const dd *Lp = Lv + lvl_off(l);
+            for (int c = t; c < np; c += kTreeThreads) {
+                const dd *P = Lp + c * st;
+                const dd p00 = P[gpidx(d, 0, 0)], p01 = P[gpidx(d, 0, 1)], p11 = P[gpidx(d, 1, 1)];
+                const dd det = dd_dot2(p00, p11, -p01, p01);
+                const dd rs = dd_rsqrt(det), inv = rs * rs;
+                const int node = np - 1 + c;
+                nQ[3 * node] = p11 * inv;
+                nQ[3 * node + 1] = -p01 * inv;
+                nQ[3 * node + 2] = p00 * inv;
+                nrs[node] = rs;
+                if (!(det.hi > 0.0)) atomicOr(&s_bad, 1);
             }
-            for (int i = d - 1; i >= 0; --i) {
-                dd s = S.X[i * kGD + j];
-                for (int m = i + 1; m < d; ++m) s = s - S.L[m * kGD + i] * S.X[m * kGD + j];
-                S.X[i * kGD + j] = s / S.L[i * kGD + i];
+            __syncthreads();
+            if (l == m - 1) break;
+            for (int f = t; f < np * dc; f += kTreeThreads) {
+                const int cp = f / dc, i = f - cp * dc, node = np - 1 + cp;
+                const dd *P = Lp + cp * st;
+                const dd b0 = P[gpidx(d, 0, i + 2)], b1 = P[gpidx(d, 1, i + 2)];
+                const dd q00 = nQ[3 * node], q01 = nQ[3 * node + 1], q11 = nQ[3 * node + 2];
+                Yb[2 * f] = dd_dot2(q00, b0, q01, b1);
+                Yb[2 * f + 1] = dd_dot2(q01, b0, q11, b1);
+            }
+            __syncthreads();
+            dd *Lc = Lv + lvl_off(l + 1);
+            for (int f = t; f < np * stc; f += kTreeThreads) {
+                const int cp = f / stc, e = f - cp * stc;
+                int i, j;
+                fold_ij(e, dc, i, j);
+                const dd *P = Lp + cp * st;
+                const dd *W = Yb + 2 * (cp * dc + i);
+                const dd v = P[gpidx(d, i + 2, j + 2)];
+                Lc[(2 * cp) * stc + gpidx(dc, i, j)] = v;
+                Lc[(2 * cp + 1) * stc + gpidx(dc, i, j)] =
+                    dd_fms2(v, W[0], P[gpidx(d, 0, j + 2)], W[1], P[gpidx(d, 1, j + 2)]);
+            }
+            __syncthreads();
+        }
+        // subtree sums, leaves up
+        for (int l = m - 1; l >= 0; --l) {
+            const int np = 1 << l;
+            for (int c = t; c < np; c += kTreeThreads) {
+                const int node = np - 1 + c;
+                if (l == m - 1) {
+                    nS[node] = nrs[node] - dd(1.0);
+                } else {
+                    const int ch = 2 * np - 1 + 2 * c;  // exclude child; ch + 1 includes
+                    nS[node] = nrs[node] * nS[ch + 1] - nS[ch];
+                }
+            }
+            __syncthreads();
+        }
+        if (t == 0) {
+            dd V = tau * nS[0];
+            if ((q - k) & 1) V = -V;
+            s_V = V;
+            s_T += V;
+        }
+        __syncthreads();
+        const dd V = s_V;
+        // reverse through the subtree: the last level's pivot blocks, then upwards
+        dd *Ach = base + ((m - 1) & 1 ? kOffAdjB : kOffAdjA);
+        for (int c = t; c < (1 << (m - 1)); c += kTreeThreads) {
+            const int node = (1 << (m - 1)) - 1 + c;
+            const dd h = nrs[node] * dd(-0.5);
+            Ach[3 * c] = h * nQ[3 * node];
+            Ach[3 * c + 1] = h * nQ[3 * node + 1];
+            Ach[3 * c + 2] = h * nQ[3 * node + 2];
+        }
+        __syncthreads();
+        for (int l = m - 2; l >= 0; --l) {
+            const int d = 2 * (m - l), dc = d - 2, np = 1 << l, st = gsym(d), stc = gsym(dc);
+            const dd *Lp = Lv + lvl_off(l);
+            const dd *Ac = base + ((l + 1) & 1 ? kOffAdjB : kOffAdjA);
+            dd *Ap = base + (l & 1 ? kOffAdjB : kOffAdjA);
+            // Y = P^{-1} B Gamma(inc), one column j per job
+            for (int f = t; f < np * dc; f += kTreeThreads) {
+                const int cp = f / dc, j = f - cp * dc, node = np - 1 + cp;
+                const dd *P = Lp + cp * st;
+                const dd *Gi = Ac + (2 * cp + 1) * stc;
+                dd z0 = dd(0.0), z1 = dd(0.0);
+                for (int i = 0; i < dc; ++i) {
+                    const dd g = Gi[gpany(dc, i, j)];
+                    z0 = z0 + P[gpidx(d, 0, i + 2)] * g;
+                    z1 = z1 + P[gpidx(d, 1, i + 2)] * g;
+                }
+                const dd q00 = nQ[3 * node], q01 = nQ[3 * node + 1], q11 = nQ[3 * node + 2];
+                Yb[2 * f] = dd_dot2(q00, z0, q01, z1);
+                Yb[2 * f + 1] = dd_dot2(q01, z0, q11, z1);
+            }
+            __syncthreads();
+            for (int f = t; f < np * st; f += kTreeThreads) {
+                const int cp = f / st, e = f - cp * st, node = np - 1 + cp;
+                int i, j;
+                fold_ij(e, d, i, j);
+                const dd rs = nrs[node];
+                dd g;
+                if (i >= 2) {
+                    g = rs * Ac[(2 * cp + 1) * stc + gpidx(dc, i - 2, j - 2)] - Ac[(2 * cp) * stc + gpidx(dc, i - 2, j - 2)];
+                } else if (j >= 2) {
+                    g = -(rs * Yb[2 * (cp * dc + j - 2) + i]);
+                } else {
+                    // (Y B^T P^{-1})(i, j) - S(inc) P^{-1}(i, j) / 2, times rs
+                    const dd *P = Lp + cp * st;
+                    dd yb0 = dd(0.0), yb1 = dd(0.0);
+                    for (int c = 0; c < dc; ++c) {
+                        const dd y = Yb[2 * (cp * dc + c) + i];
+                        yb0 = yb0 + y * P[gpidx(d, 0, c + 2)];
+                        yb1 = yb1 + y * P[gpidx(d, 1, c + 2)];
+                    }
+                    const dd qj0 = nQ[3 * node + (j == 0 ? 0 : 1)], qj1 = nQ[3 * node + (j == 0 ? 1 : 2)];
+                    const dd qij = nQ[3 * node + i + j];
+                    g = rs * (dd_dot2(yb0, qj0, yb1, qj1) - nS[2 * np - 1 + 2 * cp + 1] * qij * dd(0.5));
+                }
+                Ap[cp * st + gpidx(d, i, j)] = g;
+            }
+            __syncthreads();
+        }
+        // the unit's adjoint dV/dA_unit: the root's, scaled, then back through the prefix
+        {
+            const dd fac = (((q - k) & 1) ? -tau : tau);
+            const dd *Ar = base + kOffAdjA;  // level 0
+            for (int f = t; f < gsym(2 * m); f += kTreeThreads) {
+                int i, j;
+                fold_ij(f, 2 * m, i, j);
+                Gf[gpidx(D0, 2 * k + i, 2 * k + j)] = fac * Ar[gpidx(2 * m, i, j)];
             }
         }
-        __syncwarp();
-        // acc[loc_i][loc_j] += (-1/2) (+-tau) (A_Z^{-1})_{ij}; lanes own distinct columns
-        const dd c = tau * dd(-0.5);
-        for (int i = 0; i < d; ++i) {
-            int lr = __shfl_sync(0xffffffffu, li, i);
-            if (lane < d) S.acc[lr * D + li] += c * S.X[i * kGD + lane];
+        __syncthreads();
+        for (int e = k - 1; e >= 0; --e) {
+            const int c0 = 2 * e, R = D0 - c0 - 2;
+            const dd *Q = preQ + 3 * e;
+            for (int j = t; j < R; j += kTreeThreads) {
+                dd z0 = dd(0.0), z1 = dd(0.0);
+                for (int i = 0; i < R; ++i) {
+                    const dd g = Gf[gpany(D0, c0 + 2 + i, c0 + 2 + j)];
+                    z0 = z0 + UM[gpidx(D0, c0, c0 + 2 + i)] * g;
+                    z1 = z1 + UM[gpidx(D0, c0 + 1, c0 + 2 + i)] * g;
+                }
+                Yb[2 * j] = dd_dot2(Q[0], z0, Q[1], z1);
+                Yb[2 * j + 1] = dd_dot2(Q[1], z0, Q[2], z1);
+            }
+            __syncthreads();
+            for (int f = t; f < 2 * R + 3; f += kTreeThreads) {
+                if (f < 2 * R) {
+                    const int a = f / R, j = f - a * R;
+                    Gf[gpidx(D0, c0 + a, c0 + 2 + j)] = -Yb[2 * j + a];
+                } else {
+                    const int i = (f - 2 * R) == 2 ? 1 : 0, j = (f - 2 * R) == 0 ? 0 : 1;
+                    dd yb0 = dd(0.0), yb1 = dd(0.0);
+                    for (int c = 0; c < R; ++c) {
+                        const dd y = Yb[2 * c + i];
+                        yb0 = yb0 + y * UM[gpidx(D0, c0, c0 + 2 + c)];
+                        yb1 = yb1 + y * UM[gpidx(D0, c0 + 1, c0 + 2 + c)];
+                    }
+                    const dd qj0 = Q[j == 0 ? 0 : 1], qj1 = Q[j == 0 ? 1 : 2];
+                    Gf[gpidx(D0, c0 + i, c0 + j)] = dd_dot2(yb0, qj0, yb1, qj1) - V * Q[i + j] * dd(0.5);
+                }
+            }
+            __syncthreads();
         }
-        __syncwarp();
+        // into the pattern's Gbar at the unit's rows (the map keeps the order: i <= j)
+        for (int f = t; f < gsym(D0); f += kTreeThreads) {
+            int i, j;
+            fold_ij(f, D0, i, j);
+            dd &g = Gacc[gpidx(Dn, rowmode[i], rowmode[j])];
+            g = g + Gf[gpidx(D0, i, j)];
+        }
+        __syncthreads();
     }
-    if (lane == 0) {
-        s_T[wid][0] = tsum.hi;
-        s_T[wid][1] = tsum.lo;
-        if (bad) atomicOr(flags + p, 1);
+    // dense partial (row stride 2n) and T
+    for (int f = t; f < Dn * Dn; f += kTreeThreads) {
+        const int i = f / Dn, j = f - i * Dn;
+        const dd g = Gacc[gpany(Dn, i, j)];
+        part_hi[(size_t)p * kGD * kGD + f] = g.hi;
+        part_lo[(size_t)p * kGD * kGD + f] = g.lo;
     }
-    if (bad) atomicOr(flags + p, 1);
-    __syncthreads();
-    // sum the warps' shares (fixed order) and write the chunk partial
-    const size_t base = (size_t)cid * kGD * kGD;
-    for (int f = threadIdx.x; f < D * D; f += 32 * kGradWarps) {
-        dd s = ws[0].acc[f];
-        for (int w = 1; w < kGradWarps; ++w) s += ws[w].acc[f];
-        part_hi[base + f] = s.hi;
-        part_lo[base + f] = s.lo;
-    }
-    if (threadIdx.x == 0) {
-        dd t = dd(s_T[0][0], s_T[0][1]);
-        for (int w = 1; w < kGradWarps; ++w) t += dd(s_T[w][0], s_T[w][1]);
-        part_T[2 * cid] = t.hi;
-        part_T[2 * cid + 1] = t.lo;
+    if (t == 0) {
+        part_T[2 * p] = s_T.hi;
+        part_T[2 * p + 1] = s_T.lo;
+        if (s_bad) atomicOr(flags + p, 1);
     }
 }
 
@@ -299,7 +501,6 @@ __global__ void grad_params_kernel(int M, const double *__restrict__ U, const do
 
 // the rectangular mesh: cell order of layer l = pairs (m, m+1) with m of the parity of l
 __device__ __forceinline__ int cell_mode(int M, int c) {
-    int per2 = M - 1;  // cells in two consecutive layers (M/2 + (M-1)/2 ... for any M)
     int layer = 0, base = 0;
     for (;;) {
         int cnt = (M - 1 - (layer & 1) + 1) / 2;  // m = parity, parity+2, ... < M - 1
@@ -307,7 +508,6 @@ __device__ __forceinline__ int cell_mode(int M, int c) {
         base += cnt;
         ++layer;
     }
-    (void)per2;
 }
 
 __global__ void clements_unitary_kernel(int M, const double *__restrict__ theta, const double *__restrict__ phi,
@@ -396,17 +596,11 @@ __global__ void clements_grad_kernel(int M, const double *__restrict__ theta, co
     }
 }
 
-__global__ void grad_plan_kernel(const uint64_t *__restrict__ pats, int n_pat, int M,
-                                 long long *__restrict__ chunk_off, int *__restrict__ flags) {
-    if (threadIdx.x || blockIdx.x) return;
-    long long run = 0;
-    for (int p = 0; p < n_pat; ++p) {
-        chunk_off[p] = run;
-        int n = __popcll(pats[2 * p]) + __popcll(pats[2 * p + 1]);
-        run += n > kChunkLog ? (1ll << (n - kChunkLog)) : 1;
-        flags[p] = 0;
-    }
-    chunk_off[n_pat] = run;
+// one partial per pattern
+__global__ void grad_plan_kernel(int n_pat, long long *__restrict__ chunk_off, int *__restrict__ flags) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p <= n_pat) chunk_off[p] = p;
+    if (p < n_pat) flags[p] = 0;
 }
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -422,7 +616,7 @@ int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
     if (!hp) return gbs_fail(ctx, GBS_E_NOMEM, "gbs_grad: host buffer");
     GBS_CUDA(ctx, cudaMemcpyAsync(hp, pats, pb, cudaMemcpyDeviceToHost, ctx->stream));
     GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    long long chunks = 0;
+    const long long chunks = n_pat;
     for (int p = 0; p < n_pat; ++p) {
         uint64_t lo = hp[2 * p], hi = hp[2 * p + 1];
         int n = __builtin_popcountll(lo) + __builtin_popcountll(hi);
@@ -432,7 +626,6 @@ int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
             return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad: pattern %d has %d clicks (at most %d) or a detector >= M",
                             p, n, kGradMaxN);
         }
-        chunks += n > kChunkLog ? (1ll << (n - kChunkLog)) : 1;
     }
     free(hp);
     const int N = 2 * M;
@@ -449,14 +642,13 @@ int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
     double *phi_ = (double *)(b + o_phi), *plo = (double *)(b + o_plo), *pT = (double *)(b + o_pT);
     double *F = (double *)(b + o_F), *H = (double *)(b + o_H), *T1 = (double *)(b + o_T1),
            *T2 = (double *)(b + o_T2), *sw = (double *)(b + o_sw);
-    grad_plan_kernel<<<1, 32, 0, ctx->stream>>>(pats, n_pat, M, chunk_off, flags);
+    grad_plan_kernel<<<(n_pat + 1 + 255) / 256, 256, 0, ctx->stream>>>(n_pat, chunk_off, flags);
     GBS_CUDA(ctx, cudaGetLastError());
-    const size_t smem = sizeof(GradWarpSmem) * kGradWarps;
-    GBS_CUDA(ctx, cudaFuncSetAttribute(grad_subsets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = sizeof(dd) * (size_t)kTreeSmem;
+    GBS_CUDA(ctx, cudaFuncSetAttribute(grad_tree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     st = gbs_timing_begin(ctx);
     if (st) return st;
-    grad_subsets_kernel<<<(unsigned)chunks, 32 * kGradWarps, smem, ctx->stream>>>(M, O, pats, n_pat, chunk_off,
-                                                                                   phi_, plo, pT, flags);
+    grad_tree_kernel<<<n_pat, kTreeThreads, smem, ctx->stream>>>(M, O, pats, n_pat, phi_, plo, pT, flags);
     GBS_CUDA(ctx, cudaGetLastError());
     st = gbs_timing_end(ctx);
     if (st) return st;

@@ -61,11 +61,13 @@ def test_grad_params_chain(ctx):
 
 @pytest.mark.parametrize("eta", [1.0, 0.6])
 def test_dsigmaQ_matches_oracle(ctx, eta):
-    M = 8
+    # sizes below, at and above the 7-mode subtree of a unit: n > 7 runs 2^(n-7) units
+    # with up to n - 7 eliminated prefix modes
+    M = 14
     U = g.haar_unitary(M, 21)
-    r = g.squeezing(M, 5, 0.5, 1.1, 21)
+    r = g.squeezing(M, 8, 0.5, 1.1, 21)
     rng = np.random.default_rng(4)
-    mode_sets = [sorted(rng.choice(M, size=n, replace=False)) for n in (0, 1, 3, 5, 6, 8)]
+    mode_sets = [sorted(rng.choice(M, size=n, replace=False)) for n in (0, 1, 3, 5, 7, 8, 10, 12)]
     pats = np.stack([g.modes_to_pattern(m) for m in mode_sets])
     w = rng.standard_normal(len(pats))
     st = ctx.build_state(U, r, eta)
@@ -122,10 +124,38 @@ def test_m32_workload_gradients(ctx):
         assert abs(fd - tht.grad[cc].item()) < 1e-6 * abs(fd) + 5e-6, cc
 
 
+def test_n20_gradient_against_central_differences(ctx):
+    # a 20-click pattern of the 24-mode device (2^13 units of the tree adjoint): dL/dr
+    # through the chain against central differences of the fixed-point log P
+    c = g.CONFIGS["m24_exact"]
+    U, r = c.unitary(), c.squeezing()
+    modes = [m for m in range(24) if m not in (2, 9, 15, 22)]
+    pats = g.modes_to_pattern(modes)[None]
+    st = ctx.build_state(U, r, c.eta)
+    dsq, logP, status = ctx.grad(st["O"], st["logdet"], pats, dev(np.ones(1)))
+    assert status.item() == 0
+    Ud = torch.view_as_real(dev(U)).reshape(c.M, 2 * c.M).contiguous()
+    _, dr, deta = ctx.grad_params(Ud, dev(r), c.eta, dsq)
+    lp_fx = ctx.prob(st["O"], st["logdet"], pats, precision="fx")["logP"].item()
+    assert abs(logP.item() - lp_fx) < 1e-10
+
+    def lp(rv, ev):
+        s2 = ctx.build_state(U, rv, ev)
+        return ctx.prob(s2["O"], s2["logdet"], pats, precision="fx")["logP"].item()
+
+    h = 1e-6
+    for j in (0, 5, 11):
+        e = np.zeros(c.M); e[j] = h
+        fd = (lp(r + e, c.eta) - lp(r - e, c.eta)) / (2 * h)
+        assert abs(fd - dr[j].item()) < 1e-6 * abs(fd) + 1e-7, (j, fd, dr[j].item())
+    fd = (lp(r, c.eta + h) - lp(r, c.eta - h)) / (2 * h)
+    assert abs(fd - deta.item()) < 1e-6 * abs(fd) + 1e-7
+
+
 def test_grad_rejects_large_patterns(ctx):
     from paper_2106_01445_gb300 import GbsError
-    M = 20
+    M = 30
     st = ctx.build_state(g.haar_unitary(M, 3), g.squeezing(M, 5, 0.5, 1.0, 3), 0.7)
-    pats = g.modes_to_pattern(list(range(17)))[None]
+    pats = g.modes_to_pattern(list(range(25)))[None]
     with pytest.raises(GbsError):
         ctx.grad(st["O"], st["logdet"], pats, dev(np.ones(1)))
