@@ -69,10 +69,11 @@ def approx_unit_flops(n: int, j: int) -> float:
 
 
 def adjoint_flops(n: int) -> float:
-    """Algorithmic flops of the exact adjoint over the 2^n subsets Z of S: per subset a
-    Cholesky of A_Z ((2z)^3 / 3), its inverse from the factor (2 (2z)^3 / 3) and the
-    weighted accumulation into Gbar ((2z)^2)."""
-    return float(sum(math.comb(n, z) * ((2 * z) ** 3 + (2 * z) ** 2) for z in range(n + 1)))
+    """Algorithmic flops of the exact adjoint Gbar = dT/dA_S in reverse mode through
+    the Schur recursion: the forward recursion F(n) (schur_flops) and its reverse, 3 F(n)
+    (per include step Z = B Gamma costs 4 flops per trailing entry against the forward
+    update's 2, plus the rest-block combination)."""
+    return 4.0 * schur_flops(n)
 
 
 def workload(name: str, rank: int, world: int):
@@ -491,7 +492,7 @@ def run_workloads(dev, stream, meas, fp32_peak):
     ds_orc = ograd.grad_sigmaQ(st_or, pats[chk], np.ones(len(chk)))
     res["m32_grad"] = {"patterns": len(pats), "params": 2 * len(th) + c.M + 1,
                        "ms_forward_and_backward": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
-                       "roofline_adjoint": {"bound": "alu", "kernel": "grad_subsets_kernel (double-double)",
+                       "roofline_adjoint": {"bound": "alu", "kernel": "grad_tree_kernel (double-double)",
                                             "kernel_ms": kms_adj, "flops": fl,
                                             "achieved_tflops": fl / (kms_adj * 1e-3) / 1e12,
                                             "peak_tflops": meas["dd"] / 1e12,
