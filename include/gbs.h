@@ -135,6 +135,20 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
                  const uint64_t *patterns_host, int n_pat, int order, int precision,
                  double *logP_host, double *kappa_host, double *err_host, int32_t *status_host);
 
+/* Whole-device click-number distribution (Methods, "Model": the sum of P(S) over the
+ * C(M, n) patterns with n clicks; the paper's exact p(n) curve).  Every pattern S with n
+ * clicks contains a subset Z in C(M - |Z|, n - |Z|) ways, so
+ *   p(n) = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n - z} C(M - z, n - z) E_z,
+ *   E_z  = sum over the subsets Z of the M modes with |Z| = z of det(A_Z)^{-1/2}:
+ * one double-double sweep over all 2^M subsets with the terms binned by size, then the
+ * binomial transform in double-double with exact binomials.  4 <= M <= 40 (2^M subsets:
+ * about a second at M = 30).  logp, kappa: M + 1 doubles (device; kappa may be NULL),
+ * kappa[n] = sum_z C(M - z, n - z) E_z / |sum with signs|, the transform's cancellation;
+ * logp[n] = NaN where the sum is not positive or a pivot was not.  Errors:
+ * GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
+int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, double *logp,
+                           double *kappa);
+
 /* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
  * has no counterpart: this serves callers that cannot call cudaMalloc (code
  * running under another owner's stream capture, processes whose device memory

@@ -80,6 +80,14 @@ class Context:
     def reserve(self, n_pat: int, n_max: int):
         self._check(self.lib.gbs_reserve(self.h, n_pat, n_max))
 
+    def click_distribution(self, O: torch.Tensor, logdet: torch.Tensor):
+        """(log p(n), kappa_n) for n = 0..M: the whole device's click-number distribution."""
+        M = O.shape[0] // 2
+        logp = torch.empty(M + 1, dtype=torch.float64, device=self.device)
+        kappa = torch.empty(M + 1, dtype=torch.float64, device=self.device)
+        self._check(self.lib.gbs_click_distribution(self.h, M, _ptr(O), _ptr(logdet), _ptr(logp), _ptr(kappa)))
+        return logp, kappa
+
     def autotune(self, O: torch.Tensor, logdet: torch.Tensor, patterns, precision="fx"):
         """Pick the exact sweep's work split for this precision on these patterns
         (kept in the context); returns (split, ms of one sweep).  Synchronous; call it

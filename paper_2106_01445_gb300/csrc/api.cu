@@ -156,6 +156,15 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
     return GBS_OK;
 }
 
+int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, double *logp,
+                           double *kappa) {
+    if (!ctx) return GBS_E_INVALID;
+    if (!O || !logdet_sigmaQ || !logp)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: null pointer");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return click_distribution(ctx, M, O, logdet_sigmaQ, logp, kappa);
+}
+
 int gbs_autotune(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
                  const uint64_t *patterns, int n_pat, int precision, int *best_split, double *best_ms) {
     if (!ctx) return GBS_E_INVALID;

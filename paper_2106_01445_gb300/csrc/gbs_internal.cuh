@@ -70,6 +70,8 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
 size_t sweep_workspace_bytes(int n_pat, long long units);
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split);
 int sweep_split_of(const gbs_ctx *ctx, int precision);
+int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
+                       double *kappa);
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);

@@ -262,8 +262,27 @@ template <typename T, int MD> struct SmemMat {
 // Subtree of the node whose matrix is A viewed from mode O on (MD - O modes).
 // NEG: the node's leaves carry a minus sign relative to the subtree root.
 // Levels at depth >= nreal are padding modes (identity block): include only.
-template <typename T, int MD, int O, bool NEG, typename Src>
-__device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, Acc<T> &acc) {
+// the two leaves of a last-level node: include (+tau rs) and exclude (-tau), signed
+// into the subtree sum; or, binned by subset size (cnt = modes included so far in the
+// subtree), unsigned into the size bins
+template <bool NEG, typename T>
+__device__ __forceinline__ void leaf_pair(Acc<T> &acc, T inc, T tau, bool real, int) {
+    T comb = real ? inc - tau : inc;
+    acc_add(acc, NEG ? -comb : comb);
+    acc.abs += real ? abs_part(inc) + abs_part(tau) : abs_part(inc);
+}
+template <typename T, int NB> struct BinAcc {
+    T v[NB];
+    int bad;
+};
+template <bool NEG, typename T, int NB>
+__device__ __forceinline__ void leaf_pair(BinAcc<T, NB> &acc, T inc, T tau, bool real, int cnt) {
+    acc.v[cnt + 1] += inc;
+    if (real) acc.v[cnt] += tau;
+}
+
+template <typename T, int MD, int O, bool NEG, typename Src, typename AccT>
+__device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, AccT &acc, int cnt) {
     constexpr int m = MD - O;
     constexpr int o = 2 * O;
     const T p00 = A(o, o), p01 = A(o, o + 1), p11 = A(o + 1, o + 1);
@@ -272,11 +291,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
         const T det = det2(p00, p01, p11);
         if constexpr (Prec<T>::fixed) acc.bad |= pivot_bad(det);
         const T rs = rsq<T>(det);
-        // the two leaves: include (+tau rs) and exclude (-tau)
-        const T inc = mul_pos(tau, rs);
-        T comb = real ? inc - tau : inc;
-        acc_add(acc, NEG ? -comb : comb);
-        acc.abs += real ? abs_part(inc) + abs_part(tau) : abs_part(inc);
+        leaf_pair<NEG>(acc, mul_pos(tau, rs), tau, real, cnt);
     } else if constexpr (Prec<T>::fixed) {
         // symmetric form C - U U^T, U = B R^{-T} (offset rows)
         constexpr int d = 2 * (m - 1);
@@ -291,8 +306,8 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 #pragma unroll
             for (int j = i; j < d; ++j)
                 C.v[pidx(d, i, j)] = fx_sym_update(A(o + 2 + i, o + 2 + j), u0[i], u1[i], tt[i], u0[j], u1[j], tt[j]);
-        dfs<T, m - 1, 0, NEG>(C, fx_mul_uu(tau, v.rs), depth + 1, nreal, acc);
-        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc);
+        dfs<T, m - 1, 0, NEG>(C, fx_mul_uu(tau, v.rs), depth + 1, nreal, acc, cnt + 1);
+        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc, cnt);
     } else {
         constexpr int d = 2 * (m - 1);
         const T det = det2(p00, p01, p11);
@@ -313,8 +328,8 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 #pragma unroll
             for (int j = i; j < d; ++j)
                 C.v[pidx(d, i, j)] = fms2(A(o + 2 + i, o + 2 + j), w0[i], b0[j], w1[i], b1[j]);
-        dfs<T, m - 1, 0, NEG>(C, tau * rs, depth + 1, nreal, acc);
-        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc);
+        dfs<T, m - 1, 0, NEG>(C, tau * rs, depth + 1, nreal, acc, cnt + 1);
+        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc, cnt);
     }
 }
 
@@ -459,7 +474,9 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
 }
 
 // ---- the sweep ------------------------------------------------------------------
-template <typename T>
+// BIN: the click-number distribution mode (one pattern = all M modes): the subset
+// terms are summed unsigned into bins by subset size instead of into the signed sum
+template <typename T, bool BIN = false>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__restrict__ O,
                                                         const uint64_t *__restrict__ pats,
                                                         int n_pat, Plan pl) {
@@ -478,6 +495,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     uint16_t *dec = (uint16_t *)(smem + Lay::off_dec);
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
+    __shared__ int s_base[kThreads];        // binned mode: modes included above each bottom node
+    __shared__ dd s_ubin[kMaxN + 1];        // binned mode: the unit's size bins
     __shared__ fx s_vred[kThreads / 32];    // fixed point: per-warp aligned sums
     __shared__ float s_ared[kThreads / 32];
     __shared__ int s_ered[kThreads / 32];
@@ -588,6 +607,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         }
         __syncthreads();
         double u_hi = 0.0, u_lo = 0.0, u_abs = 0.0;
+        if constexpr (BIN) {
+            for (int z = t; z <= n; z += kThreads) s_ubin[z] = dd(0.0);
+        }
         for (int sub = 0; sub < (1 << ss); ++sub) {
             // sub-unit: include the set bits of `sub` among the next ss modes
             const int kk = __popc(sub);
@@ -707,7 +729,42 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 __syncthreads();
             }
             // register-resident bottom B levels, one node per thread
-            if constexpr (Prec<T>::fixed) {
+            if constexpr (BIN) {
+                // the thread's subtree bins (relative sizes 0..B), scaled by its prefactor,
+                // then every size bin summed over the threads in a fixed order
+                constexpr int NB = B + 1;
+                BinAcc<T, NB> acc;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc.v[b] = konst<T>(0.0);
+                acc.bad = 0;
+                const bool has = t < (1 << L_eff);
+                if (has) {
+                    const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
+                    const Node tn = ((L_eff & 1) ? tauY : tauX)[t];
+                    const int nreal = n - (n_eff - B);
+                    SmemMat<T, B> A{node};
+                    dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc, 0);
+                    const Tau sc = Tau(tn) * tsub;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) acc.v[b] = sc * acc.v[b];
+                    if (is_nan(tn)) atomicOr(&s_flag, 1);
+                }
+                __syncthreads();  // the nodes are read: X is scratch until the next sub-unit
+                T *tb = X;
+                if (has)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) tb[t * NB + b] = acc.v[b];
+                s_base[t] = has ? k + kk + __popc(t) : -(1 << 20);
+                __syncthreads();
+                for (int z = t; z <= n; z += kThreads) {
+                    T sz = konst<T>(0.0);
+                    for (int t2 = 0; t2 < (1 << L_eff); ++t2) {
+                        const int b = z - s_base[t2];
+                        if (b >= 0 && b < NB) sz += tb[t2 * NB + b];
+                    }
+                    s_ubin[z] = s_ubin[z] + sz;
+                }
+            } else if constexpr (Prec<T>::fixed) {
                 // each thread's subtree sum relative to its prefactor m 2^e, then one
                 // exponent-aligned fixed-point sum over the CTA: a single conversion to
                 // double-double per sub-unit
@@ -720,7 +777,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int nreal = n - (n_eff - B);
                     Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
                     SmemMat<T, B> A{node};
-                    dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc);
+                    dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc, 0);
                     const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
                     v = fx_neg_if(fx_mul_su(acc.hi, tn.m), excl & 1);   // |v| < 2^11
                     e = tn.e;
@@ -765,7 +822,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const int nreal = n - (n_eff - B);
                 Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
                 SmemMat<T, B> A{node};
-                dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc);
+                dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc, 0);
                 const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
                 const Tau sc = Tau((excl & 1) ? -1.0 : 1.0) * Tau(tau_node) * tsub;
                 double sh, sl;
@@ -775,6 +832,18 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 if (is_nan(acc.abs) || is_nan(tau_node)) atomicOr(&s_flag, 1);
             }
             __syncthreads();   // X / Y are rewritten by the next sub-unit
+        }
+        if constexpr (BIN) {
+            // the unit's bins times its prefix factor (thread z owns bin z)
+            double *out = pl.partials + (size_t)2 * (n + 1) * u;
+            for (int z = t; z <= n; z += kThreads) {
+                const dd v = tpre * s_ubin[z];
+                out[2 * z] = v.hi;
+                out[2 * z + 1] = v.lo;
+            }
+            if (t == 0 && (s_flag || is_nan(tpre))) atomicOr(pl.pflags + sp, 1);
+            __syncthreads();
+            continue;
         }
         double c_hi = u_hi, c_lo = u_lo, c_abs = u_abs;
         // deterministic CTA reduction (TwoSum tree)
@@ -1009,6 +1078,64 @@ int run_sweep_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O
     return GBS_OK;
 }
 
+// ---- click-number distribution: bins of all subsets of the M modes by size ----------
+__global__ void all_modes_kernel(int M, uint64_t *pat) {
+    pat[0] = M >= 64 ? ~0ull : ((1ull << M) - 1);
+    pat[1] = M > 64 ? (M >= 128 ? ~0ull : ((1ull << (M - 64)) - 1)) : 0ull;
+}
+
+// per chunk of 1024 units: every size bin summed in unit order
+__global__ void bins_chunk_kernel(int nb, const double *__restrict__ partials, const long long *__restrict__ units_p,
+                                  double *__restrict__ chunks) {
+    const long long c = blockIdx.x, units = *units_p;
+    const long long u0 = c * 1024, u1 = (c + 1) * 1024 < units ? (c + 1) * 1024 : units;
+    for (int z = threadIdx.x; z < nb; z += blockDim.x) {
+        dd acc = dd(0.0);
+        for (long long u = u0; u < u1; ++u)
+            acc += dd(partials[(size_t)2 * nb * u + 2 * z], partials[(size_t)2 * nb * u + 2 * z + 1]);
+        chunks[(size_t)2 * nb * c + 2 * z] = acc.hi;
+        chunks[(size_t)2 * nb * c + 2 * z + 1] = acc.lo;
+    }
+}
+
+// E_z = sum_{|Z| = z} det(A_Z)^{-1/2} from the chunks, then
+//   p(n) = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n - z} C(M - z, n - z) E_z
+// (every pattern S with n clicks contains the subset Z in C(M - z, n - z) ways), in
+// double-double with exact binomials; kappa_n = sum_z C E_z / |S_n|
+__global__ void bins_final_kernel(int M, long long nchunks, const double *__restrict__ chunks,
+                                  const double *__restrict__ logdet, const int *__restrict__ pflags,
+                                  const int *__restrict__ overflow, double *__restrict__ logp,
+                                  double *__restrict__ kappa) {
+    __shared__ dd E[kMaxN + 1];
+    __shared__ double Cb[kMaxN + 1][kMaxN + 1];
+    const int t = threadIdx.x, nb = M + 1;
+    for (int z = t; z < nb; z += blockDim.x) {
+        dd acc = dd(0.0);
+        for (long long c = 0; c < nchunks; ++c)
+            acc += dd(chunks[(size_t)2 * nb * c + 2 * z], chunks[(size_t)2 * nb * c + 2 * z + 1]);
+        E[z] = acc;
+    }
+    for (int a = t; a <= M; a += blockDim.x) {
+        Cb[a][0] = 1.0;
+        for (int b = 1; b <= a; ++b) Cb[a][b] = Cb[a][b - 1] * (double)(a - b + 1) / (double)b;  // exact below 2^53
+    }
+    __syncthreads();
+    const bool bad = *overflow || pflags[0];
+    for (int n = t; n <= M; n += blockDim.x) {
+        dd S = dd(0.0);
+        double A = 0.0;
+        for (int z = 0; z <= n; ++z) {
+            const double c = Cb[M - z][n - z];
+            const dd term = dd(c) * E[z];
+            S = ((n - z) & 1) ? S - term : S + term;
+            A += c * fabs(E[z].hi);
+        }
+        const bool ok = !bad && S.hi > 0.0;
+        logp[n] = ok ? -0.5 * (*logdet) + log(S.hi) + log1p(S.lo / S.hi) : nan("");
+        if (kappa) kappa[n] = bad ? nan("") : A / fabs(S.hi);
+    }
+}
+
 }  // namespace
 
 int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
@@ -1053,4 +1180,43 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
     if (precision == GBS_FX)
         return run_sweep<fx>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+}
+
+int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
+                       double *kappa) {
+    using T = dd;
+    using Lay = Layout<T>;
+    if (M < 4 || M > kMaxN)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: M = %d outside 4..%d", M, kMaxN);
+    const int split = sweep_split_of(ctx, GBS_DD);
+    const long long units = sweep_units_upper_bound(1, M, GBS_DD, split);
+    const int nb = M + 1;
+    const long long nch = (units + 1023) / 1024;
+    const WsOffsets o = ws_offsets(1, 0);
+    const size_t off_ch = align256(o.partials + (size_t)16 * nb * units);
+    const size_t off_pat = align256(off_ch + (size_t)16 * nb * nch);
+    int st = gbs_ws_ensure(ctx, off_pat + 16);
+    if (st) return st;
+    Plan pl = plan_from(ctx->ws, 1);
+    pl.split = split;
+    double *chunks = (double *)((char *)ctx->ws + off_ch);
+    uint64_t *pat = (uint64_t *)((char *)ctx->ws + off_pat);
+    all_modes_kernel<<<1, 1, 0, ctx->stream>>>(M, pat);
+    plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pat, 1, units, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    GBS_CUDA(ctx, cudaFuncSetAttribute(sweep_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Lay::bytes));
+    int nbk = 0;
+    GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, sweep_kernel<T, true>, kThreads, Lay::bytes));
+    if (nbk < 1) return gbs_fail(ctx, GBS_E_CUDA, "binned sweep kernel does not fit on an SM");
+    st = gbs_timing_begin(ctx);
+    if (st) return st;
+    sweep_kernel<T, true><<<ctx->num_sms * nbk, kThreads, Lay::bytes, ctx->stream>>>(M, O, pat, 1, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    st = gbs_timing_end(ctx);
+    if (st) return st;
+    bins_chunk_kernel<<<(unsigned)nch, 64, 0, ctx->stream>>>(nb, pl.partials, pl.unit_off + 1, chunks);
+    bins_final_kernel<<<1, 64, 0, ctx->stream>>>(M, nch, chunks, logdet, pl.pflags, pl.overflow, logp, kappa);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
 }
