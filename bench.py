@@ -534,6 +534,25 @@ def run_workloads(dev, stream, meas, fp32_peak):
                                 "peak_tflops": fp32_peak / 1e12, "frac": fl / (kms * 1e-3) / fp32_peak},
             "anchors_ff_vs_exact": {"median_rel_dP": float(np.median(rel)), "max_rel_dP": float(rel.max())}}
     res["m100_approx"] = entry
+
+    # ---- the paper's device shape (30 modes, 15 inputs squeezed r = 1.4, lossless): the
+    # exact click-number distribution over all 2^30 subsets, and the all-click point by
+    # orders 2-4 (float-float minors) against the exact sum
+    c = g.CONFIGS["m30_device"]
+    U, r = c.unitary(), c.squeezing()
+    st = ctx.build_state(U, r, c.eta)
+    ms, kms, (logp, kap) = timed(lambda: ctx.click_distribution(st["O"], st["logdet"]))
+    pn = np.exp(logp.cpu().numpy())
+    allp = g.modes_to_pattern(list(range(c.M)))[None]
+    ex = host(ctx.prob(st["O"], st["logdet"], allp, precision="fx"))
+    entry = {"M": c.M, "subsets": 2.0 ** c.M, "click_distribution_ms": ms, "sweep_kernel_ms": kms,
+             "subsets_per_s": 2.0 ** c.M / (ms * 1e-3), "sum_p_minus_1": float(pn.sum() - 1.0),
+             "p_n": [float(x) for x in pn], "kappa_max": float(np.nanmax(kap.cpu().numpy())),
+             "all_click": {"exact_logP": float(ex["logP"][0]), "err_bound": float(ex["err_bound"][0])}}
+    for order in (2, 3, 4):
+        a = host(ctx.prob(st["O"], st["logdet"], allp, order=order, precision="ff"))
+        entry["all_click"]["order%d_rel_dev" % order] = float(np.expm1(a["logP"][0] - ex["logP"][0]))
+    res["m30_device"] = entry
     ctx.close()
     return res
 

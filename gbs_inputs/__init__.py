@@ -244,7 +244,9 @@ class Config:
                             stream=STREAM_ANCHORS)
 
 
-# The five workloads.  Seeds: workload c uses seed c (the 8-mode one uses 0).
+# The five benchmark workloads, and the 30-mode device shape of the paper's click-number
+# figures (15 inputs squeezed r = 1.4, lossless).  Seeds: workload c uses seed c (the
+# 8-mode one uses 0).
 CONFIGS = {
     "m8_all": Config("m8_all", M=8, K=8, r_lo=0.8, r_hi=0.8, eta=1.0, interferometer="haar",
                      seed=0, note="all 256 patterns, sum must be 1"),
@@ -258,4 +260,6 @@ CONFIGS = {
     "m100_approx": Config("m100_approx", M=100, K=50, r_lo=1.1, r_hi=1.6, eta=0.3,
                           interferometer="haar", seed=5, n_lo=40, n_hi=90, n_pat=16384,
                           orders=(2, 3, 4), exact_n_max=0, anchors=64, anchor_n=30),
+    "m30_device": Config("m30_device", M=30, K=15, r_lo=1.4, r_hi=1.4, eta=1.0, interferometer="haar",
+                         seed=6, note="whole-device p(n); the all-click point by orders 2-4"),
 }
