@@ -215,20 +215,89 @@ __device__ __forceinline__ int fx_pivot_bad(const fx &det) {
     if (!fx_positive(det)) return 1;
     return (int32_t)det.w[3] < 256 ? 2 : 0;
 }
-// the same for a pivot block given by its Cholesky quantities: p00 and the Schur
-// remainder x = det / p00 positive, rs = det^{-1/2} below 16 (det >= 2^-8)
-__device__ __forceinline__ int fx_chol_bad(const fx &p00, const fx &x, const fx &rs) {
-    if (!fx_positive(p00) || !fx_positive(x)) return 1;
-    return (int32_t)rs.w[3] >= (16 << 16) ? 2 : 0;
+// the same for a pivot block given by p00 and det: both positive, det >= 2^-8
+__device__ __forceinline__ int fx_chol_bad(const fx &p00, const fx &det) {
+    if (!fx_positive(p00)) return 1;
+    return fx_pivot_bad(det);
 }
 
-// x^{-1/2} for x in [2^-9, 4]: double estimate y, one Newton step y (1 + e/2),
-// e = 1 - x y^2, in fixed point: relative error ~ (3/8) (2^-52)^2.  x <= 0 gives 0.
-__device__ __forceinline__ fx fx_rsqrt(const fx &x) {
-    const double y = rsqrt(fx_to_double(x));
-    const fx y0 = fx_from_double(y);
-    const fx e = fx_one() - fx_mul_uu(x, fx_mul_uu(y0, y0));
-    return y0 + fx_half(fx_mul_su(e, y0));
+// floor(A R / 2^64) for A < 2^127 and R < 2^64 (limbs of columns 2..5 of the 192-bit
+// product); the partial products of columns 0 and 1 are dropped (result low by <= 3)
+__device__ __forceinline__ fx fx_mul_r64(const fx &a, unsigned long long R) {
+    const uint32_t r0 = (uint32_t)R, r1 = (uint32_t)(R >> 32);
+    fx q;
+    asm("mul.lo.u32 %0, %6, %8;\n\t"
+        "mul.lo.u32 %1, %7, %8;\n\t"
+        "mad.hi.cc.u32 %0, %5, %8, %0;\n\t"
+        "madc.hi.cc.u32 %1, %6, %8, %1;\n\t"
+        "madc.hi.u32 %2, %7, %8, 0;\n\t"
+        "mad.lo.cc.u32 %0, %5, %9, %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %9, %1;\n\t"
+        "madc.lo.cc.u32 %2, %7, %9, %2;\n\t"
+        "addc.u32 %3, 0, 0;\n\t"
+        "mad.hi.cc.u32 %0, %4, %9, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %9, %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %9, %2;\n\t"
+        "madc.hi.u32 %3, %7, %9, %3;"
+        : "=&r"(q.w[0]), "=&r"(q.w[1]), "=&r"(q.w[2]), "=&r"(q.w[3])
+        : "r"(a.w[0]), "r"(a.w[1]), "r"(a.w[2]), "r"(a.w[3]), "r"(r0), "r"(r1));
+    return q;
+}
+
+// x^{-1/2} for x in [2^-16, 2^16) (pivots lie in [2^-8, 4]), built for a short
+// dependency chain (Newton's iteration r <- r + r e / 2, e = 1 - x r^2):
+//  * x = x_m 4^h with x_m = W / 2^64 in [1/4, 1), W the 64 bits after the leading zeros;
+//  * an FP32 estimate of r = x_m^{-1/2} in (1, 2] (~22 bits);
+//  * two Newton steps on W in 64-bit integer arithmetic, R = r 2^61 (~56 bits);
+//  * one Newton step against the whole of x: e from the top 128 bits of X R^2 (X the
+//    normalised 128-bit x), then y += y e / 2 (error ~ (3/2) e^2 + truncation 2^-110).
+// Inputs outside the range (checked by the callers) give a finite, meaningless result.
+static __device__ __noinline__ fx fx_rsqrt(fx x) {
+    uint32_t lz = __clz(x.w[3]);
+    lz = lz < 1u ? 1u : (lz > 31u ? 31u : lz);
+    int k = 16 - (int)lz;  // x = (W / 2^64) 2^k
+    unsigned long long W = ((unsigned long long)__funnelshift_l(x.w[2], x.w[3], lz) << 32) |
+                           __funnelshift_l(x.w[1], x.w[2], lz);
+    const int odd = k & 1;
+    W >>= odd;
+    k += odd;
+    const int h = k / 2;
+    // FP32 estimate, turned into R = r 2^61 through its bits
+    const float rf = rsqrtf(__uint2float_rn((uint32_t)(W >> 32)) * 0x1p-32f);
+    const uint32_t fb = __float_as_uint(rf);
+    int s0 = (int)((fb >> 23) & 0xffu) - 127 + 38;
+    s0 = s0 < 0 ? 0 : (s0 > 39 ? 39 : s0);
+    unsigned long long R = (unsigned long long)((fb & 0x7fffffu) | 0x800000u) << s0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const unsigned long long S = __umul64hi(R, R);         // r^2 2^58
+        const unsigned long long P = __umul64hi(W, S);         // x_m r^2 2^58
+        const long long E = (long long)((1ull << 58) - P);     // e 2^58
+        R += (unsigned long long)__mul64hi((long long)R, (long long)((unsigned long long)E << 5));
+    }
+    // y = r 2^-h in Q16.112: Y = R 2^(51 - h)
+    int s2 = 19 - h;
+    s2 = s2 < 11 ? 11 : (s2 > 26 ? 26 : s2);
+    const uint32_t q0 = (uint32_t)R, q1 = (uint32_t)(R >> 32);
+    const fx y{{0u, q0 << s2, __funnelshift_l(q0, q1, s2), q1 >> (32 - s2)}};
+    // e = 1 - x y^2 = 1 - T2 2^(-121 - odd), T2 = top 128 bits of X_n R^2, X_n = X 2^(lz - 1)
+    const int sx = (int)lz - 1;
+    const fx xn{{x.w[0] << sx, __funnelshift_l(x.w[0], x.w[1], sx), __funnelshift_l(x.w[1], x.w[2], sx),
+                 __funnelshift_l(x.w[2], x.w[3], sx)}};
+    const fx t2 = fx_mul_r64(fx_mul_r64(xn, R), R);
+    const int se = 9 + odd;  // e in units of 2^-112: its low 64 bits suffice (|e| < 2^-50)
+    const unsigned long long tl = ((unsigned long long)__funnelshift_r(t2.w[1], t2.w[2], se) << 32) |
+                                  __funnelshift_r(t2.w[0], t2.w[1], se);
+    const long long E = -(long long)tl;
+    // y e / 2 in units of 2^-112: R E 2^(-62 - h)
+    const unsigned long long plo = R * (unsigned long long)E;
+    const long long phi = __mul64hi((long long)R, E);
+    int sd = 62 + h;
+    sd = sd < 55 ? 55 : (sd > 70 ? 70 : sd);
+    const long long dlt = sd < 64 ? (long long)(((unsigned long long)phi << (64 - sd)) | (plo >> sd))
+                                  : (phi >> (sd - 64));
+    const uint32_t ext = (uint32_t)(dlt >> 63);
+    return y + fx{{(uint32_t)dlt, (uint32_t)((unsigned long long)dlt >> 32), ext, ext}};
 }
 // det of the SPD 2x2 block [[p00, p01], [p01, p11]]
 __device__ __forceinline__ fx fx_det2(const fx &p00, const fx &p01, const fx &p11) {
@@ -243,17 +312,23 @@ __device__ __forceinline__ fx fx_det2(const fx &p00, const fx &p01, const fx &p1
 // are stored offset, u' = u + 2 > 0, and each entry needs two unsigned products:
 //   c_ij - u_i . u_j = c_ij - (u'_i0 u'_j0 + u'_i1 u'_j1) + t_i + t_j,  t = 2 (u'0 + u'1) - 4.
 struct fx_piv {
-    fx a, r10, b, rs, x;  // x = det / p00
+    fx a, r10, b, rs, det;
 };
-__device__ __forceinline__ fx_piv fx_pivot(const fx &p00, const fx &p01, const fx &p11) {
+// the Cholesky quantities from a = p00^{-1/2} and rs = det^{-1/2} (independent, so the
+// two rsqrts need not wait for each other): b = x^{-1/2} = rs sqrt(p00) = rs p00 a
+__device__ __forceinline__ fx_piv fx_pivot_from(const fx &p00, const fx &p01, const fx &det, const fx &a,
+                                               const fx &rs) {
     fx_piv v;
-    v.a = fx_rsqrt(p00);
-    v.r10 = fx_mul_su(p01, v.a);
-    const fx r = fx_abs(v.r10);
-    v.x = p11 - fx_mul_uu(r, r);
-    v.b = fx_rsqrt(v.x);
-    v.rs = fx_mul_uu(v.a, v.b);
+    v.a = a;
+    v.rs = rs;
+    v.det = det;
+    v.r10 = fx_mul_su(p01, a);
+    v.b = fx_mul_uu(rs, fx_mul_uu(p00, a));
     return v;
+}
+__device__ __forceinline__ fx_piv fx_pivot(const fx &p00, const fx &p01, const fx &p11) {
+    const fx det = fx_det2(p00, p01, p11);
+    return fx_pivot_from(p00, p01, det, fx_rsqrt(p00), fx_rsqrt(det));
 }
 // offset row (u'0, u'1, t) of U from the pivot-row entries b0 = P(0, .), b1 = P(1, .)
 __device__ __forceinline__ void fx_urow(const fx_piv &v, const fx &b0, const fx &b1, fx &u0, fx &u1, fx &t) {

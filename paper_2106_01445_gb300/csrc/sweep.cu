@@ -71,8 +71,8 @@ template <> struct Prec<dd> {
     static constexpr int wrow = 2;
     static constexpr double u = 1.2325951644078309e-32, u_sum = 1.2325951644078309e-32;
 };
-// Q16.112 fixed point: truncated products (2^-112) and the pivot rsqrt's Newton step
-// (~2^-104 relative) give each factor a relative error far below 2^-100 while its
+// Q16.112 fixed point: truncated products (2^-112) and the pivot rsqrt (residual
+// 1 - x y^2 within 2^-108) give each factor a relative error far below 2^-100 while its
 // pivot determinant stays >= 2^-8; prefactors and sums in double-double.
 template <> struct Prec<fx> {
     static constexpr int B = 2, idx = GBS_FX;
@@ -90,11 +90,12 @@ template <> __device__ __forceinline__ double rsq<double>(double x) { return rsq
 template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
 template <> __device__ __forceinline__ fx rsq<fx>(fx x) { return fx_rsqrt(x); }
 
-// 1/sqrt(det) as a prefix factor, in the Tau type of the precision
-__device__ __forceinline__ double rsq_tau(float x) { return rsqrt((double)x); }
-__device__ __forceinline__ double rsq_tau(double x) { return rsqrt(x); }
-__device__ __forceinline__ dd rsq_tau(dd x) { return dd_rsqrt(x); }
-__device__ __forceinline__ dd rsq_tau(fx x) { return fx_to_dd(fx_rsqrt(x)); }
+// 1/sqrt(det) as a prefix factor, in the Tau type of the precision, given rs = rsq(det)
+// (FP32 prefactors are taken in FP64)
+__device__ __forceinline__ double tau_of(float det, float) { return rsqrt((double)det); }
+__device__ __forceinline__ double tau_of(double, double rs) { return rs; }
+__device__ __forceinline__ dd tau_of(dd, dd rs) { return rs; }
+__device__ __forceinline__ dd tau_of(fx, fx rs) { return fx_to_dd(rs); }
 
 // constants and conversions of the working type
 template <typename T> __device__ __forceinline__ T konst(double v) { return T(v); }
@@ -296,7 +297,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
         // symmetric form C - U U^T, U = B R^{-T} (offset rows)
         constexpr int d = 2 * (m - 1);
         const fx_piv v = fx_pivot(p00, p01, p11);
-        acc.bad |= fx_chol_bad(p00, v.x, v.rs);
+        acc.bad |= fx_chol_bad(p00, v.det);
         fx u0[d], u1[d], tt[d];
 #pragma unroll
         for (int i = 0; i < d; ++i) fx_urow(v, A(o, o + 2 + i), A(o + 1, o + 2 + i), u0[i], u1[i], tt[i]);
@@ -442,8 +443,8 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
         if (bad) atomicOr(flag, bad);
     }
     const int Dt = D - c0 - 2;
+    const T rs = rsq<T>(det);
     if (t < Dt) {
-        const T rs = rsq<T>(det);
         const T inv = rs * rs;
         const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
         for (int i = t; i < Dt; i += kThreads) {
@@ -452,7 +453,7 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
             Wb[2 * i + 1] = dot2(q01, b0, q11, b1);
         }
     }
-    const typename Prec<T>::Tau rt = rsq_tau(det);
+    const typename Prec<T>::Tau rt = tau_of(det, rs);
     __syncthreads();
     // the trailing triangle, rows p and Dt - 1 - p folded into one run of Dt + 1 entries
     const int w = Dt + 1, E = (Dt >> 1) * w;
@@ -659,27 +660,37 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
                 const int np = 1 << l;
                 // (a) the parents' pivot quantities and the children's prefactors
-                if (t < np) {
+                if constexpr (Prec<T>::fixed) {
+                    // two lanes per parent: the even lane's p00^{-1/2} and the odd lane's
+                    // det^{-1/2} run side by side (whole warps, for the shuffle)
+                    if (t < ((2 * np + 31) & ~31)) {
+                        const int cp = min(t >> 1, np - 1), odd = t & 1;
+                        const T *P = src + cp * sstr;
+                        const fx p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
+                        const fx det = fx_det2(p00, p01, p11);
+                        const fx y = fx_rsqrt(odd ? det : p00);
+                        const fx yo = fx_shfl_xor(y, 1);
+                        if (!odd && t < 2 * np) {
+                            const fx_piv v = fx_pivot_from(p00, p01, det, y, yo);
+                            Qb[3 * cp] = v.a;
+                            Qb[3 * cp + 1] = v.r10;
+                            Qb[3 * cp + 2] = v.b;
+                            tdst[2 * cp] = tsrc[cp];
+                            tdst[2 * cp + 1] = node_times(tsrc[cp], v.rs);
+                            const int bad = fx_chol_bad(p00, det);
+                            if (bad) atomicOr(&s_flag, bad);
+                        }
+                    }
+                } else if (t < np) {
                     const T *P = src + t * sstr;
                     const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
-                    T rs;
-                    int bad;
-                    if constexpr (Prec<T>::fixed) {
-                        const fx_piv v = fx_pivot(p00, p01, p11);
-                        Qb[3 * t] = v.a;
-                        Qb[3 * t + 1] = v.r10;
-                        Qb[3 * t + 2] = v.b;
-                        rs = v.rs;
-                        bad = fx_chol_bad(p00, v.x, v.rs);
-                    } else {
-                        const T det = det2(p00, p01, p11);
-                        rs = rsq<T>(det);
-                        const T inv = rs * rs;
-                        Qb[3 * t] = p11 * inv;
-                        Qb[3 * t + 1] = -p01 * inv;
-                        Qb[3 * t + 2] = p00 * inv;
-                        bad = pivot_bad(det);
-                    }
+                    const T det = det2(p00, p01, p11);
+                    const T rs = rsq<T>(det);
+                    const T inv = rs * rs;
+                    Qb[3 * t] = p11 * inv;
+                    Qb[3 * t + 1] = -p01 * inv;
+                    Qb[3 * t + 2] = p00 * inv;
+                    const int bad = pivot_bad(det);
                     tdst[2 * t] = tsrc[t];
                     tdst[2 * t + 1] = node_times(tsrc[t], rs);
                     if (bad) atomicOr(&s_flag, bad);
