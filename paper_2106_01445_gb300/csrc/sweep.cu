@@ -621,19 +621,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 if (j < i) continue;
                 int ai = i >> 1, bj = j >> 1;
                 // position of the ai-th row mode inside Ublk
-                int ui, uj;
-                {
-                    int c = 0, m = 0;
-                    ui = -1;
-                    for (; m < ss; ++m)
-                        if (sub >> m & 1) { if (c == ai) { ui = m; break; } ++c; }
-                    if (ui < 0) ui = ss + (ai - kk);
-                    c = 0;
-                    uj = -1;
-                    for (m = 0; m < ss; ++m)
-                        if (sub >> m & 1) { if (c == bj) { uj = m; break; } ++c; }
-                    if (uj < 0) uj = ss + (bj - kk);
-                }
+                const int ui = ai < kk ? (int)__fns((unsigned)sub, 0u, ai + 1) : ss + (ai - kk);
+                const int uj = bj < kk ? (int)__fns((unsigned)sub, 0u, bj + 1) : ss + (bj - kk);
                 Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
             }
             __syncthreads();
