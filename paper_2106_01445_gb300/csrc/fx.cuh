@@ -308,11 +308,12 @@ __device__ __forceinline__ fx fx_det2(const fx &p00, const fx &p01, const fx &p1
 // Symmetric form of the 2x2 block elimination used by the fixed-point sweep.  With
 // the pivot block P = R R^T (R lower triangular, 1/r00 = a, r10, 1/r11 = b), the
 // Schur update C - B P^{-1} B^T equals C - U U^T, U = B R^{-T}: row i of U is
-// u0 = b_i0 a, u1 = (b_i1 - r10 u0) b.  |u_ik| <= sqrt(c_ii) <= sqrt(2), so the rows
+// u0 = b_i0 a, u1 = (b_i1 - r10 u0) b = b_i1 b - u0 c with c = r10 b = p01 det^{-1/2}
+// (two products side by side).  |u_ik| <= sqrt(c_ii) <= sqrt(2), so the rows
 // are stored offset, u' = u + 2 > 0, and each entry needs two unsigned products:
 //   c_ij - u_i . u_j = c_ij - (u'_i0 u'_j0 + u'_i1 u'_j1) + t_i + t_j,  t = 2 (u'0 + u'1) - 4.
 struct fx_piv {
-    fx a, r10, b, rs, det;
+    fx a, c, b, rs, det;
 };
 // the Cholesky quantities from a = p00^{-1/2} and rs = det^{-1/2} (independent, so the
 // two rsqrts need not wait for each other): b = x^{-1/2} = rs sqrt(p00) = rs p00 a
@@ -322,7 +323,7 @@ __device__ __forceinline__ fx_piv fx_pivot_from(const fx &p00, const fx &p01, co
     v.a = a;
     v.rs = rs;
     v.det = det;
-    v.r10 = fx_mul_su(p01, a);
+    v.c = fx_mul_su(p01, rs);
     v.b = fx_mul_uu(rs, fx_mul_uu(p00, a));
     return v;
 }
@@ -333,7 +334,7 @@ __device__ __forceinline__ fx_piv fx_pivot(const fx &p00, const fx &p01, const f
 // offset row (u'0, u'1, t) of U from the pivot-row entries b0 = P(0, .), b1 = P(1, .)
 __device__ __forceinline__ void fx_urow(const fx_piv &v, const fx &b0, const fx &b1, fx &u0, fx &u1, fx &t) {
     const fx x0 = fx_mul_su(b0, v.a);
-    const fx x1 = fx_mul_su(b1 - x0 * v.r10, v.b);
+    const fx x1 = fx_mul_su(b1, v.b) - x0 * v.c;
     u0 = fx_add_top(x0, 2 << 16);
     u1 = fx_add_top(x1, 2 << 16);
     const fx s = u0 + u1;

@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                         if (!odd && t < 2 * np) {
                             const fx_piv v = fx_pivot_from(p00, p01, det, y, yo);
                             Qb[3 * cp] = v.a;
-                            Qb[3 * cp + 1] = v.r10;
+                            Qb[3 * cp + 1] = v.c;
                             Qb[3 * cp + 2] = v.b;
                             tdst[2 * cp] = tsrc[cp];
                             tdst[2 * cp + 1] = node_times(tsrc[cp], v.rs);
