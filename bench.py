@@ -36,7 +36,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None, "fx": None}
+DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None, "fx": 160256.0}
 UNIT = "subset logdets/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
