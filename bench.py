@@ -36,7 +36,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": None, "dd": None, "fp64": None, "fx": 160256.0}
+DRAM_TRAFFIC = {"fp32": None, "dd": 222976.0, "fp64": None, "fx": 160256.0}
 UNIT = "subset logdets/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
@@ -553,6 +553,31 @@ def run_workloads(dev, stream, meas, fp32_peak):
         a = host(ctx.prob(st["O"], st["logdet"], allp, order=order, precision="ff"))
         entry["all_click"]["order%d_rel_dev" % order] = float(np.expm1(a["logP"][0] - ex["logP"][0]))
     res["m30_device"] = entry
+
+    # ---- the fourth-order accuracy study (the paper's Fig. 4): relative deviation of the
+    # order-4 estimate (float-float minors) from the exact sum over 100 random outcomes per
+    # point; the exact sum in fixed point, with double-double for patterns outside its range
+    def study_point(c):
+        U, r, pats = c.unitary(), c.squeezing(), c.patterns()
+        st = ctx.build_state(U, r, c.eta)
+        ex = host(ctx.prob(st["O"], st["logdet"], pats, precision="fx"))
+        redo = np.nonzero(ex["status"] != 0)[0]
+        if redo.size:
+            ex2 = host(ctx.prob(st["O"], st["logdet"], pats[redo], precision="dd"))
+            for kk in ex:
+                ex[kk][redo] = ex2[kk]
+        ap = host(ctx.prob(st["O"], st["logdet"], pats, order=4, precision="ff"))
+        ok = (ex["status"] == 0) & (ap["status"] == 0)
+        dev_ = np.abs(np.expm1(ap["logP"][ok] - ex["logP"][ok]))
+        return {"M": c.M, "n": c.n_lo, "r": c.r_lo, "outcomes": int(len(pats)), "ok": int(ok.sum()),
+                "mean_rel_dev": float(dev_.mean()), "std_rel_dev": float(dev_.std()),
+                "median_rel_dev": float(np.median(dev_)), "max_rel_dev": float(dev_.max()),
+                "fit_fallbacks": int((ap["status"] == 7).sum())}
+    grid = g.accuracy_study()
+    t0 = time.time()
+    res["accuracy_study_order4"] = {"vs_m_r1.6": [study_point(c) for c in grid["vs_m"]],
+                                    "vs_r_m30_n20": [study_point(c) for c in grid["vs_r"]]}
+    res["accuracy_study_order4"]["wall_s"] = time.time() - t0
     ctx.close()
     return res
 

@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "philox4x32_10", "philox_words", "uniform01", "normals", "haar_unitary",
     "clements_unitary", "clements_phases", "squeezing", "gen_patterns",
-    "all_patterns", "pattern_modes", "modes_to_pattern", "Config", "CONFIGS",
+    "all_patterns", "pattern_modes", "modes_to_pattern", "Config", "CONFIGS", "accuracy_study",
     "STREAM_U", "STREAM_R", "STREAM_PATTERNS", "STREAM_ANCHORS",
 ]
 
@@ -263,3 +263,30 @@ CONFIGS = {
     "m30_device": Config("m30_device", M=30, K=15, r_lo=1.4, r_hi=1.4, eta=1.0, interferometer="haar",
                          seed=6, note="whole-device p(n); the all-click point by orders 2-4"),
 }
+
+
+def accuracy_study():
+    """The grid of the fourth-order accuracy study (the paper's Fig. 4): lossless devices with
+    half of the inputs squeezed, Haar U, 100 uniformly random n-click outcomes per point.
+
+    * ``vs_m``: r = 1.6, n in {6, 10, 14, 18, 22} clicks on M = round(n / f) modes for the
+      clicked fractions f = 1/3, 1/2, 0.7 (n = 18 gives the paper's 54, 36 and 26 modes);
+    * ``vs_r``: 20 clicks on 30 modes (15 inputs squeezed), r = 0.4 .. 2.0.
+
+    Returns ``{"vs_m": [Config, ...], "vs_r": [Config, ...]}``; seeds 100 + point index.
+    """
+    vs_m, vs_r = [], []
+    k = 0
+    for frac, tag in ((1.0 / 3.0, "f33"), (0.5, "f50"), (0.7, "f70")):
+        for n in (6, 10, 14, 18, 22):
+            M = int(round(n / frac))
+            vs_m.append(Config("acc_%s_n%d" % (tag, n), M=M, K=M // 2, r_lo=1.6, r_hi=1.6, eta=1.0,
+                               interferometer="haar", seed=100 + k, n_lo=n, n_hi=n, n_pat=100,
+                               orders=(4,), note="clicked fraction %.2f" % frac))
+            k += 1
+    for i in range(9):
+        rr = round(0.4 + 0.2 * i, 1)
+        vs_r.append(Config("acc_r%.1f" % rr, M=30, K=15, r_lo=rr, r_hi=rr, eta=1.0, interferometer="haar",
+                           seed=100 + k, n_lo=20, n_hi=20, n_pat=100, orders=(4,)))
+        k += 1
+    return {"vs_m": vs_m, "vs_r": vs_r}
