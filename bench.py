@@ -552,6 +552,17 @@ def run_workloads(dev, stream, meas, fp32_peak):
     for order in (2, 3, 4):
         a = host(ctx.prob(st["O"], st["logdet"], allp, order=order, precision="ff"))
         entry["all_click"]["order%d_rel_dev" % order] = float(np.expm1(a["logP"][0] - ex["logP"][0]))
+    # the photon-number sectors p_k(n) of the same device (lossless: even sectors only),
+    # 256 circle points (65 complex sweeps of 2^30 subsets)
+    ms, kms, pkn = timed(lambda: ctx.sector_distribution(st["O"], st["logdet"], L=256, rho=1.0, K=255,
+                                                         even_only=True))
+    pkn = pkn.cpu().numpy()
+    entry["sectors"] = {"L": 256, "sweeps": 65, "ms": ms, "sweep_kernel_ms": kms,
+                        "subsets_per_s": 65 * 2.0 ** c.M / (kms * 1e-3),
+                        "max_abs_sum_k_minus_p_n": float(np.abs(pkn.sum(axis=0) - pn).max()),
+                        "max_abs_odd_sector": float(np.abs(pkn[1::2]).max()),
+                        "p_k_n": {str(k): [float(x) for x in pkn[k]] for k in (20, 50, 80, 110, 140, 170)},
+                        "peak_n": {str(k): int(np.argmax(pkn[k])) for k in (20, 50, 80, 110, 140, 170)}}
     res["m30_device"] = entry
 
     # ---- the fourth-order accuracy study (the paper's Fig. 4): relative deviation of the

@@ -149,6 +149,28 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
 int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, double *logp,
                            double *kappa);
 
+/* Photon-number sectors of the whole device's click-number distribution (Results,
+ * "Calculation of sectors p_k(n)", and Methods, "Partition function": p(n) = sum_k p_k(n),
+ * p_k(n) the probability of n clicks with k photons in the device).  With the sector
+ * generating function of a set Z of modes, det(I - t O_Z)^{-1/2} (t marks each photon),
+ *   G_n(t) = sum_k p_k(n) t^k = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n-z} C(M-z, n-z) E_z(t),
+ *   E_z(t) = sum over the subsets Z with |Z| = z of det(I - t O_Z)^{-1/2},
+ * evaluated at t_j = rho e^{2 pi i j / L}, j = 0..L/2, by a complex FP64 sweep over all
+ * 2^M subsets binned by size (principal branch: I - t O_Z is accretive for |t| <= 1), then
+ * p_k(n) = rho^-k / L sum_{j < L} G_n(t_j) e^{-2 pi i j k / L} (G_n(t_{L-j}) = conj G_n(t_j)).
+ * 4 <= M <= 40; L a power of two in 4..4096 (sectors k >= L alias onto k mod L: choose L
+ * beyond the photon numbers that matter); 0 < rho <= 1; 0 <= K < L.  even_only != 0 declares
+ * that every odd sector vanishes (a lossless state: photons come in pairs, G_n(-t) = G_n(t)),
+ * which halves the sweeps; the odd rows of pkn are then zero to rounding.  pkn: (K + 1) x
+ * (M + 1) doubles (device), row k = p_k(0..M).  Cost: L/2 + 1 sweeps of 2^M subsets (L/4 + 1
+ * with even_only).  Accuracy:
+ * the subset terms are FP64, so each G_n(t_j) carries an absolute error of about 1e-16
+ * times the transform's cancellation (kappa of gbs_click_distribution) times p(n)
+ * (|G_n(t)| <= p(n) for |t| <= 1), and p_k(n) that error times rho^-k.  NaN everywhere if
+ * a pivot was zero.  Errors: GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
+int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
+                            int K, int even_only, double *pkn);
+
 /* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
  * has no counterpart: this serves callers that cannot call cudaMalloc (code
  * running under another owner's stream capture, processes whose device memory

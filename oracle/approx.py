@@ -272,3 +272,16 @@ def exact_sector_last_points(O: np.ndarray, M: int, modes, K: int) -> np.ndarray
         sgn = -1.0 if (n - len(Z)) & 1 else 1.0
         out += sgn * series_coeffs(O[np.ix_(rows, rows)], K)
     return out
+
+
+def sector_distribution(O: np.ndarray, logdet_sigmaQ: float, M: int, K: int) -> np.ndarray:
+    """Whole-device sectors p_k(n), k = 0..K, n = 0..M (Results, "Calculation of sectors"):
+    the probability of n clicks with k photons, summed over every pattern S with n clicks
+    of P(S, k) = det(sigma_Q)^{-1/2} q_k(S), q_k(S) the inclusion-exclusion of the sector
+    coefficients over the subsets of S (exact_sector_last_points).  All 2^M patterns:
+    small M only."""
+    out = np.zeros((K + 1, M + 1))
+    for mask in range(1 << M):
+        modes = [i for i in range(M) if mask >> i & 1]
+        out[:, len(modes)] += exact_sector_last_points(O, M, modes, K)
+    return out * math.exp(-0.5 * logdet_sigmaQ)

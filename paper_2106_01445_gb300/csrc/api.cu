@@ -165,6 +165,14 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
     return click_distribution(ctx, M, O, logdet_sigmaQ, logp, kappa);
 }
 
+int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
+                            int K, int even_only, double *pkn) {
+    if (!ctx) return GBS_E_INVALID;
+    if (!O || !logdet_sigmaQ || !pkn) return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: null pointer");
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return sector_distribution(ctx, M, O, logdet_sigmaQ, L, rho, K, even_only, pkn);
+}
+
 int gbs_autotune(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
                  const uint64_t *patterns, int n_pat, int precision, int *best_split, double *best_ms) {
     if (!ctx) return GBS_E_INVALID;

@@ -72,6 +72,8 @@ long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split
 int sweep_split_of(const gbs_ctx *ctx, int precision);
 int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
                        double *kappa);
+int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
+                        int even, double *pkn);
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);

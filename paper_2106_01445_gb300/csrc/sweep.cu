@@ -26,6 +26,7 @@
 #include "dd.cuh"
 #include "fx.cuh"
 #include "gbs_internal.cuh"
+#include "zc.cuh"
 
 namespace {
 
@@ -84,7 +85,21 @@ template <> struct Prec<fx> {
     static constexpr double u = 7.888609052210118e-31, u_sum = 1.2325951644078309e-32;
 };
 
+// Complex FP64 (the sector-resolved binned sweep at a complex generating variable t):
+// the matrices I - t O_Z are accretive for |t| <= 1, so the unpivoted recursion is safe and
+// the product of the principal det^{-1/2} of the pivot blocks is the principal branch of
+// the whole (it is continuous in t and real positive at t = 0).
+template <> struct Prec<zc> {
+    static constexpr int B = 3;
+    using Tau = zc;
+    using Abs = double;
+    using Node = zc;
+    static constexpr bool fixed = false;
+    static constexpr int wrow = 2;
+};
+
 template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ zc rsq<zc>(zc x) { return zc_rsqrt(x); }
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
@@ -96,6 +111,7 @@ __device__ __forceinline__ double tau_of(float det, float) { return rsqrt((doubl
 __device__ __forceinline__ double tau_of(double, double rs) { return rs; }
 __device__ __forceinline__ dd tau_of(dd, dd rs) { return rs; }
 __device__ __forceinline__ dd tau_of(fx, fx rs) { return fx_to_dd(rs); }
+__device__ __forceinline__ zc tau_of(zc, zc rs) { return rs; }
 
 // constants and conversions of the working type
 template <typename T> __device__ __forceinline__ T konst(double v) { return T(v); }
@@ -103,6 +119,7 @@ template <> __device__ __forceinline__ fx konst<fx>(double v) { return fx_from_d
 __device__ __forceinline__ float to_node(float x) { return x; }
 __device__ __forceinline__ double to_node(double x) { return x; }
 __device__ __forceinline__ dd to_node(dd x) { return x; }
+__device__ __forceinline__ zc to_node(zc x) { return x; }
 // a child's prefactor: the parent's times det^{-1/2} of the parent's pivot
 template <typename N, typename T> __device__ __forceinline__ N node_times(const N &p, const T &rs) { return p * to_node(rs); }
 template <> __device__ __forceinline__ fxe node_times<fxe, fx>(const fxe &p, const fx &rs) { return fxe_mul(p, rs); }
@@ -114,6 +131,10 @@ template <> __device__ __forceinline__ fx mul_pos<fx>(fx a, fx b) { return fx_mu
 // pivot check: 0 fine, 1 not positive (or NaN), 2 outside the fixed-point range
 template <typename T> __device__ __forceinline__ int pivot_bad(T det) { return det > T(0) ? 0 : 1; }
 template <> __device__ __forceinline__ int pivot_bad<fx>(fx det) { return fx_pivot_bad(det); }
+// complex pivots: their determinants may have any argument in (-pi, pi); only zero or NaN is bad
+template <> __device__ __forceinline__ int pivot_bad<zc>(zc det) {
+    return fabs(det.re) + fabs(det.im) > 0.0 ? 0 : 1;
+}
 
 // the Schur-update kernels: a0 b0 + a1 b1, c - a0 b0 - a1 b1, det of a 2x2 block
 template <typename T> __device__ __forceinline__ T dot2(T a0, T b0, T a1, T b1) { return a0 * b0 + a1 * b1; }
@@ -130,6 +151,14 @@ template <> __device__ __forceinline__ fx a_entry<fx>(double delta, double o) {
     return fx_from_double(delta) - fx_from_double(o);
 }
 
+// the same with the generating variable t of the complex binned sweep: I - t O
+template <typename T> __device__ __forceinline__ T a_entry_t(double delta, double o, double, double) {
+    return a_entry<T>(delta, o);
+}
+template <> __device__ __forceinline__ zc a_entry_t<zc>(double delta, double o, double t_re, double t_im) {
+    return zc(delta - t_re * o, -t_im * o);
+}
+
 __device__ __forceinline__ double to_hi(float x) { return x; }
 __device__ __forceinline__ double to_hi(double x) { return x; }
 // leading part of a (positive) term, in the type its magnitude is summed in
@@ -140,6 +169,7 @@ __device__ __forceinline__ float abs_part(fx x) { return (float)(int32_t)x.w[3] 
 __device__ __forceinline__ bool is_nan(float x) { return x != x; }
 __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
+__device__ __forceinline__ bool is_nan(zc x) { return zc_nan(x); }
 // a thread's subtree sum as (hi, lo) doubles
 __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
@@ -358,6 +388,7 @@ struct Plan {
     int *pflags;        // per sorted position: status bits
     double *partials;   // 3 per unit
     int split;          // prefix levels looped inside a unit (0..kS)
+    double t_re, t_im;  // complex binned sweep: the generating variable t of A = I - t O
 };
 
 template <typename T>
@@ -474,6 +505,13 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
     return rt;
 }
 
+// the size bins of the binned mode: double-double sums of real terms, complex sums of
+// complex ones
+template <typename T> struct BinOf { using type = dd; };
+template <> struct BinOf<zc> { using type = zc; };
+__device__ __forceinline__ void store2(double *o, dd v) { o[0] = v.hi; o[1] = v.lo; }
+__device__ __forceinline__ void store2(double *o, zc v) { o[0] = v.re; o[1] = v.im; }
+
 // ---- the sweep ------------------------------------------------------------------
 // BIN: the click-number distribution mode (one pattern = all M modes): the subset
 // terms are summed unsigned into bins by subset size instead of into the signed sum
@@ -497,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     __shared__ long long s_unit;
     __shared__ int s_n, s_k, s_flag;
     __shared__ int s_base[kThreads];        // binned mode: modes included above each bottom node
-    __shared__ dd s_ubin[kMaxN + 1];        // binned mode: the unit's size bins
+    __shared__ typename BinOf<T>::type s_ubin[kMaxN + 1];  // binned mode: the unit's size bins
     __shared__ fx s_vred[kThreads / 32];    // fixed point: per-warp aligned sums
     __shared__ float s_ared[kThreads / 32];
     __shared__ int s_ered[kThreads / 32];
@@ -580,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const int si = modes[a] + (i & 1) * M, sj = modes[b] + (j & 1) * M;
                 const double o = O[(size_t)si * N2 + sj];
                 if (Prec<T>::fixed && !(fabs(o) <= 4.0)) atomicOr(&s_flag, 2);
-                v = a_entry<T>(i == j ? 1.0 : 0.0, o);
+                v = a_entry_t<T>(i == j ? 1.0 : 0.0, o, pl.t_re, pl.t_im);
             }
             X[pidx(D0, i, j)] = v;
         }
@@ -609,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         __syncthreads();
         double u_hi = 0.0, u_lo = 0.0, u_abs = 0.0;
         if constexpr (BIN) {
-            for (int z = t; z <= n; z += kThreads) s_ubin[z] = dd(0.0);
+            for (int z = t; z <= n; z += kThreads) s_ubin[z] = typename BinOf<T>::type(0.0);
         }
         for (int sub = 0; sub < (1 << ss); ++sub) {
             // sub-unit: include the set bits of `sub` among the next ss modes
@@ -837,14 +875,11 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             // the unit's bins times its prefix factor (thread z owns bin z)
             double *out = pl.partials + (size_t)2 * (n + 1) * u;
             for (int z = t; z <= n; z += kThreads) {
-                const dd v = tpre * s_ubin[z];
-                out[2 * z] = v.hi;
-                out[2 * z + 1] = v.lo;
+                store2(out + 2 * z, tpre * s_ubin[z]);
             }
             if (t == 0 && (s_flag || is_nan(tpre))) atomicOr(pl.pflags + sp, 1);
             __syncthreads();
-            continue;
-        }
+        } else {
         double c_hi = u_hi, c_lo = u_lo, c_abs = u_abs;
         // deterministic CTA reduction (TwoSum tree)
         for (int off = 16; off; off >>= 1) {
@@ -883,6 +918,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             if (fl) atomicOr(pl.pflags + sp, fl);
         }
         __syncthreads();
+        }
     }
 }
 
@@ -981,6 +1017,9 @@ Plan plan_from(void *ws, int n_pat) {
     pl.unit_off = (long long *)(b + o.unit_off);
     pl.pflags = (int *)(b + o.pflags);
     pl.partials = (double *)(b + o.partials);
+    pl.split = kS;
+    pl.t_re = 0.0;
+    pl.t_im = 0.0;
     return pl;
 }
 
@@ -1136,6 +1175,98 @@ __global__ void bins_final_kernel(int M, long long nchunks, const double *__rest
     }
 }
 
+// ---- sector-resolved distribution: complex bins at one t, then the DFT over t ---------
+// per chunk of 1024 units: every size bin's complex sum in unit order (double-double parts)
+__global__ void zbins_chunk_kernel(int nb, const double *__restrict__ partials, const long long *__restrict__ units_p,
+                                   double *__restrict__ chunks) {
+    const long long c = blockIdx.x, units = *units_p;
+    const long long u0 = c * 1024, u1 = (c + 1) * 1024 < units ? (c + 1) * 1024 : units;
+    for (int z = threadIdx.x; z < nb; z += blockDim.x) {
+        dd re = dd(0.0), im = dd(0.0);
+        for (long long u = u0; u < u1; ++u) {
+            re += dd(partials[(size_t)2 * nb * u + 2 * z]);
+            im += dd(partials[(size_t)2 * nb * u + 2 * z + 1]);
+        }
+        double *o = chunks + (size_t)4 * nb * c + 4 * z;
+        o[0] = re.hi;
+        o[1] = re.lo;
+        o[2] = im.hi;
+        o[3] = im.lo;
+    }
+}
+
+// G_n(t) = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n - z} C(M - z, n - z) E_z(t) for one t,
+// E_z(t) = sum_{|Z| = z} det(I - t O_Z)^{-1/2}: the generating function of the sectors of
+// the n-click probability, sum_k p_k(n) t^k.  Real and imaginary parts in double-double.
+__global__ void zbins_final_kernel(int M, long long nchunks, const double *__restrict__ chunks,
+                                   const double *__restrict__ logdet, const int *__restrict__ pflags,
+                                   const int *__restrict__ overflow, double *__restrict__ G, int *__restrict__ bad) {
+    __shared__ dd Er[kMaxN + 1], Ei[kMaxN + 1];
+    __shared__ double Cb[kMaxN + 1][kMaxN + 1];
+    const int t = threadIdx.x, nb = M + 1;
+    for (int z = t; z < nb; z += blockDim.x) {
+        dd re = dd(0.0), im = dd(0.0);
+        for (long long c = 0; c < nchunks; ++c) {
+            const double *o = chunks + (size_t)4 * nb * c + 4 * z;
+            re += dd(o[0], o[1]);
+            im += dd(o[2], o[3]);
+        }
+        Er[z] = re;
+        Ei[z] = im;
+    }
+    for (int a = t; a <= M; a += blockDim.x) {
+        Cb[a][0] = 1.0;
+        for (int b = 1; b <= a; ++b) Cb[a][b] = Cb[a][b - 1] * (double)(a - b + 1) / (double)b;  // exact below 2^53
+    }
+    __syncthreads();
+    const double sc = exp(-0.5 * (*logdet));
+    for (int n = t; n <= M; n += blockDim.x) {
+        dd Sr = dd(0.0), Si = dd(0.0);
+        for (int z = 0; z <= n; ++z) {
+            const dd c = dd(Cb[M - z][n - z]);
+            if ((n - z) & 1) {
+                Sr -= c * Er[z];
+                Si -= c * Ei[z];
+            } else {
+                Sr += c * Er[z];
+                Si += c * Ei[z];
+            }
+        }
+        G[2 * n] = sc * Sr.hi;
+        G[2 * n + 1] = sc * Si.hi;
+    }
+    if (t == 0 && (*overflow || pflags[0])) *bad = 1;
+}
+
+// even sectors only: G_j = conj G_{L/2 - j} for the points j = jmax + 1..h not swept
+__global__ void mirror_kernel(int nb, int h, int jmax, double *__restrict__ G) {
+    const int j = jmax + 1 + blockIdx.x;
+    for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+        G[2 * nb * j + 2 * n] = G[2 * nb * (h - j) + 2 * n];
+        G[2 * nb * j + 2 * n + 1] = -G[2 * nb * (h - j) + 2 * n + 1];
+    }
+}
+
+// p_k(n) = rho^-k / L sum_{j < L} G_n(t_j) e^{-2 pi i j k / L}, t_j = rho e^{2 pi i j / L}, from
+// j = 0..L/2 (the coefficients are real: G_n(t_{L-j}) is the conjugate of G_n(t_j));
+// one thread per (k, n), row k of pkn holds p_k(0..M)
+__global__ void sector_dft_kernel(int M, int L, double rho, int K, const double *__restrict__ G,
+                                  const int *__restrict__ bad, double *__restrict__ pkn) {
+    const int nb = M + 1;
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= (long long)(K + 1) * nb) return;
+    const int k = (int)(f / nb), n = (int)(f - (long long)k * nb);
+    const int h = L / 2;
+    double s = G[2 * n] + ((k & 1) ? -G[2 * nb * h + 2 * n] : G[2 * nb * h + 2 * n]);
+    for (int j = 1; j < h; ++j) {
+        double sn, cs;
+        sincospi(2.0 * (double)(((long long)j * k) % L) / (double)L, &sn, &cs);
+        const double gr = G[2 * nb * j + 2 * n], gi = G[2 * nb * j + 2 * n + 1];
+        s += 2.0 * (gr * cs + gi * sn);  // 2 Re(G e^{-i theta})
+    }
+    pkn[f] = *bad ? nan("") : s / (double)L * pow(rho, -(double)k);
+}
+
 }  // namespace
 
 int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
@@ -1217,6 +1348,71 @@ int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logde
     if (st) return st;
     bins_chunk_kernel<<<(unsigned)nch, 64, 0, ctx->stream>>>(nb, pl.partials, pl.unit_off + 1, chunks);
     bins_final_kernel<<<1, 64, 0, ctx->stream>>>(M, nch, chunks, logdet, pl.pflags, pl.overflow, logp, kappa);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
+
+int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
+                        int even, double *pkn) {
+    using T = zc;
+    using Lay = Layout<T>;
+    if (M < 4 || M > kMaxN)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: M = %d outside 4..%d", M, kMaxN);
+    if (L < 4 || L > 4096 || (L & (L - 1)))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: L = %d is not a power of two in 4..4096", L);
+    if (!(rho > 0.0 && rho <= 1.0))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: rho = %g outside (0, 1]", rho);
+    if (K < 0 || K >= L)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: K = %d outside 0..L-1", K);
+    int n_eff, L_eff, q, ss;
+    unit_shape<T>(M, n_eff, L_eff, q, ss, kS);
+    const long long units = 1ll << (q - ss);
+    const int nb = M + 1, h = L / 2;
+    const long long nch = (units + 1023) / 1024;
+    const WsOffsets o = ws_offsets(1, 0);
+    const size_t off_ch = align256(o.partials + (size_t)16 * nb * units);
+    const size_t off_pat = align256(off_ch + (size_t)32 * nb * nch);
+    const size_t off_G = align256(off_pat + 16);
+    const size_t off_bad = align256(off_G + (size_t)16 * nb * (h + 1));
+    int st = gbs_ws_ensure(ctx, off_bad + 16);
+    if (st) return st;
+    Plan pl = plan_from(ctx->ws, 1);
+    pl.split = kS;
+    double *chunks = (double *)((char *)ctx->ws + off_ch);
+    uint64_t *pat = (uint64_t *)((char *)ctx->ws + off_pat);
+    double *G = (double *)((char *)ctx->ws + off_G);
+    int *bad = (int *)((char *)ctx->ws + off_bad);
+    GBS_CUDA(ctx, cudaFuncSetAttribute(sweep_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Lay::bytes));
+    int nbk = 0;
+    GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, sweep_kernel<T, true>, kThreads, Lay::bytes));
+    if (nbk < 1) return gbs_fail(ctx, GBS_E_CUDA, "complex binned sweep kernel does not fit on an SM");
+    all_modes_kernel<<<1, 1, 0, ctx->stream>>>(M, pat);
+    GBS_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    // only even sectors (G_n(-t) = G_n(t)): G at t_{j + L/2} = -t_j repeats t_j, so the
+    // points j = 0..L/4 give the rest, G_j = conj G_{L/2 - j} for L/4 < j <= L/2
+    const int jmax = even ? L / 4 : h;
+    for (int j = 0; j <= jmax; ++j) {
+        const double ang = 2.0 * 3.14159265358979323846 * (double)j / (double)L;
+        pl.t_re = rho * cos(ang);
+        pl.t_im = rho * sin(ang);
+        plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pat, 1, units, pl);
+        GBS_CUDA(ctx, cudaGetLastError());
+        st = gbs_timing_begin(ctx);
+        if (st) return st;
+        sweep_kernel<T, true><<<ctx->num_sms * nbk, kThreads, Lay::bytes, ctx->stream>>>(M, O, pat, 1, pl);
+        GBS_CUDA(ctx, cudaGetLastError());
+        st = gbs_timing_end(ctx);
+        if (st) return st;
+        zbins_chunk_kernel<<<(unsigned)nch, 64, 0, ctx->stream>>>(nb, pl.partials, pl.unit_off + 1, chunks);
+        zbins_final_kernel<<<1, 64, 0, ctx->stream>>>(M, nch, chunks, logdet, pl.pflags, pl.overflow,
+                                                       G + (size_t)2 * nb * j, bad);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    if (even && jmax < h)
+        mirror_kernel<<<(unsigned)(h - jmax), 64, 0, ctx->stream>>>(nb, h, jmax, G);
+    const long long tot = (long long)(K + 1) * nb;
+    sector_dft_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(M, L, rho, K, G, bad, pkn);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }

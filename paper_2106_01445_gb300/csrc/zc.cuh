@@ -1,0 +1,37 @@
+// Complex FP64 arithmetic for the sector-resolved sweep (the generating-function
+// variable t of the photon-number sectors is taken on a circle in the complex plane).
+#pragma once
+#include <math.h>
+
+struct zc {
+    double re, im;
+    zc() = default;
+    __host__ __device__ zc(double r) : re(r), im(0.0) {}
+    __host__ __device__ zc(double r, double i) : re(r), im(i) {}
+};
+
+__device__ __forceinline__ zc operator+(zc a, zc b) { return zc(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ zc operator-(zc a, zc b) { return zc(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ zc operator-(zc a) { return zc(-a.re, -a.im); }
+__device__ __forceinline__ zc operator*(zc a, zc b) {
+    return zc(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+__device__ __forceinline__ zc &operator+=(zc &a, zc b) { return a = a + b; }
+__device__ __forceinline__ bool zc_nan(zc a) { return a.re != a.re || a.im != a.im; }
+
+// principal 1/sqrt(z), z != 0: sqrt(z) = (s, y / 2s), s = sqrt((|z| + x) / 2) for x >= 0
+// (the mirrored form for x < 0), then its reciprocal
+__device__ __forceinline__ zc zc_rsqrt(zc z) {
+    const double r = hypot(z.re, z.im);
+    double sr, si;
+    if (z.re >= 0.0) {
+        sr = sqrt(0.5 * (r + z.re));
+        si = z.im / (2.0 * sr);
+    } else {
+        const double s = sqrt(0.5 * (r - z.re));
+        sr = fabs(z.im) / (2.0 * s);
+        si = copysign(s, z.im);
+    }
+    const double q = 1.0 / (sr * sr + si * si);
+    return zc(sr * q, -si * q);
+}

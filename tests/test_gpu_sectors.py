@@ -1,0 +1,80 @@
+"""Photon-number sectors of the whole device's click distribution (gbs_sector_distribution):
+complex FP64 sweeps over all 2^M subsets at L points of a circle, binned by size, then the
+DFT over the circle.  Checked against the oracle (all patterns, exact sector series), against
+the click-number distribution of the double-double sweep (sum over k) and against the closed
+form of the total photon-number distribution (sum over n)."""
+import numpy as np
+import pytest
+import torch
+
+import gbs_inputs as g
+import oracle
+from oracle import approx as ap
+
+from test_oracle_sectors import photon_distribution
+
+pytestmark = pytest.mark.gpu
+
+# FP64 subset terms: absolute error ~ 1.1e-16 x the transform's cancellation (kappa <= 1e3 on
+# these small devices) x the DFT's L terms (<= 256) ~ 3e-11; the bound below keeps a margin.
+ATOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_ok):
+    from paper_2106_01445_gb300 import build
+    build.build()
+    from paper_2106_01445_gb300.api import Context
+    return Context(0)
+
+
+def gpu_pkn(ctx, U, r, eta, L, rho, K, even_only=False):
+    st = ctx.build_state(U, r, eta)
+    pkn = ctx.sector_distribution(st["O"], st["logdet"], L=L, rho=rho, K=K, even_only=even_only)
+    torch.cuda.synchronize()
+    return pkn.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("eta,rho", [(1.0, 1.0), (1.0, 0.9), (0.5, 1.0), (0.7, 0.8)])
+def test_matches_oracle_over_all_patterns(ctx, eta, rho):
+    M, K = 8, 60
+    U, r = g.haar_unitary(M, 21), g.squeezing(M, 4, 0.6, 1.0, 21)
+    got, _ = gpu_pkn(ctx, U, r, eta, 128, rho, K)
+    st = oracle.build_state(U, r, eta)
+    ref = ap.sector_distribution(st.O, st.logdet, M, K)
+    assert got.shape == (K + 1, M + 1)
+    # the DFT divides sector k by rho^k: so does its error
+    tol = ATOL * rho ** -np.arange(K + 1.0)
+    assert (np.abs(got - ref) < tol[:, None]).all()
+    if eta == 1.0:
+        even, _ = gpu_pkn(ctx, U, r, eta, 128, rho, K, even_only=True)
+        assert (np.abs(even - ref) < tol[:, None]).all()
+
+
+def test_sum_over_sectors_is_click_distribution(ctx):
+    M = 20
+    U, r = g.haar_unitary(M, 22), g.squeezing(M, 10, 0.5, 0.9, 22)
+    got, st = gpu_pkn(ctx, U, r, 0.7, 256, 1.0, 255)
+    logp, kappa = ctx.click_distribution(st["O"], st["logdet"])
+    pn = np.exp(logp.cpu().numpy())
+    big = pn > 1e-6
+    assert np.allclose(got.sum(axis=0)[big], pn[big], rtol=1e-8)
+
+
+@pytest.mark.parametrize("eta", [1.0, 0.5])
+def test_sum_over_clicks_is_photon_distribution(ctx, eta):
+    M, K = 16, 80
+    U, r = g.haar_unitary(M, 23), g.squeezing(M, 8, 0.6, 0.9, 23)
+    got, _ = gpu_pkn(ctx, U, r, eta, 256, 1.0, K)
+    assert np.abs(got.sum(axis=1) - photon_distribution(r, eta, K)).max() < ATOL
+    if eta == 1.0:
+        assert np.abs(got[1::2]).max() < ATOL
+
+
+@pytest.mark.parametrize("L,rho,K,M", [(100, 1.0, 10, 8), (64, 1.5, 10, 8), (64, 1.0, 64, 8), (64, 1.0, 10, 3)])
+def test_rejects_bad_arguments(ctx, L, rho, K, M):
+    from paper_2106_01445_gb300._lib import GbsError
+    U, r = g.haar_unitary(M, 1), g.squeezing(M, M // 2, 0.5, 0.5, 1)
+    st = ctx.build_state(U, r, 1.0)
+    with pytest.raises(GbsError):
+        ctx.sector_distribution(st["O"], st["logdet"], L=L, rho=rho, K=K)
