@@ -563,6 +563,25 @@ def run_workloads(dev, stream, meas, fp32_peak):
                         "max_abs_odd_sector": float(np.abs(pkn[1::2]).max()),
                         "p_k_n": {str(k): [float(x) for x in pkn[k]] for k in (20, 50, 80, 110, 140, 170)},
                         "peak_n": {str(k): int(np.argmax(pkn[k])) for k in (20, 50, 80, 110, 140, 170)}}
+    # the approximation's fitted sector curves of the all-click pattern (the whole device)
+    # against these exact sectors: the k = 110 curve and every sector's all-click point
+    # (the paper's Fig. 3a and 3b)
+    fig3 = {}
+    main = pkn[110] > 1e-3 * pkn[110].max()
+    w30 = pkn[:, c.M]
+    big = w30 > 1e-3 * w30.max()
+    for order in (2, 3, 4):
+        cur, lp, _ = ctx.approx_sector_curves(st["O"], st["logdet"], allp, order=order, precision="ff", K=255)
+        cur = cur.cpu().numpy()
+        dev110 = np.abs(cur[110] / np.where(main, pkn[110], 1.0) - 1.0)[main]
+        dev30 = np.abs(cur[big, c.M] / w30[big] - 1.0)
+        fig3["order%d" % order] = {"k110_max_rel_dev_main_body": float(dev110.max()),
+                                   "k110_rel_dev_at_n30": float(cur[110, c.M] / pkn[110, c.M] - 1.0),
+                                   "k110_curve": [float(x) for x in cur[110]],
+                                   "all_click_sectors_rel_dev_median": float(np.median(dev30)),
+                                   "all_click_sectors_rel_dev_max": float(dev30.max()),
+                                   "all_click_sum_rel_dev": float(cur[:, c.M].sum() / w30.sum() - 1.0)}
+    entry["sectors"]["fit_vs_exact"] = fig3
     res["m30_device"] = entry
 
     # ---- the fourth-order accuracy study (the paper's Fig. 4): relative deviation of the

@@ -171,6 +171,23 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
 int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
                             int K, int even_only, double *pkn);
 
+/* The approximation's fitted sector curves for one pattern S with n clicks (Results,
+ * "Approximation scheme": p_k ~ exp(-f_j), and the paper's Fig. 3a): the same steps as
+ * gbs_prob at order j (minors at the tilted contour points, DFT, per-sector factorial
+ * moments, maximum-entropy fit of degree min(j, support - 1)), but each sector's whole
+ * fitted distribution is returned, not only its all-clicked point: row k of curves
+ * ((K + 1) x (n + 1) doubles, device) holds det(sigma_Q)^{-1/2} rho^-k q_k(v) at column
+ * c = n - v, the estimate of P(c of the n detectors of S click, every other dark, k photons).
+ * For S = all M modes this is the estimate of the whole device's sectors p_k(c)
+ * (compare gbs_sector_distribution).  Sectors with fewer photons than clicks needed are
+ * fitted too; rows past the pattern's sector range and sectors below the noise floor are
+ * zero.  pattern: one device pattern; n must be its click count.  precision: GBS_FP64 or
+ * GBS_FF.  logP, status: the pattern's estimate as gbs_prob (device, one each).  Errors:
+ * GBS_E_INVALID (sizes, n not the pattern's clicks), GBS_E_CUDA, GBS_E_NOMEM. */
+int gbs_approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                             const uint64_t *pattern, int n, int order, int precision, int K, double *curves,
+                             double *logP, int32_t *status);
+
 /* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
  * has no counterpart: this serves callers that cannot call cudaMalloc (code
  * running under another owner's stream capture, processes whose device memory

@@ -285,3 +285,45 @@ def sector_distribution(O: np.ndarray, logdet_sigmaQ: float, M: int, K: int) -> 
         modes = [i for i in range(M) if mask >> i & 1]
         out[:, len(modes)] += exact_sector_last_points(O, M, modes, K)
     return out * math.exp(-0.5 * logdet_sigmaQ)
+
+
+def sector_curve(Dk: np.ndarray, n: int, k: int, j: int):
+    """The order-j estimate of sector k's whole distribution q_k(v), v = 0..n, from its
+    factorial moments D_0..D_j (Results, "Approximation scheme": exp(-f_j) fitted to the
+    moments on the sector's support v in [max(0, n-k), n-1]; k = 0 is v = n alone).
+    Returns (q, flag) with the flags of sector_last_point."""
+    q = np.zeros(n + 1)
+    if Dk[0] <= 0.0:
+        return q, 0
+    if k == 0 or n == 0:
+        q[n] = Dk[0] if k == 0 else 0.0
+        return q, 0
+    v = np.arange(max(0, n - k), n, dtype=np.float64)
+    Jmax = min(j, v.size - 1)
+    mu = raw_moments(Dk, Jmax)
+    x = v / n
+    for J in range(Jmax, -1, -1):
+        mnorm = np.array([mu[i] / n ** i for i in range(J + 1)]) / mu[0]
+        a, ok = maxent_fit(x, mnorm)
+        if ok:
+            q[v.astype(int)] = mu[0] * np.exp(-np.vander(x, J + 1, increasing=True) @ a)
+            return q, 0 if J == Jmax else 1
+    return q, 2
+
+
+def approx_sector_curves(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int, K: int):
+    """Every sector's fitted distribution for the pattern S (the tilt and sector range of
+    approx_logprob): out[k, c] = det(sigma_Q)^{-1/2} rho^-k q_k(v = n - c), k = 0..K."""
+    modes = list(modes)
+    n = len(modes)
+    rho = choose_tilt(O, M, modes)
+    Kmax = choose_kmax(O, M, modes, rho)
+    D = factorial_moment_tables(O, M, modes, j, Kmax, rho)
+    floor = EPS_SECTOR * D[0].max()
+    out = np.zeros((K + 1, n + 1))
+    for k in range(min(K, Kmax) + 1):
+        if D[0, k] < floor:
+            continue
+        q, _ = sector_curve(D[:, k], n, k, j)
+        out[k] = q[::-1] * math.exp(-0.5 * logdet_sigmaQ - k * math.log(rho))
+    return out

@@ -100,6 +100,23 @@ class Context:
                                                      int(bool(even_only)), _ptr(pkn)))
         return pkn
 
+    def approx_sector_curves(self, O: torch.Tensor, logdet: torch.Tensor, pattern, order: int = 4,
+                             precision="ff", K: int = 255):
+        """The order-j fit of every photon-number sector of one pattern S with n clicks:
+        (K + 1) x (n + 1) device tensor, row k = the estimate of P(c clicks in S, k photons)
+        at column c; plus the pattern's (logP, status)."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(pattern, self.device)[:1]
+        pat = pats.cpu().numpy()[0]
+        n = sum(bin(int(w) & 0xFFFFFFFFFFFFFFFF).count("1") for w in pat)
+        curves = torch.empty((K + 1, n + 1), dtype=torch.float64, device=self.device)
+        logP = torch.empty(1, dtype=torch.float64, device=self.device)
+        status = torch.empty(1, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gbs_approx_sector_curves(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), n, int(order),
+                                                      PRECISIONS[precision], int(K), _ptr(curves), _ptr(logP),
+                                                      _ptr(status)))
+        return curves, logP, status
+
     def autotune(self, O: torch.Tensor, logdet: torch.Tensor, patterns, precision="fx"):
         """Pick the exact sweep's work split for this precision on these patterns
         (kept in the context); returns (split, ms of one sweep).  Synchronous; call it

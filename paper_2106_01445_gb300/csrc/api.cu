@@ -165,6 +165,17 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
     return click_distribution(ctx, M, O, logdet_sigmaQ, logp, kappa);
 }
 
+int gbs_approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                             const uint64_t *pattern, int n, int order, int precision, int K, double *curves,
+                             double *logP, int32_t *status) {
+    if (!ctx) return GBS_E_INVALID;
+    if (!O || !logdet_sigmaQ || !pattern || !curves || !logP || !status)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: null pointer");
+    if (M < 1 || M > 128) return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: M = %d", M);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return approx_sector_curves(ctx, M, O, logdet_sigmaQ, pattern, n, order, precision, K, curves, logP, status);
+}
+
 int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
                             int K, int even_only, double *pkn) {
     if (!ctx) return GBS_E_INVALID;

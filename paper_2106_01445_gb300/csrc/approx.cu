@@ -701,9 +701,13 @@ __global__ void __launch_bounds__(kDftThreads) approx_dft_kernel(int order, Appr
 }
 
 // one warp per (pattern, sector k): factorial moments -> raw moments (Stirling numbers)
-// -> maximum-entropy fit on the support v in [max(0, n - k), n - 1] -> the last point
+// -> maximum-entropy fit on the support v in [max(0, n - k), n - 1] -> the last point.
+// curves (one pattern only, else null): every sector's fitted distribution over the
+// clicks c = n - v, tilted, row k of curve_K + 1 rows of n + 1 (sectors with fewer photons
+// than detectors are fitted too)
 __global__ void __launch_bounds__(kSecThreads) approx_sector_fit_kernel(int n_pat, int order, double sector_eps,
-                                                                      ApproxPlan pl) {
+                                                                      ApproxPlan pl, double *__restrict__ curves,
+                                                                      int curve_K) {
     const int lane = threadIdx.x & 31;
     const long long nsec = pl.sec_off[n_pat];
     const long long nwarps = (long long)gridDim.x * (kSecThreads / 32);
@@ -721,9 +725,11 @@ __global__ void __launch_bounds__(kSecThreads) approx_sector_fit_kernel(int n_pa
         const double D0 = Dk[0];
         double val = 0.0;
         bool fell = false;
+        const bool curve = curves != nullptr && k <= curve_K;
+        if (curve && k == 0 && D0 > 0.0 && lane == 0) curves[0] = D0;   // no photon: no click (c = 0)
         if (n == 0) {
             val = (k == 0) ? D0 : 0.0;
-        } else if (k >= n && D0 >= sector_eps * pl.pat_max[p] && D0 > 0.0) {
+        } else if ((k >= n || (curve && k >= 1)) && D0 >= sector_eps * pl.pat_max[p] && D0 > 0.0) {
             const int v0 = n - k > 0 ? n - k : 0;
             const int S = n - v0;
             const int Jmax = order < S - 1 ? order : S - 1;
@@ -742,15 +748,31 @@ __global__ void __launch_bounds__(kSecThreads) approx_sector_fit_kernel(int n_pa
                 double np = 1.0;
                 for (int i = 0; i <= J; ++i) { m[i] = mu[i] / np / mu[0]; np *= n; }
                 if (maxent_fit_warp(v0, n, J, m, a, lane)) {
-                    val = mu[0] * exp(-a[0]);
+                    val = k >= n ? mu[0] * exp(-a[0]) : 0.0;
                     done = true;
                     if (J != Jmax) fell = true;
+                    if (curve)
+                        for (int v = v0 + lane; v < n; v += 32) {
+                            const double x = (double)v / n;
+                            double f = a[J];
+                            for (int i = J - 1; i >= 0; --i) f = f * x + a[i];
+                            curves[(size_t)k * (n + 1) + (n - v)] = mu[0] * exp(-f);
+                        }
                 }
             }
             if (!done) fell = true;
         }
         if (lane == 0) pl.sec_part[gs] = fell ? -val : val;   // the sign marks a fallback
     }
+}
+
+// the curves untilted (rho^-k) and scaled by det(sigma_Q)^{-1/2}
+__global__ void approx_curve_scale_kernel(int curve_K, int n, const double *__restrict__ logdet, ApproxPlan pl,
+                                          double *__restrict__ curves) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= (long long)(curve_K + 1) * (n + 1)) return;
+    const int k = (int)(f / (n + 1));
+    curves[f] = *pl.overflow ? nan("") : curves[f] * exp(-0.5 * (*logdet) - k * log(pl.pat_rho[0]));
 }
 
 // per pattern (one warp): sum_k part_k rho^{-k} in logs (the tables are tilted by rho^k)
@@ -846,7 +868,8 @@ ApproxPlan approx_plan_from(void *ws, int n_pat, long long units = 0, long long 
 
 template <typename R>
 int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
-               int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status) {
+               int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status,
+               double *curves = nullptr, int curve_K = -1, int curve_n = -1) {
     // patterns up to this size are taken
     const int nmax_smem = MinorPrec<R>::nmax;
     static_assert(kMaxK + 1 <= 4096, "sector table");
@@ -904,9 +927,23 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     GBS_CUDA(ctx, cudaGetLastError());
     const long long want = (secs + kSecThreads / 32 - 1) / (kSecThreads / 32);
     const int fit_blocks = (int)(want < (long long)ctx->num_sms * 16 ? (want > 0 ? want : 1) : ctx->num_sms * 16);
+    if (curves) {
+        // one pattern: its clicks (read back above) must be the caller's row width - 1
+        if (nmax != curve_n)
+            return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: the pattern has %d clicks, not n = %d",
+                            nmax, curve_n);
+        GBS_CUDA(ctx, cudaMemsetAsync(curves, 0, sizeof(double) * (size_t)(curve_K + 1) * (curve_n + 1),
+                                      ctx->stream));
+    }
     approx_sector_fit_kernel<<<fit_blocks, kSecThreads, 0, ctx->stream>>>(
-        n_pat, order, MinorPrec<R>::sector_eps, pl);
+        n_pat, order, MinorPrec<R>::sector_eps, pl, curves, curve_K);
     GBS_CUDA(ctx, cudaGetLastError());
+    if (curves) {
+        const long long tot = (long long)(curve_K + 1) * (nmax + 1);
+        approx_curve_scale_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(curve_K, nmax, logdet, pl,
+                                                                                          curves);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
     approx_sum_kernel<<<(n_pat + kSumThreads / 32 - 1) / (kSumThreads / 32), kSumThreads, 0, ctx->stream>>>(
         n_pat, logdet, pl, logP, kappa, err_bound, status);
     GBS_CUDA(ctx, cudaGetLastError());
@@ -927,4 +964,17 @@ int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
     if (precision == GBS_FF)
         return run_approx<ff>(ctx, M, O, logdet, patterns, n_pat, order, logP, kappa, err_bound, status);
     return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: the approximation runs in FP64, float-float or the FP32 split");
+}
+
+int approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pattern,
+                         int n, int order, int precision, int K, double *curves, double *logP, int32_t *status) {
+    if (order < 1 || order > kMaxOrder)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: order %d not in 1..%d", order, kMaxOrder);
+    if (n < 1 || n > M || K < 0)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: bad sizes (n=%d, M=%d, K=%d)", n, M, K);
+    if (precision == GBS_FP64)
+        return run_approx<double>(ctx, M, O, logdet, pattern, 1, order, logP, nullptr, nullptr, status, curves, K, n);
+    if (precision == GBS_FF)
+        return run_approx<ff>(ctx, M, O, logdet, pattern, 1, order, logP, nullptr, nullptr, status, curves, K, n);
+    return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: the curves run in FP64 or float-float");
 }

@@ -77,6 +77,8 @@ int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logd
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);
+int approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pattern,
+                         int n, int order, int precision, int K, double *curves, double *logP, int32_t *status);
 int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                 int n_pat, const double *w, double *dsq, double *logP, int32_t *status);
 int grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta, const double *dsq,

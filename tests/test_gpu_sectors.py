@@ -78,3 +78,53 @@ def test_rejects_bad_arguments(ctx, L, rho, K, M):
     st = ctx.build_state(U, r, 1.0)
     with pytest.raises(GbsError):
         ctx.sector_distribution(st["O"], st["logdet"], L=L, rho=rho, K=K)
+
+
+# ---- the approximation's fitted sector curves (gbs_approx_sector_curves) ---------------
+@pytest.mark.parametrize("order,precision", [(2, "fp64"), (3, "fp64"), (4, "fp64"), (4, "ff")])
+def test_curves_match_oracle(ctx, order, precision):
+    """Whole-device curves (S = all 8 modes) against the oracle's fit, row by row: the fit's
+    parameters agree to the 1e-8 of the last points (gbs_prob's tolerance), relative to the
+    row's largest value."""
+    M, K = 8, 255
+    U, r = g.haar_unitary(M, 24), g.squeezing(M, 4, 0.7, 1.0, 24)
+    st = ctx.build_state(U, r, 0.8)
+    pat = g.modes_to_pattern(range(M))[None]
+    curves, logP, status = ctx.approx_sector_curves(st["O"], st["logdet"], pat, order=order,
+                                                    precision=precision, K=K)
+    got = curves.cpu().numpy()
+    so = oracle.build_state(U, r, 0.8)
+    ref = ap.approx_sector_curves(so.O, so.logdet, M, range(M), order, K)
+    # plus a floor for the rows one side leaves empty: sectors past the oracle's exact range
+    # (the kernel's Chernoff bound reaches further; their mass is below 1e-14) and sectors
+    # under the noise floor (1e-12 of the largest tilted sector)
+    tol = (1e-8 if precision == "fp64" else 1e-6) * np.abs(ref).max(axis=1, keepdims=True) + 1e-11 * ref.max()
+    assert (np.abs(got - ref) <= tol).all()
+    # the all-clicked column summed over the sectors (every row of the pattern's sector
+    # range: K covers it here) is the pattern's estimate
+    assert abs(np.log(got[:, M].sum()) - logP.item()) < 1e-12
+
+
+def test_curves_at_full_order_are_the_exact_sectors(ctx):
+    M = 5
+    U, r = g.haar_unitary(M, 25), g.squeezing(M, 3, 0.6, 0.9, 25)
+    st = ctx.build_state(U, r, 0.6)
+    pat = g.modes_to_pattern(range(M))[None]
+    curves, _, _ = ctx.approx_sector_curves(st["O"], st["logdet"], pat, order=4, precision="fp64", K=60)
+    exact = ctx.sector_distribution(st["O"], st["logdet"], L=128, rho=1.0, K=60)
+    assert np.abs(curves.cpu().numpy() - exact.cpu().numpy()).max() < ATOL
+
+
+def test_curves_reject_a_wrong_click_count(ctx):
+    from paper_2106_01445_gb300._lib import GbsError, GBS_FP64
+    from paper_2106_01445_gb300.api import _ptr, patterns_tensor
+    M = 8
+    U, r = g.haar_unitary(M, 26), g.squeezing(M, 4, 0.7, 0.7, 26)
+    st = ctx.build_state(U, r, 1.0)
+    pats = patterns_tensor(g.modes_to_pattern(range(M))[None], ctx.device)
+    curves = torch.empty((11, 8), dtype=torch.float64, device=ctx.device)
+    lp = torch.empty(1, dtype=torch.float64, device=ctx.device)
+    stt = torch.empty(1, dtype=torch.int32, device=ctx.device)
+    with pytest.raises(GbsError):
+        ctx._check(ctx.lib.gbs_approx_sector_curves(ctx.h, M, _ptr(st["O"]), _ptr(st["logdet"]), _ptr(pats), 7, 4,
+                                                    GBS_FP64, 10, _ptr(curves), _ptr(lp), _ptr(stt)))

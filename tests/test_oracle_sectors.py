@@ -64,3 +64,31 @@ def test_sector_support():
     assert np.abs(pkn[k < n]).max() < 1e-14
     assert np.abs(pkn[1::2]).max() < 1e-14
     assert abs(pkn[0, 0] - math.exp(-0.5 * st.logdet)) < 1e-15
+
+
+@pytest.mark.parametrize("M,eta", [(4, 1.0), (5, 0.6)])
+def test_curves_at_full_order_are_the_exact_sectors(M, eta):
+    """With order >= the support size - 1 the fit reproduces the moments' distribution
+    exactly, so the whole-device curves of S = all modes are the sectors p_k(c)."""
+    U, r = g.haar_unitary(M, 14), g.squeezing(M, M // 2 + 1, 0.6, 0.9, 14)
+    st = oracle.build_state(U, r, eta)
+    K = 30
+    got = ap.approx_sector_curves(st.O, st.logdet, M, range(M), 4, K)
+    ref = ap.sector_distribution(st.O, st.logdet, M, K)
+    assert np.abs(got - ref).max() < 1e-12
+
+
+def test_curve_matches_the_sector_moments():
+    """A fitted sector distribution reproduces its factorial moments D_0..D_j."""
+    M, n, j = 10, 8, 3
+    U, r = g.haar_unitary(M, 15), g.squeezing(M, 5, 0.8, 1.0, 15)
+    st = oracle.build_state(U, r, 0.7)
+    modes = list(range(n))
+    D = ap.factorial_moment_tables(st.O, M, modes, j, 40)
+    for k in (8, 12, 20):
+        q, flag = ap.sector_curve(D[:, k], n, k, j)
+        assert flag == 0
+        v = np.arange(n + 1)
+        for w in range(j + 1):
+            fm = (q * np.array([math.comb(int(x), w) for x in v])).sum()
+            assert abs(fm - D[w, k]) <= 1e-9 * D[w, k]
