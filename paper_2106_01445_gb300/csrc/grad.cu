@@ -108,9 +108,13 @@ __device__ dd tree_pivot(dd *UM, int D, int c0, dd *Wb, dd *Qout, dd *rsout, int
 //   pivot rows:  -rs Y,  Y = P^{-1} B Gamma(inc)
 //   pivot block: rs (Y B^T P^{-1} - S(inc) P^{-1} / 2)
 // then back through the prefix pivots the same way (with -V P^{-1} / 2 from tau_prefix),
-// added into the pattern's Gbar at the unit's rows.  One CTA per pattern; units in order.
+// added into the chunk's partial Gbar at the unit's rows.  One CTA per chunk: a run of
+// consecutive units [u0, u1) of one pattern, in order (the chunks of a pattern are
+// summed in order afterwards: deterministic).
 __global__ void __launch_bounds__(kTreeThreads) grad_tree_kernel(int M, const double *__restrict__ O,
                                                                const uint64_t *__restrict__ pats, int n_pat,
+                                                               const int *__restrict__ chunk_p,
+                                                               const long long *__restrict__ chunk_u,
                                                                double *__restrict__ part_hi,
                                                                double *__restrict__ part_lo,
                                                                double *__restrict__ part_T, int *__restrict__ flags) {
@@ -123,7 +127,8 @@ __global__ void __launch_bounds__(kTreeThreads) grad_tree_kernel(int M, const do
     __shared__ int rowmode[kGD];
     __shared__ int s_n, s_k, s_bad;
     __shared__ dd s_T, s_V;
-    const int t = threadIdx.x, p = blockIdx.x, N2 = 2 * M;
+    const int t = threadIdx.x, ch = blockIdx.x, p = chunk_p[ch], N2 = 2 * M;
+    const long long u_begin = chunk_u[2 * ch], u_end = chunk_u[2 * ch + 1];
     if (t == 0) {
         int n = 0;
         for (int i = 0; i < M; ++i) {
@@ -132,12 +137,12 @@ __global__ void __launch_bounds__(kTreeThreads) grad_tree_kernel(int M, const do
         }
         s_n = n;
         s_bad = 0;
-        s_T = dd(n == 0 ? 1.0 : 0.0);
+        s_T = dd(n == 0 && u_begin == 0 ? 1.0 : 0.0);
     }
     __syncthreads();
     const int n = s_n, m = n < kTM ? n : kTM, q = n - m, Dn = 2 * n;
     for (int f = t; f < gsym(Dn); f += kTreeThreads) Gacc[f] = dd(0.0);
-    for (long long u = 0; n > 0 && u < (1ll << q); ++u) {
+    for (long long u = u_begin; n > 0 && u < u_end; ++u) {
         if (t == 0) {
             int k = 0;
             for (int a = 0; a < q; ++a)
@@ -349,12 +354,12 @@ __global__ void __launch_bounds__(kTreeThreads) grad_tree_kernel(int M, const do
     for (int f = t; f < Dn * Dn; f += kTreeThreads) {
         const int i = f / Dn, j = f - i * Dn;
         const dd g = Gacc[gpany(Dn, i, j)];
-        part_hi[(size_t)p * kGD * kGD + f] = g.hi;
-        part_lo[(size_t)p * kGD * kGD + f] = g.lo;
+        part_hi[(size_t)ch * kGD * kGD + f] = g.hi;
+        part_lo[(size_t)ch * kGD * kGD + f] = g.lo;
     }
     if (t == 0) {
-        part_T[2 * p] = s_T.hi;
-        part_T[2 * p + 1] = s_T.lo;
+        part_T[2 * ch] = s_T.hi;
+        part_T[2 * ch + 1] = s_T.lo;
         if (s_bad) atomicOr(flags + p, 1);
     }
 }
@@ -597,12 +602,6 @@ __global__ void clements_grad_kernel(int M, const double *__restrict__ theta, co
 }
 
 // one partial per pattern
-__global__ void grad_plan_kernel(int n_pat, long long *__restrict__ chunk_off, int *__restrict__ flags) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p <= n_pat) chunk_off[p] = p;
-    if (p < n_pat) flags[p] = 0;
-}
-
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
@@ -610,13 +609,13 @@ size_t al(size_t x) { return (x + 255) / 256 * 256; }
 int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                 int n_pat, const double *w, double *dsq, double *logP, int32_t *status) {
     // every pattern must be valid and have at most kGradMaxN clicks: checked on the host
-    // from a copy of the pattern words (one small readback)
+    // from a copy of the pattern words (one small readback), which also sizes the chunks
     size_t pb = (size_t)n_pat * 16;
     uint64_t *hp = (uint64_t *)malloc(pb + 16);
     if (!hp) return gbs_fail(ctx, GBS_E_NOMEM, "gbs_grad: host buffer");
     GBS_CUDA(ctx, cudaMemcpyAsync(hp, pats, pb, cudaMemcpyDeviceToHost, ctx->stream));
     GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const long long chunks = n_pat;
+    long long total_units = 0;
     for (int p = 0; p < n_pat; ++p) {
         uint64_t lo = hp[2 * p], hi = hp[2 * p + 1];
         int n = __builtin_popcountll(lo) + __builtin_popcountll(hi);
@@ -626,29 +625,77 @@ int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
             return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad: pattern %d has %d clicks (at most %d) or a detector >= M",
                             p, n, kGradMaxN);
         }
+        total_units += 1ll << (n > kTM ? n - kTM : 0);
     }
+    // chunks: runs of at most `per` consecutive units of one pattern, `per` sized for about
+    // eight chunks per SM over the whole batch (the largest patterns no longer set the
+    // time of the launch alone)
+    const long long target = 8ll * ctx->num_sms;
+    const long long per = total_units / target > 1 ? (total_units + target - 1) / target : 1;
+    long long chunks = 0;
+    for (int p = 0; p < n_pat; ++p) {
+        const int n = __builtin_popcountll(hp[2 * p]) + __builtin_popcountll(hp[2 * p + 1]);
+        const long long units = 1ll << (n > kTM ? n - kTM : 0);
+        chunks += (units + per - 1) / per;
+    }
+    const size_t tb = sizeof(long long) * ((size_t)n_pat + 1) + sizeof(long long) * 2 * (size_t)chunks +
+                      sizeof(int) * (size_t)chunks;
+    char *ht = (char *)malloc(tb);
+    if (!ht) {
+        free(hp);
+        return gbs_fail(ctx, GBS_E_NOMEM, "gbs_grad: host buffer");
+    }
+    long long *h_off = (long long *)ht, *h_u = h_off + (n_pat + 1);
+    int *h_p = (int *)(h_u + 2 * chunks);
+    long long c = 0;
+    for (int p = 0; p < n_pat; ++p) {
+        const int n = __builtin_popcountll(hp[2 * p]) + __builtin_popcountll(hp[2 * p + 1]);
+        const long long units = 1ll << (n > kTM ? n - kTM : 0);
+        h_off[p] = c;
+        for (long long u0 = 0; u0 < units; u0 += per, ++c) {
+            h_p[c] = p;
+            h_u[2 * c] = u0;
+            h_u[2 * c + 1] = u0 + per < units ? u0 + per : units;
+        }
+    }
+    h_off[n_pat] = c;
     free(hp);
     const int N = 2 * M;
-    size_t o_off = 0, o_flags = al(o_off + 8 * ((size_t)n_pat + 1)), o_phi = al(o_flags + 4 * (size_t)n_pat),
+    size_t o_off = 0, o_cu = al(o_off + 8 * ((size_t)n_pat + 1)), o_cp = al(o_cu + 16 * (size_t)chunks),
+           o_flags = al(o_cp + 4 * (size_t)chunks), o_phi = al(o_flags + 4 * (size_t)n_pat),
            o_plo = al(o_phi + 8 * (size_t)chunks * kGD * kGD), o_pT = al(o_plo + 8 * (size_t)chunks * kGD * kGD),
            o_F = al(o_pT + 16 * (size_t)chunks), o_H = al(o_F + 8 * (size_t)n_pat * kGD * kGD),
            o_T1 = al(o_H + 8 * (size_t)N * N), o_T2 = al(o_T1 + 8 * (size_t)N * N), o_sw = al(o_T2 + 8 * (size_t)N * N),
            total = o_sw + 64;
     int st = gbs_ws_ensure(ctx, total);
-    if (st) return st;
+    if (st) {
+        free(ht);
+        return st;
+    }
     char *b = (char *)ctx->ws;
-    long long *chunk_off = (long long *)(b + o_off);
+    long long *chunk_off = (long long *)(b + o_off), *chunk_u = (long long *)(b + o_cu);
+    int *chunk_p = (int *)(b + o_cp);
     int *flags = (int *)(b + o_flags);
     double *phi_ = (double *)(b + o_phi), *plo = (double *)(b + o_plo), *pT = (double *)(b + o_pT);
     double *F = (double *)(b + o_F), *H = (double *)(b + o_H), *T1 = (double *)(b + o_T1),
            *T2 = (double *)(b + o_T2), *sw = (double *)(b + o_sw);
-    grad_plan_kernel<<<(n_pat + 1 + 255) / 256, 256, 0, ctx->stream>>>(n_pat, chunk_off, flags);
-    GBS_CUDA(ctx, cudaGetLastError());
+    // the chunk table (copied before the host buffer is released)
+    cudaError_t ce = cudaMemcpyAsync(chunk_off, h_off, sizeof(long long) * ((size_t)n_pat + 1),
+                                     cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(chunk_u, h_u, sizeof(long long) * 2 * (size_t)chunks, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(chunk_p, h_p, sizeof(int) * (size_t)chunks, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    free(ht);
+    GBS_CUDA(ctx, ce);
+    GBS_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n_pat, ctx->stream));
     const size_t smem = sizeof(dd) * (size_t)kTreeSmem;
     GBS_CUDA(ctx, cudaFuncSetAttribute(grad_tree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     st = gbs_timing_begin(ctx);
     if (st) return st;
-    grad_tree_kernel<<<n_pat, kTreeThreads, smem, ctx->stream>>>(M, O, pats, n_pat, phi_, plo, pT, flags);
+    grad_tree_kernel<<<(unsigned)chunks, kTreeThreads, smem, ctx->stream>>>(M, O, pats, n_pat, chunk_p, chunk_u,
+                                                                           phi_, plo, pT, flags);
     GBS_CUDA(ctx, cudaGetLastError());
     st = gbs_timing_end(ctx);
     if (st) return st;
