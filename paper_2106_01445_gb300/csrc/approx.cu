@@ -85,14 +85,19 @@ template <typename R> __device__ __forceinline__ cx<R> init_entry(bool diag, dou
 // memory) and the tilted-sector share below which a sector counts as rounding noise
 template <typename R> struct MinorPrec;
 template <> struct MinorPrec<double> {
+    static constexpr int min_blocks = 1;
     static constexpr int nmax = 79;
     static constexpr double sector_eps = 1e-12;  // tilted sectors below this share of the largest: noise
 };
 template <> struct MinorPrec<ff> {
+    // two CTAs per SM: capped at 128 registers (a few spills) it runs 14% faster than one
+    // CTA of 255-register threads
+    static constexpr int min_blocks = 2;
     static constexpr int nmax = 79;
     static constexpr double sector_eps = 1e-12;
 };
 template <> struct MinorPrec<float> {
+    static constexpr int min_blocks = 1;
     static constexpr int nmax = 112;
     static constexpr double sector_eps = 1e-6;  // moments resolved to ~1e-7 K
 };
@@ -308,7 +313,7 @@ template <> struct GroupAcc<float> {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kMinorThreads) approx_minors_kernel(int M, const double *__restrict__ O,
+__global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) approx_minors_kernel(int M, const double *__restrict__ O,
                                                                     const uint64_t *__restrict__ pats,
                                                                     int n_pat, int order,
                                                                     unsigned long long *counter,

@@ -152,6 +152,29 @@ def test_n20_gradient_against_central_differences(ctx):
     assert abs(fd - deta.item()) < 1e-6 * abs(fd) + 1e-7
 
 
+def test_batch_chunks_match_single_pattern_calls(ctx):
+    """A batch large enough for chunks of several units each (about eight chunks per SM
+    over 96 patterns of 14 clicks, 128 units each) gives the sum of the one-pattern calls
+    (each a chunk per unit): the chunking changes only the order of the double-double sums."""
+    M = 20
+    U, r = g.haar_unitary(M, 41), g.squeezing(M, 10, 0.6, 1.0, 41)
+    st = ctx.build_state(U, r, 0.7)
+    pats = g.gen_patterns(41, M, 14, 14, 96)
+    w = torch.linspace(0.5, 1.5, len(pats), dtype=torch.float64, device="cuda")
+    dsq, logP, status = ctx.grad(st["O"], st["logdet"], pats, w)
+    assert (status.cpu().numpy() == 0).all()
+    acc = torch.zeros_like(dsq)
+    lps = []
+    for i in range(len(pats)):
+        d1, lp1, s1 = ctx.grad(st["O"], st["logdet"], pats[i:i + 1], w[i:i + 1])
+        acc += d1
+        lps.append(lp1.item())
+    # the -1/2 (sum w) A term is linear in w: the single calls add up to the batch's
+    got, ref = dsq.cpu().numpy(), acc.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.abs(logP.cpu().numpy() - np.array(lps)).max() < 1e-12
+
+
 def test_grad_rejects_large_patterns(ctx):
     from paper_2106_01445_gb300 import GbsError
     M = 30
