@@ -103,7 +103,7 @@ template <> struct MinorPrec<ff> {
     static constexpr double sector_eps = 1e-12;
 };
 template <> struct MinorPrec<float> {
-    static constexpr int min_blocks = 1;
+    static constexpr int min_blocks = 2;  // 127 registers: two CTAs per SM
     static constexpr int nmax = 112;
     static constexpr double sector_eps = 1e-6;  // moments resolved to ~1e-7 K
 };
