@@ -141,8 +141,9 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
  *   p(n) = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n - z} C(M - z, n - z) E_z,
  *   E_z  = sum over the subsets Z of the M modes with |Z| = z of det(A_Z)^{-1/2}:
  * one double-double sweep over all 2^M subsets with the terms binned by size, then the
- * binomial transform in double-double with exact binomials.  4 <= M <= 40 (2^M subsets:
- * about a second at M = 30).  logp, kappa: M + 1 doubles (device; kappa may be NULL),
+ * binomial transform in double-double with exact binomials.  4 <= M <= 36 (2^M subsets:
+ * about a second at M = 30, a minute at 36; the workspace holds 16 (M + 1) bytes per unit of
+ * 2^13 subsets, 5 GB at M = 36).  logp, kappa: M + 1 doubles (device; kappa may be NULL),
  * kappa[n] = sum_z C(M - z, n - z) E_z / |sum with signs|, the transform's cancellation;
  * logp[n] = NaN where the sum is not positive or a pivot was not.  Errors:
  * GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
@@ -158,7 +159,7 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
  * evaluated at t_j = rho e^{2 pi i j / L}, j = 0..L/2, by a complex FP64 sweep over all
  * 2^M subsets binned by size (principal branch: I - t O_Z is accretive for |t| <= 1), then
  * p_k(n) = rho^-k / L sum_{j < L} G_n(t_j) e^{-2 pi i j k / L} (G_n(t_{L-j}) = conj G_n(t_j)).
- * 4 <= M <= 40; L a power of two in 4..4096 (sectors k >= L alias onto k mod L: choose L
+ * 4 <= M <= 36; L a power of two in 4..4096 (sectors k >= L alias onto k mod L: choose L
  * beyond the photon numbers that matter); 0 < rho <= 1; 0 <= K < L.  even_only != 0 declares
  * that every odd sector vanishes (a lossless state: photons come in pairs, G_n(-t) = G_n(t)),
  * which halves the sweeps; the odd rows of pkn are then zero to rounding.  pkn: (K + 1) x

@@ -35,6 +35,10 @@ constexpr int kThreads = 1 << kL;      // one thread per node after the expansio
 constexpr int kS = 3;                  // prefix levels a CTA loops over inside one unit
 constexpr int kMaxN = 40;              // clicks per pattern on the exact path
 constexpr int kPlanThreads = 1024;
+// whole-device sweeps (all 2^M subsets of one device): 2^36 subsets is about a minute per
+// double-double sweep and a 5 GB table of unit bins; beyond that the table alone outgrows
+// a sensible workspace (88 GB at M = 40)
+constexpr int kMaxDevice = 36;
 
 __host__ __device__ constexpr int sym(int d) { return d * (d + 1) / 2; }
 // packed upper-triangle index of (i, j), i <= j, in a d x d symmetric matrix
@@ -1317,8 +1321,8 @@ int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logde
                        double *kappa) {
     using T = dd;
     using Lay = Layout<T>;
-    if (M < 4 || M > kMaxN)
-        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: M = %d outside 4..%d", M, kMaxN);
+    if (M < 4 || M > kMaxDevice)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: M = %d outside 4..%d", M, kMaxDevice);
     const int split = sweep_split_of(ctx, GBS_DD);
     const long long units = sweep_units_upper_bound(1, M, GBS_DD, split);
     const int nb = M + 1;
@@ -1356,8 +1360,8 @@ int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logd
                         int even, double *pkn) {
     using T = zc;
     using Lay = Layout<T>;
-    if (M < 4 || M > kMaxN)
-        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: M = %d outside 4..%d", M, kMaxN);
+    if (M < 4 || M > kMaxDevice)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: M = %d outside 4..%d", M, kMaxDevice);
     if (L < 4 || L > 4096 || (L & (L - 1)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: L = %d is not a power of two in 4..4096", L);
     if (!(rho > 0.0 && rho <= 1.0))

@@ -68,8 +68,9 @@ def test_independent_modes_closed_form(ctx):
     assert np.abs(got[ok] - np.log(e[ok])).max() < 1e-10
 
 
-def test_rejects_tiny_devices(ctx):
+@pytest.mark.parametrize("M", [3, 37])
+def test_rejects_devices_out_of_range(ctx, M):
     from paper_2106_01445_gb300 import GbsError
-    st = ctx.build_state(g.haar_unitary(3, 1), g.squeezing(3, 2, 0.5, 0.8, 1), 0.9)
+    st = ctx.build_state(g.haar_unitary(M, 1), g.squeezing(M, 2, 0.5, 0.8, 1), 0.9)
     with pytest.raises(GbsError):
         ctx.click_distribution(st["O"], st["logdet"])

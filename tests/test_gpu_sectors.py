@@ -71,7 +71,8 @@ def test_sum_over_clicks_is_photon_distribution(ctx, eta):
         assert np.abs(got[1::2]).max() < ATOL
 
 
-@pytest.mark.parametrize("L,rho,K,M", [(100, 1.0, 10, 8), (64, 1.5, 10, 8), (64, 1.0, 64, 8), (64, 1.0, 10, 3)])
+@pytest.mark.parametrize("L,rho,K,M", [(100, 1.0, 10, 8), (64, 1.5, 10, 8), (64, 1.0, 64, 8), (64, 1.0, 10, 3),
+                                       (64, 1.0, 10, 37)])
 def test_rejects_bad_arguments(ctx, L, rho, K, M):
     from paper_2106_01445_gb300._lib import GbsError
     U, r = g.haar_unitary(M, 1), g.squeezing(M, M // 2, 0.5, 0.5, 1)
