@@ -55,8 +55,11 @@ typedef enum {
                             (~2^-100 per term) at a fraction of its cost.  Needs every pivot
                             determinant of the Schur recursion >= 2^-8 (true when the largest
                             eigenvalue of sigma_Q is below 16); else GBS_E_RANGE */
-    GBS_FF = 4           /* approximation only: float-float (~48-bit) complex minors on the FP32
+    GBS_FF = 4,          /* approximation only: float-float (~48-bit) complex minors on the FP32
                             pipes; FP64-class moments at a fraction of FP64's cost (n <= 79) */
+    GBS_AUTO = 5         /* exact sum: GBS_FX, then GBS_DD for the patterns it reports GBS_E_RANGE
+                            (on the device, no host synchronisation; gbs_reserve covers it);
+                            approximation: GBS_FF */
 } gbs_precision;
 
 /* ---- context ------------------------------------------------------------ */
@@ -111,8 +114,9 @@ int gbs_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, doubl
  *   sector tables of the minors removing <= j detectors at t = e^{i nu} (nu on
  *   L points, L - 1 a bound on the sector index with tail < 1e-14), inverse
  *   DFT, per-sector maximum-entropy fit of moments 0..j, sum of the all-clicked
- *   points.  Order 0 takes GBS_FP64, GBS_FP32_SPLIT, GBS_DD and GBS_FX; order > 0
- *   takes GBS_FF (float-float complex minors, n <= 79), GBS_FP64 (n <= 79) or GBS_FP32_SPLIT (FP32 complex
+ *   points.  Order 0 takes GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX and GBS_AUTO (GBS_FX,
+ *   then GBS_DD for its out-of-range patterns); order > 0 takes GBS_FF (float-float complex
+ *   minors, n <= 79; also GBS_AUTO), GBS_FP64 (n <= 79) or GBS_FP32_SPLIT (FP32 complex
  *   minors, FP64 sums and fits; n <= 112).  For order > 0, kappa returns the
  *   sector bound K, err_bound is NaN, and status GBS_E_FIT marks a pattern where
  *   some sector fit fell back to a lower order (logP is still returned).

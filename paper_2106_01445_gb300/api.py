@@ -11,10 +11,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF, GBS_AUTO
 
 PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, "fx": GBS_FX, "ff": GBS_FF,
-              GBS_FP64: GBS_FP64, GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX, GBS_FF: GBS_FF}
+              "auto": GBS_AUTO, GBS_FP64: GBS_FP64, GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX,
+              GBS_FF: GBS_FF, GBS_AUTO: GBS_AUTO}
 
 
 def _ptr(t) -> ctypes.c_void_p:
@@ -280,13 +281,8 @@ class LogProbClements(torch.autograd.Function):
         Ud = gbs.clements_unitary(theta, phi, M)
         rd = r.detach().to(device=gbs.device, dtype=torch.float64).contiguous()
         st = gbs.build_state(torch.view_as_complex(Ud.view(M, M, 2)), rd, float(eta), check=False)
-        out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="fx")
-        bad = out["status"] == _lib.GBS_E_RANGE
-        if bool(bad.any()):
-            idx = torch.nonzero(bad).flatten()
-            sub = gbs.prob(st["O"], st["logdet"], patterns_tensor(patterns, gbs.device)[idx], order=0,
-                           precision="dd")
-            out["logP"][idx] = sub["logP"]
+        # fixed point, double-double for the patterns outside its range (in the library)
+        out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="auto")
         fctx.save_for_backward(rd, theta.detach(), phi.detach(), Ud, st["O"], st["logdet"])
         fctx.gbs, fctx.eta, fctx.patterns = gbs, float(eta), patterns
         return out["logP"]

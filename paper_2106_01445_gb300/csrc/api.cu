@@ -121,6 +121,7 @@ int gbs_destroy(gbs_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->host_io) cudaFree(ctx->host_io);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->dscratch) cudaFree(ctx->dscratch);
     if (ctx->tev) {
@@ -150,6 +151,19 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
     }
     int st = gbs_ws_ensure(ctx, sweep_workspace_bytes(n_pat, units));
     if (st) return st;
+    // GBS_AUTO's rerun buffers
+    const size_t aux = sweep_auto_bytes(n_pat);
+    if (aux > ctx->aux_bytes) {
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->aux) GBS_CUDA(ctx, cudaFree(ctx->aux));
+        ctx->aux = nullptr;
+        ctx->aux_bytes = 0;
+        if (cudaMalloc(&ctx->aux, aux) != cudaSuccess) {
+            cudaGetLastError();
+            return gbs_fail(ctx, GBS_E_NOMEM, "gbs_reserve: %zu bytes", aux);
+        }
+        ctx->aux_bytes = aux;
+    }
     ctx->reserved = true;
     ctx->cap_pat = n_pat;
     ctx->cap_units = units;
@@ -263,17 +277,19 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
     if (M < 1 || M > 128 || n_pat < 0 || !O || !logdet_sigmaQ || (n_pat && (!patterns || !logP)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: bad arguments (M=%d, n_pat=%d)", M, n_pat);
     if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX &&
-        precision != GBS_FF)
+        precision != GBS_FF && precision != GBS_AUTO)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: unknown precision %d", precision);
     if (order == 0 && precision == GBS_FF)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: float-float serves the approximation (order > 0) only");
     if (n_pat == 0) return GBS_OK;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (order == 0 && precision == GBS_AUTO)
+        return sweep_auto(ctx, M, O, logdet_sigmaQ, patterns, n_pat, logP, kappa, err_bound, status);
     if (order == 0)
         return sweep_exact(ctx, M, O, logdet_sigmaQ, patterns, n_pat, precision, logP, kappa,
                            err_bound, status);
-    return approx_prob(ctx, M, O, logdet_sigmaQ, patterns, n_pat, order, precision, logP, kappa,
-                       err_bound, status);
+    return approx_prob(ctx, M, O, logdet_sigmaQ, patterns, n_pat, order, precision == GBS_AUTO ? GBS_FF : precision,
+                       logP, kappa, err_bound, status);
 }
 
 int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host, double eta,

@@ -24,6 +24,9 @@ struct gbs_ctx {
     // buffers of gbs_run_host (device copies of the host inputs)
     void *host_io = nullptr;
     size_t host_io_bytes = 0;
+    // GBS_AUTO: the double-double rerun's patterns and outputs
+    void *aux = nullptr;
+    size_t aux_bytes = 0;
     // persistent-grid sizes of the sweep kernels (CTAs per SM), by precision
     int sweep_blocks_per_sm[4] = {0, 0, 0, 0};
     // prefix levels looped inside one sweep unit, by precision (-1: the default);
@@ -70,6 +73,9 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
 size_t sweep_workspace_bytes(int n_pat, long long units);
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split);
 int sweep_split_of(const gbs_ctx *ctx, int precision);
+int sweep_auto(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns, int n_pat,
+               double *logP, double *kappa, double *err_bound, int32_t *status);
+size_t sweep_auto_bytes(int n_pat);
 int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
                        double *kappa);
 int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,

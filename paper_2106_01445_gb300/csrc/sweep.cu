@@ -1271,7 +1271,71 @@ __global__ void sector_dft_kernel(int M, int L, double rho, int K, const double 
     pkn[f] = *bad ? nan("") : s / (double)L * pow(rho, -(double)k);
 }
 
+// GBS_AUTO: the patterns the fixed-point pass flagged out of range, the others replaced by a
+// pattern no plan accepts (every bit set: a detector >= M, or more than kMaxN clicks)
+__global__ void auto_mark_kernel(int n_pat, const int32_t *__restrict__ st, const uint64_t *__restrict__ pats,
+                                 uint64_t *__restrict__ redo) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pat) return;
+    const bool again = st[p] == GBS_E_RANGE;
+    redo[2 * p] = again ? pats[2 * p] : ~0ull;
+    redo[2 * p + 1] = again ? pats[2 * p + 1] : ~0ull;
+}
+// ... and the double-double results in their places
+__global__ void auto_merge_kernel(int n_pat, const int32_t *__restrict__ st, const double *__restrict__ lp2,
+                                  const double *__restrict__ ka2, const double *__restrict__ er2,
+                                  const int32_t *__restrict__ st2, double *__restrict__ logP, double *__restrict__ kappa,
+                                  double *__restrict__ err_bound, int32_t *__restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pat || st[p] != GBS_E_RANGE) return;
+    logP[p] = lp2[p];
+    if (kappa) kappa[p] = ka2[p];
+    if (err_bound) err_bound[p] = er2[p];
+    if (status) status[p] = st2[p];
+}
+
 }  // namespace
+
+size_t sweep_auto_bytes(int n_pat) {
+    const size_t n = (size_t)n_pat;
+    return align256(16 * n) + 3 * align256(8 * n) + 2 * align256(4 * n);
+}
+
+int sweep_auto(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns, int n_pat,
+               double *logP, double *kappa, double *err_bound, int32_t *status) {
+    const size_t need = sweep_auto_bytes(n_pat);
+    if (need > ctx->aux_bytes) {
+        if (ctx->reserved)
+            return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: %d patterns exceed the reservation of %d", n_pat,
+                            ctx->cap_pat);
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->aux) GBS_CUDA(ctx, cudaFree(ctx->aux));
+        ctx->aux = nullptr;
+        ctx->aux_bytes = 0;
+        if (cudaMalloc(&ctx->aux, need) != cudaSuccess) {
+            cudaGetLastError();
+            return gbs_fail(ctx, GBS_E_NOMEM, "gbs_prob: %zu bytes for the automatic precision", need);
+        }
+        ctx->aux_bytes = need;
+    }
+    const size_t n = (size_t)n_pat;
+    char *b = (char *)ctx->aux;
+    uint64_t *redo = (uint64_t *)b;
+    double *lp2 = (double *)(b + align256(16 * n));
+    double *ka2 = lp2 + align256(8 * n) / 8, *er2 = ka2 + align256(8 * n) / 8;
+    int32_t *st2 = (int32_t *)(er2 + align256(8 * n) / 8);
+    int32_t *st1 = status ? status : st2 + align256(4 * n) / 4;
+    int r = sweep_exact(ctx, M, O, logdet, patterns, n_pat, GBS_FX, logP, kappa, err_bound, st1);
+    if (r) return r;
+    const unsigned g = (unsigned)((n_pat + 255) / 256);
+    auto_mark_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, patterns, redo);
+    GBS_CUDA(ctx, cudaGetLastError());
+    r = sweep_exact(ctx, M, O, logdet, redo, n_pat, GBS_DD, lp2, ka2, er2, st2);
+    if (r) return r;
+    auto_merge_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, lp2, ka2, er2, st2, logP, kappa, err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
 
 int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O,
                    const double *logdet, const uint64_t *patterns, int n_pat, int precision,

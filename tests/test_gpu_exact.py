@@ -260,6 +260,28 @@ def test_fixed_point_range_flagged(ctx):
     assert np.abs(dd["logP"] - ref["logP"]).max() <= TOL64
 
 
+def test_auto_precision_reruns_out_of_range_patterns(ctx):
+    """GBS_AUTO: the fixed-point pass, then double-double for the patterns it flagged out of
+    range, on the device: every pattern ok; the in-range ones carry the fixed-point result bit
+    for bit, the others the double-double one."""
+    M = 6
+    U = np.eye(M, dtype=complex)
+    r = np.array([4.0, 4.0, 0.5, 0.6, 0.7, 0.8])
+    mode_sets = [[2, 3], [2, 3, 4, 5], [4], [0], [1, 2], [0, 1, 4], [3, 5], [0, 2, 3, 4, 5]]
+    pats = np.stack([g.modes_to_pattern(m) for m in mode_sets])
+    st = gpu_state(ctx, U, r, 1.0)
+    auto = gpu_prob(ctx, st, pats, "auto")
+    fx = gpu_prob(ctx, st, pats, "fx")
+    dd = gpu_prob(ctx, st, pats, "dd")
+    ref = oracle_dd(U, r, 1.0, pats)
+    assert (auto["status"] == 0).all(), auto["status"]
+    flagged = fx["status"] == 8
+    assert flagged.any() and (~flagged).any()
+    assert np.array_equal(auto["logP"][~flagged], fx["logP"][~flagged])
+    assert np.array_equal(auto["logP"][flagged], dd["logP"][flagged])
+    assert np.abs(auto["logP"] - ref["logP"]).max() <= TOL64
+
+
 def test_invalid_patterns_flagged(ctx):
     M = 10
     st = gpu_state(ctx, g.haar_unitary(M, 3), g.squeezing(M, 5, 0.5, 1.0, 3), 0.7)

@@ -18,7 +18,7 @@ def setup(cuda_ok):
     return Context, patterns_tensor, _complex_interleaved
 
 
-@pytest.mark.parametrize("precision", ["fx", "fp64"])
+@pytest.mark.parametrize("precision", ["fx", "fp64", "auto"])
 def test_cuda_graph_capture_and_replay(setup, precision):
     Context, patterns_tensor, _complex_interleaved = setup
     dev = torch.device("cuda", 0)
