@@ -13,7 +13,7 @@ Metric: subset log-dets per second (whole job), plus patterns per second.
 
     python bench.py [--gpus N --steps K --warmup W --precision fx|dd|fp64|fp32]
     python bench.py --impl reference     # the FP64 CPU oracle on the host cores
-    python bench.py --profile sweep|approx --precision ...   # one call, for ncu
+    python bench.py --profile sweep|approx|grad --precision ...   # one call, for ncu
 """
 from __future__ import annotations
 
@@ -642,6 +642,17 @@ def run_profile_case(args):
     from paper_2106_01445_gb300 import build as b
     b.build()
     from paper_2106_01445_gb300.api import Context
+    if args.profile == "grad":
+        c = g.CONFIGS["m32_grad"]
+        ctx = Context(0)
+        st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
+        pats = c.patterns()
+        w = torch.ones(len(pats), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            dsq, lp, stt = ctx.grad(st["O"], st["logdet"], pats, w)
+        torch.cuda.synchronize()
+        print("profile case grad: %d patterns, %d ok" % (len(pats), int((stt == 0).sum().item())))
+        return 0
     c = g.CONFIGS[args.workload if args.profile == "sweep" else "m50_approx"]
     ctx = Context(0)
     st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
@@ -667,7 +678,7 @@ def main():
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["sweep", "approx"], default=None,
+    ap.add_argument("--profile", choices=["sweep", "approx", "grad"], default=None,
                     help="run one kernel path twice (for ncu) instead of the benchmark")
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--workloads", choices=["all", "none"], default="all",
