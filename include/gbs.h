@@ -144,10 +144,11 @@ int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host
  * clicks contains a subset Z in C(M - |Z|, n - |Z|) ways, so
  *   p(n) = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n - z} C(M - z, n - z) E_z,
  *   E_z  = sum over the subsets Z of the M modes with |Z| = z of det(A_Z)^{-1/2}:
- * one double-double sweep over all 2^M subsets with the terms binned by size, then the
+ * one fixed-point sweep over all 2^M subsets with the terms binned by size (double-double
+ * instead when a pivot leaves the fixed-point range: one readback decides), then the
  * binomial transform in double-double with exact binomials.  4 <= M <= 36 (2^M subsets:
- * about a second at M = 30, a minute at 36; the workspace holds 16 (M + 1) bytes per unit of
- * 2^13 subsets, 5 GB at M = 36).  logp, kappa: M + 1 doubles (device; kappa may be NULL),
+ * 0.42 s at M = 30; the workspace holds 16 (M + 1) bytes per unit of 2^12..2^13 subsets,
+ * 5..10 GB at M = 36).  Synchronises the stream once.  logp, kappa: M + 1 doubles (device; kappa may be NULL),
  * kappa[n] = sum_z C(M - z, n - z) E_z / |sum with signs|, the transform's cancellation;
  * logp[n] = NaN where the sum is not positive or a pivot was not.  Errors:
  * GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */

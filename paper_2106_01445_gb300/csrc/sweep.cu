@@ -514,6 +514,16 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
 template <typename T> struct BinOf { using type = dd; };
 template <> struct BinOf<zc> { using type = zc; };
 __device__ __forceinline__ void store2(double *o, dd v) { o[0] = v.hi; o[1] = v.lo; }
+// a thread's bin of the binned mode times its prefactor and the sub-unit factor, in the bin type
+template <typename T, typename N, typename Tau> __device__ __forceinline__ typename BinOf<T>::type
+scale_bin(const N &tn, const Tau &tsub, T v) {
+    return (Tau(tn) * tsub) * v;
+}
+template <> __device__ __forceinline__ dd scale_bin<fx, fxe, dd>(const fxe &tn, const dd &tsub, fx v) {
+    return (fxe_to_dd(tn) * tsub) * fx_to_dd(v);
+}
+__device__ __forceinline__ bool node_nan(const fxe &) { return false; }
+template <typename N> __device__ __forceinline__ bool node_nan(const N &x) { return is_nan(x); }
 __device__ __forceinline__ void store2(double *o, zc v) { o[0] = v.re; o[1] = v.im; }
 
 // ---- the sweep ------------------------------------------------------------------
@@ -775,10 +785,12 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 // the thread's subtree bins (relative sizes 0..B), scaled by its prefactor,
                 // then every size bin summed over the threads in a fixed order
                 constexpr int NB = B + 1;
+                using BT = typename BinOf<T>::type;
                 BinAcc<T, NB> acc;
 #pragma unroll
                 for (int b = 0; b < NB; ++b) acc.v[b] = konst<T>(0.0);
                 acc.bad = 0;
+                BT sb[NB];
                 const bool has = t < (1 << L_eff);
                 if (has) {
                     const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
@@ -786,20 +798,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int nreal = n - (n_eff - B);
                     SmemMat<T, B> A{node};
                     dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc, 0);
-                    const Tau sc = Tau(tn) * tsub;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) acc.v[b] = sc * acc.v[b];
-                    if (is_nan(tn)) atomicOr(&s_flag, 1);
+                    for (int b = 0; b < NB; ++b) sb[b] = scale_bin(tn, tsub, acc.v[b]);
+                    if (node_nan(tn)) atomicOr(&s_flag, 1);
+                    if (acc.bad) atomicOr(&s_flag, acc.bad);
                 }
                 __syncthreads();  // the nodes are read: X is scratch until the next sub-unit
-                T *tb = X;
+                BT *tb = (BT *)X;
                 if (has)
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) tb[t * NB + b] = acc.v[b];
+                    for (int b = 0; b < NB; ++b) tb[t * NB + b] = sb[b];
                 s_base[t] = has ? k + kk + __popc(t) : -(1 << 20);
                 __syncthreads();
                 for (int z = t; z <= n; z += kThreads) {
-                    T sz = konst<T>(0.0);
+                    BT sz = BT(0.0);
                     for (int t2 = 0; t2 < (1 << L_eff); ++t2) {
                         const int b = z - s_base[t2];
                         if (b >= 0 && b < NB) sz += tb[t2 * NB + b];
@@ -1381,14 +1393,18 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
 }
 
-int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
-                       double *kappa) {
-    using T = dd;
+namespace {
+constexpr int kRetryInDD = -1;
+
+// the binned sweep in T: fixed point first (flagged out of range -> kRetryInDD, read back:
+// the whole device's distribution is one result), double-double otherwise
+template <typename T>
+int click_distribution_in(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
+                          double *kappa) {
     using Lay = Layout<T>;
-    if (M < 4 || M > kMaxDevice)
-        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: M = %d outside 4..%d", M, kMaxDevice);
-    const int split = sweep_split_of(ctx, GBS_DD);
-    const long long units = sweep_units_upper_bound(1, M, GBS_DD, split);
+    const int pi = Prec<T>::idx;
+    const int split = sweep_split_of(ctx, pi);
+    const long long units = sweep_units_upper_bound(1, M, pi, split);
     const int nb = M + 1;
     const long long nch = (units + 1023) / 1024;
     const WsOffsets o = ws_offsets(1, 0);
@@ -1414,10 +1430,24 @@ int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logde
     GBS_CUDA(ctx, cudaGetLastError());
     st = gbs_timing_end(ctx);
     if (st) return st;
+    if (Prec<T>::fixed) {
+        GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.pflags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (*(int *)ctx->pinned) return kRetryInDD;
+    }
     bins_chunk_kernel<<<(unsigned)nch, 64, 0, ctx->stream>>>(nb, pl.partials, pl.unit_off + 1, chunks);
     bins_final_kernel<<<1, 64, 0, ctx->stream>>>(M, nch, chunks, logdet, pl.pflags, pl.overflow, logp, kappa);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
+}
+}  // namespace
+
+int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
+                       double *kappa) {
+    if (M < 4 || M > kMaxDevice)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_click_distribution: M = %d outside 4..%d", M, kMaxDevice);
+    const int r = click_distribution_in<fx>(ctx, M, O, logdet, logp, kappa);
+    return r == kRetryInDD ? click_distribution_in<dd>(ctx, M, O, logdet, logp, kappa) : r;
 }
 
 int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,

@@ -68,6 +68,23 @@ def test_independent_modes_closed_form(ctx):
     assert np.abs(got[ok] - np.log(e[ok])).max() < 1e-10
 
 
+def test_strong_squeezing_falls_back_to_double_double(ctx):
+    """Squeezing beyond the fixed-point range (r = 4: pivot determinants below 2^-8) is
+    flagged by the fixed-point pass and the distribution is taken in double-double; the
+    closed form of independent modes checks it."""
+    M, eta = 8, 1.0
+    r = np.array([4.0, 3.5, 0.5, 0.6, 0.7, 0.8, 0.0, 0.0])
+    q = 1.0 - (1.0 + eta * (2.0 - eta) * np.sinh(r) ** 2) ** -0.5
+    e = np.zeros(M + 1)
+    e[0] = 1.0
+    for qi in q:
+        e[1:] = e[1:] * (1.0 - qi) + e[:-1] * qi
+        e[0] *= 1.0 - qi
+    got, _ = gpu_pn(ctx, np.eye(M, dtype=complex), r, eta)
+    ok = e > 1e-250
+    assert np.abs(got[ok] - np.log(e[ok])).max() < 1e-10
+
+
 @pytest.mark.parametrize("M", [3, 37])
 def test_rejects_devices_out_of_range(ctx, M):
     from paper_2106_01445_gb300 import GbsError
