@@ -365,6 +365,13 @@ def run_gpu(args):
                         "loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
     line["other_precisions"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
                                 for k, v in others.items()}
+    # each precision's sweep against its own pipe: FP32 (derived peak), FP64 (measured FMA
+    # loop), double-double and fixed point (measured update-entry loops)
+    all_peaks = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["dd"], "fx": meas["fx"]}
+    for k, v in line["other_precisions"].items():
+        ach = flops / (v["kernel_ms"] * 1e-3)
+        v["roofline"] = {"achieved_tflops": ach / 1e12, "peak_tflops": all_peaks[k] / 1e12,
+                         "frac": ach / all_peaks[k]}
     line["clocks"] = ck
     # oracle on the host cores: baseline (FP64 oracle as it stands) and the stated
     # error of every precision against the double-double oracle on a sample
