@@ -584,11 +584,11 @@ def run_workloads(dev, stream, meas, fp32_peak):
         a = host(ctx.prob(st["O"], st["logdet"], allp, order=order, precision="ff"))
         entry["all_click"]["order%d_rel_dev" % order] = float(np.expm1(a["logP"][0] - ex["logP"][0]))
     # the photon-number sectors p_k(n) of the same device (lossless: even sectors only),
-    # 256 circle points (65 complex sweeps of 2^30 subsets)
+    # 256 circle points (65 complex float-float sweeps of 2^30 subsets; FP64 takes twice as long)
     ms, kms, pkn = timed(lambda: ctx.sector_distribution(st["O"], st["logdet"], L=256, rho=1.0, K=255,
-                                                         even_only=True))
+                                                         even_only=True, precision="ff"))
     pkn = pkn.cpu().numpy()
-    entry["sectors"] = {"L": 256, "sweeps": 65, "ms": ms, "sweep_kernel_ms_per_sweep": kms,
+    entry["sectors"] = {"L": 256, "sweeps": 65, "precision": "ff", "ms": ms, "sweep_kernel_ms_per_sweep": kms,
                         "subsets_per_s": 2.0 ** c.M / (kms * 1e-3),
                         "max_abs_sum_k_minus_p_n": float(np.abs(pkn.sum(axis=0) - pn).max()),
                         "max_abs_odd_sector": float(np.abs(pkn[1::2]).max()),

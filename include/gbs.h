@@ -161,8 +161,9 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
  * generating function of a set Z of modes, det(I - t O_Z)^{-1/2} (t marks each photon),
  *   G_n(t) = sum_k p_k(n) t^k = det(sigma_Q)^{-1/2} sum_{z <= n} (-1)^{n-z} C(M-z, n-z) E_z(t),
  *   E_z(t) = sum over the subsets Z with |Z| = z of det(I - t O_Z)^{-1/2},
- * evaluated at t_j = rho e^{2 pi i j / L}, j = 0..L/2, by a complex FP64 sweep over all
- * 2^M subsets binned by size (principal branch: I - t O_Z is accretive for |t| <= 1), then
+ * evaluated at t_j = rho e^{2 pi i j / L}, j = 0..L/2, by a complex sweep over all 2^M
+ * subsets binned by size (principal branch: I - t O_Z is accretive for |t| <= 1) in FP64
+ * (precision GBS_FP64) or float-float (GBS_FF: ~48-bit parts on the FP32 pipes), then
  * p_k(n) = rho^-k / L sum_{j < L} G_n(t_j) e^{-2 pi i j k / L} (G_n(t_{L-j}) = conj G_n(t_j)).
  * 4 <= M <= 36; L a power of two in 4..4096 (sectors k >= L alias onto k mod L: choose L
  * beyond the photon numbers that matter); 0 < rho <= 1; 0 <= K < L.  even_only != 0 declares
@@ -170,12 +171,12 @@ int gbs_click_distribution(gbs_ctx *ctx, int M, const double *O, const double *l
  * which halves the sweeps; the odd rows of pkn are then zero to rounding.  pkn: (K + 1) x
  * (M + 1) doubles (device), row k = p_k(0..M).  Cost: L/2 + 1 sweeps of 2^M subsets (L/4 + 1
  * with even_only).  Accuracy:
- * the subset terms are FP64, so each G_n(t_j) carries an absolute error of about 1e-16
- * times the transform's cancellation (kappa of gbs_click_distribution) times p(n)
+ * with FP64 subset terms each G_n(t_j) carries an absolute error of about 1e-16 (float-float:
+ * ~1e-14) times the transform's cancellation (kappa of gbs_click_distribution) times p(n)
  * (|G_n(t)| <= p(n) for |t| <= 1), and p_k(n) that error times rho^-k.  NaN everywhere if
  * a pivot was zero.  Errors: GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
 int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
-                            int K, int even_only, double *pkn);
+                            int K, int even_only, int precision, double *pkn);
 
 /* The approximation's fitted sector curves for one pattern S with n clicks (Results,
  * "Approximation scheme": p_k ~ exp(-f_j), and the paper's Fig. 3a): the same steps as

@@ -29,7 +29,7 @@ SIGNATURES = {
     "gbs_version": (_i, []),
     "gbs_reserve": (_i, [_vp, _i, _i]),
     "gbs_click_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
-    "gbs_sector_distribution": (_i, [_vp, _i, _vp, _vp, _i, _d, _i, _i, _vp]),
+    "gbs_sector_distribution": (_i, [_vp, _i, _vp, _vp, _i, _d, _i, _i, _i, _vp]),
     "gbs_approx_sector_curves": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]),
     "gbs_autotune": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "gbs_build_state": (_i, [_vp, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),

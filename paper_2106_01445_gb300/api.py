@@ -90,7 +90,7 @@ class Context:
         return logp, kappa
 
     def sector_distribution(self, O: torch.Tensor, logdet: torch.Tensor, L: int = 256, rho: float = 1.0,
-                            K: int | None = None, even_only: bool = False):
+                            K: int | None = None, even_only: bool = False, precision="fp64"):
         """p_k(n) for k = 0..K, n = 0..M ((K + 1) x (M + 1), device): the photon-number
         sectors of the whole device's click-number distribution, from L circle points
         (even_only: the state is lossless, odd sectors vanish; half the sweeps)."""
@@ -98,7 +98,7 @@ class Context:
         K = L - 1 if K is None else K
         pkn = torch.empty((K + 1, M + 1), dtype=torch.float64, device=self.device)
         self._check(self.lib.gbs_sector_distribution(self.h, M, _ptr(O), _ptr(logdet), int(L), float(rho), int(K),
-                                                     int(bool(even_only)), _ptr(pkn)))
+                                                     int(bool(even_only)), PRECISIONS[precision], _ptr(pkn)))
         return pkn
 
     def approx_sector_curves(self, O: torch.Tensor, logdet: torch.Tensor, pattern, order: int = 4,

@@ -191,11 +191,11 @@ int gbs_approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double 
 }
 
 int gbs_sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ, int L, double rho,
-                            int K, int even_only, double *pkn) {
+                            int K, int even_only, int precision, double *pkn) {
     if (!ctx) return GBS_E_INVALID;
     if (!O || !logdet_sigmaQ || !pkn) return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: null pointer");
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
-    return sector_distribution(ctx, M, O, logdet_sigmaQ, L, rho, K, even_only, pkn);
+    return sector_distribution(ctx, M, O, logdet_sigmaQ, L, rho, K, even_only, precision, pkn);
 }
 
 int gbs_autotune(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,

@@ -79,7 +79,7 @@ size_t sweep_auto_bytes(int n_pat);
 int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, double *logp,
                        double *kappa);
 int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
-                        int even, double *pkn);
+                        int even, int precision, double *pkn);
 int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns,
                 int n_pat, int order, int precision, double *logP, double *kappa, double *err_bound,
                 int32_t *status);

@@ -102,8 +102,18 @@ template <> struct Prec<zc> {
     static constexpr int wrow = 2;
 };
 
+template <> struct Prec<zf> {
+    static constexpr int B = 3;
+    using Tau = zf;
+    using Abs = double;
+    using Node = zf;
+    static constexpr bool fixed = false;
+    static constexpr int wrow = 2;
+};
+
 template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ zc rsq<zc>(zc x) { return zc_rsqrt(x); }
+template <> __device__ __forceinline__ zf rsq<zf>(zf x) { return zf_rsqrt(x); }
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
@@ -116,6 +126,7 @@ __device__ __forceinline__ double tau_of(double, double rs) { return rs; }
 __device__ __forceinline__ dd tau_of(dd, dd rs) { return rs; }
 __device__ __forceinline__ dd tau_of(fx, fx rs) { return fx_to_dd(rs); }
 __device__ __forceinline__ zc tau_of(zc, zc rs) { return rs; }
+__device__ __forceinline__ zf tau_of(zf, zf rs) { return rs; }
 
 // constants and conversions of the working type
 template <typename T> __device__ __forceinline__ T konst(double v) { return T(v); }
@@ -124,6 +135,7 @@ __device__ __forceinline__ float to_node(float x) { return x; }
 __device__ __forceinline__ double to_node(double x) { return x; }
 __device__ __forceinline__ dd to_node(dd x) { return x; }
 __device__ __forceinline__ zc to_node(zc x) { return x; }
+__device__ __forceinline__ zf to_node(zf x) { return x; }
 // a child's prefactor: the parent's times det^{-1/2} of the parent's pivot
 template <typename N, typename T> __device__ __forceinline__ N node_times(const N &p, const T &rs) { return p * to_node(rs); }
 template <> __device__ __forceinline__ fxe node_times<fxe, fx>(const fxe &p, const fx &rs) { return fxe_mul(p, rs); }
@@ -138,6 +150,9 @@ template <> __device__ __forceinline__ int pivot_bad<fx>(fx det) { return fx_piv
 // complex pivots: their determinants may have any argument in (-pi, pi); only zero or NaN is bad
 template <> __device__ __forceinline__ int pivot_bad<zc>(zc det) {
     return fabs(det.re) + fabs(det.im) > 0.0 ? 0 : 1;
+}
+template <> __device__ __forceinline__ int pivot_bad<zf>(zf det) {
+    return fabsf(det.re.hi) + fabsf(det.im.hi) > 0.0f ? 0 : 1;
 }
 
 // the Schur-update kernels: a0 b0 + a1 b1, c - a0 b0 - a1 b1, det of a 2x2 block
@@ -162,6 +177,9 @@ template <typename T> __device__ __forceinline__ T a_entry_t(double delta, doubl
 template <> __device__ __forceinline__ zc a_entry_t<zc>(double delta, double o, double t_re, double t_im) {
     return zc(delta - t_re * o, -t_im * o);
 }
+template <> __device__ __forceinline__ zf a_entry_t<zf>(double delta, double o, double t_re, double t_im) {
+    return zf(ff(delta - t_re * o), ff(-t_im * o));
+}
 
 __device__ __forceinline__ double to_hi(float x) { return x; }
 __device__ __forceinline__ double to_hi(double x) { return x; }
@@ -174,6 +192,7 @@ __device__ __forceinline__ bool is_nan(float x) { return x != x; }
 __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 __device__ __forceinline__ bool is_nan(zc x) { return zc_nan(x); }
+__device__ __forceinline__ bool is_nan(zf x) { return zf_nan(x); }
 // a thread's subtree sum as (hi, lo) doubles
 __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
@@ -513,6 +532,7 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
 // complex ones
 template <typename T> struct BinOf { using type = dd; };
 template <> struct BinOf<zc> { using type = zc; };
+template <> struct BinOf<zf> { using type = zf; };
 __device__ __forceinline__ void store2(double *o, dd v) { o[0] = v.hi; o[1] = v.lo; }
 // a thread's bin of the binned mode times its prefactor and the sub-unit factor, in the bin type
 template <typename T, typename N, typename Tau> __device__ __forceinline__ typename BinOf<T>::type
@@ -525,6 +545,7 @@ template <> __device__ __forceinline__ dd scale_bin<fx, fxe, dd>(const fxe &tn, 
 __device__ __forceinline__ bool node_nan(const fxe &) { return false; }
 template <typename N> __device__ __forceinline__ bool node_nan(const N &x) { return is_nan(x); }
 __device__ __forceinline__ void store2(double *o, zc v) { o[0] = v.re; o[1] = v.im; }
+__device__ __forceinline__ void store2(double *o, zf v) { o[0] = ff_to_double(v.re); o[1] = ff_to_double(v.im); }
 
 // ---- the sweep ------------------------------------------------------------------
 // BIN: the click-number distribution mode (one pattern = all M modes): the subset
@@ -1450,9 +1471,10 @@ int click_distribution(gbs_ctx *ctx, int M, const double *O, const double *logde
     return r == kRetryInDD ? click_distribution_in<dd>(ctx, M, O, logdet, logp, kappa) : r;
 }
 
-int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
-                        int even, double *pkn) {
-    using T = zc;
+namespace {
+template <typename T>
+int sector_distribution_in(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
+                           int even, double *pkn) {
     using Lay = Layout<T>;
     if (M < 4 || M > kMaxDevice)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: M = %d outside 4..%d", M, kMaxDevice);
@@ -1513,4 +1535,12 @@ int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logd
     sector_dft_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(M, L, rho, K, G, bad, pkn);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
+}
+}  // namespace
+
+int sector_distribution(gbs_ctx *ctx, int M, const double *O, const double *logdet, int L, double rho, int K,
+                        int even, int precision, double *pkn) {
+    if (precision == GBS_FF) return sector_distribution_in<zf>(ctx, M, O, logdet, L, rho, K, even, pkn);
+    if (precision == GBS_FP64) return sector_distribution_in<zc>(ctx, M, O, logdet, L, rho, K, even, pkn);
+    return gbs_fail(ctx, GBS_E_INVALID, "gbs_sector_distribution: precision %d (GBS_FP64 or GBS_FF)", precision);
 }

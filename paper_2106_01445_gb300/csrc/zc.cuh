@@ -35,3 +35,47 @@ __device__ __forceinline__ zc zc_rsqrt(zc z) {
     const double q = 1.0 / (sr * sr + si * si);
     return zc(sr * q, -si * q);
 }
+
+// Complex float-float (~48-bit parts on the FP32 pipes): the same sweep at a fraction of
+// complex FP64's cost where its precision suffices.
+#include "ff.cuh"
+
+struct zf {
+    ff re, im;
+    zf() = default;
+    __host__ __device__ zf(double r) : re(r), im(0.0f, 0.0f) {}
+    __host__ __device__ zf(ff r, ff i) : re(r), im(i) {}
+};
+
+__device__ __forceinline__ zf operator+(zf a, zf b) { return zf(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ zf operator-(zf a, zf b) { return zf(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ zf operator-(zf a) { return zf(-a.re, -a.im); }
+__device__ __forceinline__ zf operator*(zf a, zf b) {
+    return zf(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ zf &operator+=(zf &a, zf b) { return a = a + b; }
+__device__ __forceinline__ bool zf_nan(zf a) { return a.re.hi != a.re.hi || a.im.hi != a.im.hi; }
+
+// principal 1/sqrt(z), z != 0, as zc_rsqrt: |z| and the half-angle root from two reciprocal
+// square roots, 1/sqrt(z) = conj(sqrt z) / |z|
+__device__ __forceinline__ zf zf_rsqrt(zf z) {
+    const ff n2 = z.re * z.re + z.im * z.im;
+    const ff ra = ff_rsqrt(n2);  // 1 / |z|
+    const ff a = n2 * ra;        // |z|
+    const ff half(0.5f, 0.0f);
+    ff sr, si;
+    if (z.re.hi >= 0.0f) {
+        const ff h = (a + z.re) * half;
+        const ff rh = ff_rsqrt(h);
+        sr = h * rh;
+        si = z.im * rh * half;
+    } else {
+        const ff h = (a - z.re) * half;
+        const ff rh = ff_rsqrt(h);
+        const ff s = h * rh;
+        const ff ay = z.im.hi < 0.0f ? -z.im : z.im;
+        sr = ay * rh * half;
+        si = z.im.hi < 0.0f ? -s : s;
+    }
+    return zf(sr * ra, -(si * ra));
+}
