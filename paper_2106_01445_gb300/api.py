@@ -143,8 +143,10 @@ class Context:
         return dict(O=O, logdet=logdet, sigma=sigma, status=status)
 
     def prob(self, O: torch.Tensor, logdet: torch.Tensor, patterns, order: int = 0,
-             precision="fp64", out=None):
-        """log P per pattern (device tensors): dict(logP, kappa, err_bound, status)."""
+             precision="auto", out=None):
+        """log P per pattern (device tensors): dict(logP, kappa, err_bound, status).
+        precision "auto": the exact sum in 128-bit fixed point with a double-double rerun of
+        the patterns outside its range; the approximation with float-float minors."""
         M = O.shape[0] // 2
         pats = patterns_tensor(patterns, self.device)
         n_pat = pats.shape[0]
@@ -175,7 +177,7 @@ class Context:
                                               _ptr(out["err_bound"]), _ptr(out["status"])))
         return out
 
-    def run_host(self, U, r, eta: float, patterns, order: int = 0, precision="fp64", out=None):
+    def run_host(self, U, r, eta: float, patterns, order: int = 0, precision="auto", out=None):
         """The whole path from host (numpy) buffers; returns numpy arrays."""
         U = np.ascontiguousarray(U, dtype=np.complex128)
         M = U.shape[0]
