@@ -204,15 +204,13 @@ def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter:
     return a, bool(np.max(np.abs(m - X.T @ q)) <= 1e3 * tol)
 
 
-def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int):
-    """Estimate of q_k(v = 0) from the factorial moments D_0..D_j of sector k.
-
-    Returns (value, flag) with flag 0 = fitted at order j' = min(j, |V|-1),
-    1 = fell back to a lower order, 2 = no fit possible (value 0)."""
+def sector_fit(Dk: np.ndarray, n: int, k: int, j: int):
+    """The fit behind sector_last_point: (value, flag, a, J) with a the coefficients of
+    the normalised fit exp(-sum_i a_i x^i), x = v / n, of degree J (None when no fit)."""
     if k < n or Dk[0] <= 0.0:
-        return 0.0, 0
+        return 0.0, 0, None, -1
     if n == 0:
-        return Dk[0], 0
+        return Dk[0], 0, None, -1
     v = np.arange(max(0, n - k), n, dtype=np.float64)          # v = n is empty for k >= 1
     Jmax = min(j, v.size - 1)
     mu = raw_moments(Dk, Jmax)
@@ -221,16 +219,28 @@ def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int):
         mnorm = np.array([mu[i] / n ** i for i in range(J + 1)]) / mu[0]
         a, ok = maxent_fit(x, mnorm)
         if ok:
-            return mu[0] * math.exp(-a[0]), 0 if J == Jmax else 1
-    return 0.0, 2
+            return mu[0] * math.exp(-a[0]), 0 if J == Jmax else 1, a, J
+    return 0.0, 2, None, -1
+
+
+def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int):
+    """Estimate of q_k(v = 0) from the factorial moments D_0..D_j of sector k.
+
+    Returns (value, flag) with flag 0 = fitted at order j' = min(j, |V|-1),
+    1 = fell back to a lower order, 2 = no fit possible (value 0)."""
+    val, flag, _, _ = sector_fit(Dk, n, k, j)
+    return val, flag
 
 
 def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
-                   K: int | None = None, eps_sector: float = EPS_SECTOR):
-    """log P(S) by the order-j approximation.  Returns (logP, info dict)."""
+                   K: int | None = None, eps_sector: float = EPS_SECTOR, rho: float | None = None):
+    """log P(S) by the order-j approximation.  Returns (logP, info dict).  K and rho
+    default to choose_kmax and choose_tilt; fixing them makes log P a smooth function
+    of O (for derivatives by differences)."""
     modes = list(modes)
     n = len(modes)
-    rho = choose_tilt(O, M, modes)
+    if rho is None:
+        rho = choose_tilt(O, M, modes)
     if K is None:
         K = choose_kmax(O, M, modes, rho)
     D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
@@ -327,3 +337,83 @@ def approx_sector_curves(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: 
         q, _ = sector_curve(D[:, k], n, k, j)
         out[k] = q[::-1] * math.exp(-0.5 * logdet_sigmaQ - k * math.log(rho))
     return out
+
+
+# ---- gradient of the approximation (not in the paper) -----------------------------
+# log P = -1/2 log det sigma_Q + log sum_k part_k rho^-k, part_k the fitted last point of
+# sector k.  Reverse mode, step by step:
+#  * the sum:   d/d part_k = rho^-k / sum_k' part_k' rho^-k';
+#  * the fit:   the unnormalised fit F(x) = exp(-sum_i b_i x^i) matches the moments
+#               mu'_i = mu_i / n^i on its support, so by implicit differentiation of
+#               sum_s x_s^i F(x_s) = mu'_i,  d F(0) = F(0) (H^-1 d mu')_0 with
+#               H_il = sum_s x_s^(i+l) F(x_s); with the normalised fit of coefficients a
+#               (F = mu_0 exp(-sum a_i x^i)) that is  d part / d mu'_i = e^-a_0 (Hn^-1)_0i;
+#  * moments:   mu'_i = sum_{w <= i} S(i, w) w! D_w / n^i;
+#  * sectors:   D_w^(k) = sum_{|W| = w} c_k[rho O_{S \ W}], and for a real symmetric X
+#               d c_k[X] / dX = 1/2 sum_{m < k} c_{k-1-m} X^m  (the t^k coefficient of
+#               d det(I - t X)^-1/2 / dX = 1/2 t Z(t) (I - t X)^-1), evaluated on the
+#               eigenvectors of X;
+#  * O = I - A:  d / dA_S = -d / dO_S.
+
+def fit_last_point_adjoint(n: int, a: np.ndarray, J: int, jmax: int) -> np.ndarray:
+    """d part / d D_w, w = 0..jmax, of a sector fitted on v = 0..n-1 at degree J."""
+    x = np.arange(n, dtype=np.float64) / n
+    X = np.vander(x, J + 1, increasing=True)
+    q = np.exp(-X @ a)
+    Hn = (X * q[:, None]).T @ X
+    e0 = np.zeros(J + 1)
+    e0[0] = 1.0
+    y = np.linalg.solve(Hn, e0)                    # row 0 of Hn^-1 (Hn symmetric)
+    beta = np.zeros(jmax + 1)
+    for w in range(J + 1):
+        beta[w] = math.exp(-a[0]) * sum(y[i] * stirling2(i, w) * math.factorial(w) / n ** i
+                                        for i in range(w, J + 1))
+    return beta
+
+
+def series_coeffs_adjoint(X: np.ndarray, gam: np.ndarray) -> np.ndarray:
+    """sum_k gam_k d c_k[X] / dX for X real symmetric, k = 0..len(gam)-1."""
+    K = gam.size - 1
+    lam, Q = np.linalg.eigh(X)
+    c = series_coeffs(X, K)
+    # r_m = sum_{k > m} gam_k c_{k-1-m};  h(lambda) = 1/2 sum_m r_m lambda^m
+    r = np.array([np.dot(gam[m + 1:], c[:K - m]) for m in range(K)])
+    h = np.zeros_like(lam)
+    for m in range(K - 1, -1, -1):
+        h = h * lam + r[m]
+    return 0.5 * (Q * h[None, :]) @ Q.T
+
+
+def approx_logprob_grad(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
+                        K: int | None = None, rho: float | None = None):
+    """(log P, dlog P / dA_S) of the order-j approximation, A = I - O; the second is
+    2n x 2n in the row order of sub_rows(modes) and excludes the -1/2 log det sigma_Q
+    term (which depends on sigma_Q, not on A_S)."""
+    modes = list(modes)
+    n = len(modes)
+    logP, info = approx_logprob(O, logdet_sigmaQ, M, modes, j, K=K, rho=rho)
+    grad = np.zeros((2 * n, 2 * n))
+    if n == 0 or not np.isfinite(logP):
+        return logP, grad
+    rho, K, D = info["rho"], info["K"], info["D"]
+    logsum = logP + 0.5 * logdet_sigmaQ
+    floor = EPS_SECTOR * D[0].max()
+    gam = np.zeros((j + 1, K + 1))                 # d log sum / d D[w, k] (tilted tables)
+    for k in range(K + 1):
+        if D[0, k] < floor:
+            continue
+        val, _, a, J = sector_fit(D[:, k], n, k, j)
+        if val <= 0.0 or a is None:
+            continue
+        g = math.exp(-k * math.log(rho) - logsum)
+        gam[:, k] = g * fit_last_point_adjoint(n, a, J, j)
+    for w in range(min(j, n) + 1):
+        if not gam[w].any():
+            continue
+        for W in combinations(range(n), w):
+            keep = [a for a in range(n) if a not in W]
+            loc = keep + [a + n for a in keep]      # local rows of S \\ W (x block, p block)
+            rows = sub_rows([modes[a] for a in keep], M)
+            dX = series_coeffs_adjoint(rho * O[np.ix_(rows, rows)], gam[w])
+            grad[np.ix_(loc, loc)] -= rho * dX
+    return logP, grad

@@ -8,6 +8,7 @@ sample"): log P = -1/2 log det sigma_Q + log T(A_S), A = sigma_Q^{-1}, and
 Chain to the physical parameters with sigma_Q = eta R diag(d) R^T + (1 - eta/2) I,
 d = (e^{-2r}/2 on x, e^{2r}/2 on p), R the xp form of U, and through the
 rectangular mesh U = T_last ... T_1 of cells T(theta, phi) on modes (m, m+1).
+The same chain carries the gradient of the moment approximation (grad_sigmaQ_approx).
 """
 from __future__ import annotations
 
@@ -49,6 +50,24 @@ def grad_sigmaQ(state, patterns, w) -> np.ndarray:
             rows += [m, m + M]
         H[np.ix_(rows, rows)] += G
     return -0.5 * float(np.sum(w)) * state.A - state.A @ H @ state.A
+
+
+def grad_sigmaQ_approx(state, patterns, w, order: int):
+    """dL/dsigma_Q for L = sum_p w_p log P_p with the order-j approximation of every P_p
+    (oracle/approx.py: approx_logprob_grad); the same chain as grad_sigmaQ.  Returns
+    (dL/dsigma_Q, log P per pattern)."""
+    from gbs_inputs import pattern_modes
+    from .approx import approx_logprob_grad, sub_rows
+    M = state.M
+    H = np.zeros((2 * M, 2 * M))
+    logP = []
+    for p, wp in zip(patterns, w):
+        modes = pattern_modes(p)
+        lp, g = approx_logprob_grad(state.O, state.logdet, M, modes, order)
+        logP.append(lp)
+        rows = sub_rows(modes, M)
+        H[np.ix_(rows, rows)] += wp * g
+    return -0.5 * float(np.sum(w)) * state.A - state.A @ H @ state.A, np.array(logP)
 
 
 def xp_form(U: np.ndarray) -> np.ndarray:
