@@ -530,6 +530,32 @@ def run_workloads(dev, stream, meas, fp32_peak):
                                             "frac": fl / (kms_adj * 1e-3) / meas["dd"]},
                        "max_abs_d_dsigmaQ_vs_oracle": float(np.abs(ds_gpu - ds_orc).max()),
                        "oracle_patterns_n": [int(n[i]) for i in chk]}
+    # the order-j approximation and its gradient (gbs_grad_approx, FP64 minors) on the same
+    # device, through the mesh: all 512 patterns at order 2, the first 64 at order 4; the
+    # gradient against the oracle's on the two smallest patterns.  An informational entry:
+    # a failure here is reported in the line, not raised
+    try:
+        from paper_2106_01445_gb300.api import LogProbClementsApprox
+        ap = {}
+        for order, npat in ((2, len(pats)), (4, 64)):
+            pdo, wo = pd[:npat], wts[:npat]
+
+            def astep():
+                lp = LogProbClementsApprox.apply(rt, et, tt, pt, pdo, ctx, order)
+                return torch.autograd.grad((wo * lp).sum(), (rt, et, tt, pt))
+
+            astep()
+            ms_a, _, _ = timed(astep, reps=2)
+            ap["order%d" % order] = {"patterns": npat, "ms_forward_and_backward": ms_a,
+                                     "patterns_per_s": npat / (ms_a * 1e-3)}
+        ones = torch.ones(len(chk), dtype=torch.float64, device=dev)
+        ds_a = ctx.grad_approx(st["O"], st["logdet"], pd[torch.as_tensor(chk, device=dev)], ones, 4)[0]
+        ds_ao, _ = ograd.grad_sigmaQ_approx(st_or, pats[chk], np.ones(len(chk)), 4)
+        ap["max_abs_d_dsigmaQ_vs_oracle_order4"] = float(np.abs(ds_a.cpu().numpy() - ds_ao).max())
+        ap["max_abs_dsigmaQ_order4"] = float(np.abs(ds_ao).max())
+        res["m32_grad"]["approx_gradient"] = ap
+    except Exception as e:
+        res["m32_grad"]["approx_gradient"] = {"error": repr(e)[:300]}
 
     # ---- 100 modes: approximation on a slice of the 16384 patterns (n = 40..90); exact
     # fixed point on 8 of the 64 n = 30 anchors and the approximation against it

@@ -228,6 +228,28 @@ int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
              const uint64_t *patterns, int n_pat, const double *w, double *dsigmaQ, double *logP,
              int32_t *status);
 
+/* Gradient of the order-j moment approximation (j = order, 1..4; FP64 minors), the
+ * same L and output as gbs_grad: dL/dsigma_Q = -1/2 (sum w) A - A H A with
+ * H = sum_p w_p dlog(sum_k part_k rho^-k)/dA_S (embedded), in reverse mode through the
+ * approximation's steps (Methods, "Partition function", "Moments calculation",
+ * "Approximation method"): the sum over sectors; the fit, by the implicit derivative
+ * of its moment conditions at the solution (d part / d mu'_i = e^{-a_0} (Hn^-1)_0i,
+ * Hn the fit's Newton matrix); the Stirling moments; the discrete Fourier transform;
+ * and every group minor, through d Z_{S\W}(t)/dA_S = -1/2 t Z_{S\W}(t)
+ * (G - G_{.W} G_WW^-1 G_{W.}), G = (I - t O_S)^-1.  The contour radius, the sector
+ * range and the order each sector's fit used are those of the forward pass (held
+ * fixed: log P is piecewise smooth in them).  Per pattern, O(C(n, j) n^2) work per
+ * contour point.  w: n_pat doubles (device).  dsigmaQ: 2M x 2M out (device).  logP,
+ * status: optional per-pattern outputs of the forward pass (as gbs_prob with
+ * GBS_FP64; GBS_E_NOT_SPD also when the adjoint met a non-positive pivot).  A
+ * pattern whose status is not GBS_OK or GBS_E_FIT adds nothing to H.  Synchronises
+ * (pattern sizes are checked on the host); GBS_E_INVALID for a pattern with more
+ * than 48 clicks or a detector >= M, or an order outside 1..4.  May grow the
+ * context's buffers: re-capture a CUDA graph of gbs_prob taken before it. */
+int gbs_grad_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                    const uint64_t *patterns, int n_pat, int order, const double *w, double *dsigmaQ,
+                    double *logP, int32_t *status);
+
 /* Chain to the state parameters of gbs_build_state: from dL/dsigma_Q (= dL/dsigma)
  * to dU (M x M complex interleaved: dL/dRe U + i dL/dIm U), dr (M) and deta (one
  * double), all on the device. */

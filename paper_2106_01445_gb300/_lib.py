@@ -38,6 +38,7 @@ SIGNATURES = {
     "gbs_prob_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_gen_patterns": (_i, [_vp, _u64, _u32, _i, _i, _i, _i, _vp]),
     "gbs_grad": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "gbs_grad_approx": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_grad_params": (_i, [_vp, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
     "gbs_clements_unitary": (_i, [_vp, _i, _vp, _vp, _vp]),
     "gbs_clements_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -226,6 +226,20 @@ class Context:
                                       _ptr(logP), _ptr(status)))
         return dsq, logP, status
 
+    def grad_approx(self, O: torch.Tensor, logdet: torch.Tensor, patterns, w: torch.Tensor, order: int = 4):
+        """dL/dsigma_Q for L = sum_p w_p log P_p with the order-j approximation of every P_p
+        (FP64 minors); also the forward's log P and status."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        w = w.to(device=self.device, dtype=torch.float64).contiguous()
+        dsq = torch.empty_like(O)
+        logP = torch.empty(n_pat, dtype=torch.float64, device=self.device)
+        status = torch.empty(n_pat, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gbs_grad_approx(self.h, M, _ptr(O), _ptr(logdet), _ptr(pats), n_pat, int(order),
+                                             _ptr(w), _ptr(dsq), _ptr(logP), _ptr(status)))
+        return dsq, logP, status
+
     def grad_params(self, Ud: torch.Tensor, rd: torch.Tensor, eta: float, dsq: torch.Tensor):
         """(dU interleaved (M, 2M), dr (M,), deta (1,)) from dL/dsigma_Q."""
         M = Ud.shape[0]
@@ -266,6 +280,24 @@ def patterns_numpy(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint64)
 
 
+def _clements_state(r, eta, theta, phi, gbs: "Context"):
+    """Mesh unitary and state build on the device: (rd, Ud, state dict)."""
+    M = r.shape[0]
+    Ud = gbs.clements_unitary(theta, phi, M)
+    rd = r.detach().to(device=gbs.device, dtype=torch.float64).contiguous()
+    st = gbs.build_state(torch.view_as_complex(Ud.view(M, M, 2)), rd, float(eta), check=False)
+    return rd, Ud, st
+
+
+def _clements_chain(fctx, dsq):
+    """(dr, deta, dtheta, dphi) from dL/dsigma_Q through the state build and the mesh."""
+    rd, theta, phi, Ud, _, _ = fctx.saved_tensors
+    gbs = fctx.gbs
+    dU, dr, deta = gbs.grad_params(Ud, rd, fctx.eta, dsq)
+    dth, dph = gbs.clements_grad(theta, phi, Ud, dU)
+    return dr, deta[0], dth, dph
+
+
 class LogProbClements(torch.autograd.Function):
     """log P of click patterns as a differentiable function of the squeezing r,
     the transmission eta and the mesh phases (theta, phi).  Forward: mesh
@@ -279,10 +311,7 @@ class LogProbClements(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, r, eta, theta, phi, patterns, gbs: Context):
-        M = r.shape[0]
-        Ud = gbs.clements_unitary(theta, phi, M)
-        rd = r.detach().to(device=gbs.device, dtype=torch.float64).contiguous()
-        st = gbs.build_state(torch.view_as_complex(Ud.view(M, M, 2)), rd, float(eta), check=False)
+        rd, Ud, st = _clements_state(r, eta, theta, phi, gbs)
         # fixed point, double-double for the patterns outside its range (in the library)
         out = gbs.prob(st["O"], st["logdet"], patterns, order=0, precision="auto")
         fctx.save_for_backward(rd, theta.detach(), phi.detach(), Ud, st["O"], st["logdet"])
@@ -291,9 +320,29 @@ class LogProbClements(torch.autograd.Function):
 
     @staticmethod
     def backward(fctx, grad_logP):
-        rd, theta, phi, Ud, O, logdet = fctx.saved_tensors
-        gbs = fctx.gbs
-        dsq, _, _ = gbs.grad(O, logdet, fctx.patterns, grad_logP.detach())
-        dU, dr, deta = gbs.grad_params(Ud, rd, fctx.eta, dsq)
-        dth, dph = gbs.clements_grad(theta, phi, Ud, dU)
-        return dr, deta[0], dth, dph, None, None
+        O, logdet = fctx.saved_tensors[4], fctx.saved_tensors[5]
+        dsq, _, _ = fctx.gbs.grad(O, logdet, fctx.patterns, grad_logP.detach())
+        return (*_clements_chain(fctx, dsq), None, None)
+
+
+class LogProbClementsApprox(torch.autograd.Function):
+    """As LogProbClements with the order-j moment approximation of log P (FP64
+    minors) in the forward and its adjoint (gbs_grad_approx) in the backward: for
+    patterns beyond the exact adjoint's 24 clicks.
+
+        logP = LogProbClementsApprox.apply(r, eta, theta, phi, patterns, ctx, order)
+    """
+
+    @staticmethod
+    def forward(fctx, r, eta, theta, phi, patterns, gbs: Context, order: int):
+        rd, Ud, st = _clements_state(r, eta, theta, phi, gbs)
+        out = gbs.prob(st["O"], st["logdet"], patterns, order=order, precision="fp64")
+        fctx.save_for_backward(rd, theta.detach(), phi.detach(), Ud, st["O"], st["logdet"])
+        fctx.gbs, fctx.eta, fctx.patterns, fctx.order = gbs, float(eta), patterns, int(order)
+        return out["logP"]
+
+    @staticmethod
+    def backward(fctx, grad_logP):
+        O, logdet = fctx.saved_tensors[4], fctx.saved_tensors[5]
+        dsq, _, _ = fctx.gbs.grad_approx(O, logdet, fctx.patterns, grad_logP.detach(), fctx.order)
+        return (*_clements_chain(fctx, dsq), None, None, None)

@@ -31,6 +31,29 @@ int gbs_ws_ensure(gbs_ctx *ctx, size_t bytes) {
     return GBS_OK;
 }
 
+int gbs_aux_ensure(gbs_ctx *ctx, size_t bytes, size_t keep) {
+    if (bytes <= ctx->aux_bytes) return GBS_OK;
+    GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    void *nb = nullptr;
+    if (cudaMalloc(&nb, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return gbs_fail(ctx, GBS_E_NOMEM, "cannot allocate %zu bytes of auxiliary workspace", bytes);
+    }
+    if (keep && ctx->aux) {
+        cudaError_t e = cudaMemcpyAsync(nb, ctx->aux, keep < ctx->aux_bytes ? keep : ctx->aux_bytes,
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(nb);
+            GBS_CUDA(ctx, e);
+        }
+    }
+    if (ctx->aux) GBS_CUDA(ctx, cudaFree(ctx->aux));
+    ctx->aux = nb;
+    ctx->aux_bytes = bytes;
+    return GBS_OK;
+}
+
 static int timing_fold_oldest(gbs_ctx *ctx) {
     const int R = gbs_ctx::kTimingRing;
     cudaEvent_t *e = ctx->tev + 2 * (ctx->t_tail % R);
@@ -358,6 +381,16 @@ int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad: bad arguments (M=%d, n_pat=%d)", M, n_pat);
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     return grad_sigmaQ(ctx, M, O, logdet_sigmaQ, patterns, n_pat, w, dsigmaQ, logP, status);
+}
+
+int gbs_grad_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
+                    const uint64_t *patterns, int n_pat, int order, const double *w, double *dsigmaQ,
+                    double *logP, int32_t *status) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 1 || !O || !logdet_sigmaQ || !patterns || !w || !dsigmaQ)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad_approx: bad arguments (M=%d, n_pat=%d)", M, n_pat);
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return approx_grad(ctx, M, O, logdet_sigmaQ, patterns, n_pat, order, w, dsigmaQ, logP, status);
 }
 
 int gbs_grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,

@@ -318,6 +318,82 @@ template <> struct GroupAcc<float> {
     __device__ __forceinline__ double get(int q) const { return (double)hi[q] + (double)lo[q]; }
 };
 
+// G <- -(I - t O_S)^{-1} in shared memory (packed upper triangle of 2n x 2n, then four
+// staged pivot columns of 2n entries), t = cs + i sn, by the symmetric sweep operator on
+// every pivot; Z_S(t) = prod of principal pivot^{-1/2} (the LDL^T pivots, one root per
+// pair) to s_zs on thread 0.  A pivot with Re <= 0 sets *s_bad.  All kMinorThreads threads
+// take part; ends with a barrier.
+template <typename R>
+__device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ O, const int *modes, int n,
+                                              double cs, double sn, cx<R> *G, int *s_bad, double *s_zs) {
+    const int t = threadIdx.x;
+    const int N = 2 * n, N2 = 2 * M;
+    for (int f = t; f < N * N; f += kMinorThreads) {
+        int i = f / N, j = f - i * N;
+        if (j < i) continue;
+        int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
+        double o = O[(size_t)si * N2 + sj];
+        G[pidx(N, i, j)] = init_entry<R>(i == j, cs, sn, o);
+    }
+    __syncthreads();
+    // symmetric sweep operator on every pivot: G <- -(I - t O_S)^{-1};
+    // Z_S(t) = prod of principal pivot^{-1/2} (pivots are the LDL^T pivots).
+    // Pivot k's column is staged in cb (and cb / pivot in cu) by the previous pivot's
+    // second phase, so an entry update is one complex product of staged values.
+    cx<R> *const cb0 = G + sym(N), *const cb1 = cb0 + N, *const cu0 = cb0 + 2 * N, *const cu1 = cb0 + 3 * N;
+    {
+        const cx<R> inv0 = cinv(G[0]);
+        for (int i = t; i < N; i += kMinorThreads) {
+            const cx<R> v = G[pidx(N, 0, i)];
+            cb0[i] = v;
+            cu0[i] = v * inv0;
+        }
+    }
+    __syncthreads();
+    cx<double> zs = mk<double>(1.0, 0.0);
+    cx<R> dprev = mk<R>(R(1), R(0));
+    const int fw = N + 1, fE = (N >> 1) * fw;  // rows p and N - 1 - p folded: N + 1 entries
+    for (int k = 0; k < N; ++k) {
+        const cx<R> *cb = (k & 1) ? cb1 : cb0, *cu = (k & 1) ? cu1 : cu0;
+        const cx<R> d = cb[k];
+        if (!(d.re > R(0)) && t == 0) *s_bad = 1;
+        if ((k & 1) && t == 0) zs = zs * widen(crsqrt(dprev * d));
+        dprev = d;
+        const cx<R> inv = cinv(d);
+        int fp = t / fw, fq = t - fp * fw;
+        const int sp = kMinorThreads / fw, sq = kMinorThreads - sp * fw;
+        for (int f = t; f < fE; f += kMinorThreads) {
+            int i, j;
+            if (fq < N - fp) { i = fp; j = fp + fq; } else { i = N - 1 - fp; j = i + (fq - (N - fp)); }
+            if (i != k && j != k) {
+                cx<R> &e = G[i * N - (i * (i - 1)) / 2 + (j - i)];
+                e = e - cb[i] * cu[j];
+            }
+            fq += sq;
+            fp += sp;
+            if (fq >= fw) { fq -= fw; ++fp; }
+        }
+        __syncthreads();
+        // scale pivot k's row and column; stage pivot k + 1's column
+        cx<R> *cbn = (k & 1) ? cb0 : cb1, *cun = (k & 1) ? cu0 : cu1;
+        const bool more = k + 1 < N;
+        const cx<R> invn = more ? cinv(G[pidx(N, k + 1, k + 1)]) : mk<R>(R(0), R(0));
+        for (int i = t; i < N; i += kMinorThreads) {
+            if (i != k) G[pidx_any(N, i, k)] = cu[i];
+            if (more) {
+                // entry (k, k + 1) is the one just scaled: cu[k + 1]
+                const cx<R> v = i == k ? cu[k + 1] : G[pidx_any(N, i, k + 1)];
+                cbn[i] = v;
+                cun[i] = v * invn;
+            }
+        }
+        if (t == 0) G[pidx(N, k, k)] = mk<R>(R(0), R(0)) - inv;
+        __syncthreads();
+    }
+    if (t == 0) { s_zs[0] = zs.re; s_zs[1] = zs.im; }
+    __syncthreads();
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) approx_minors_kernel(int M, const double *__restrict__ O,
                                                                     const uint64_t *__restrict__ pats,
@@ -359,77 +435,14 @@ __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) appro
             s_bad = 0;
         }
         __syncthreads();
-        const int N = 2 * n, N2 = 2 * M;
+        const int N = 2 * n;
         // t = rho e^{i nu}, nu = 2 pi l / L; M_t = I - t O_S (complex symmetric)
         double sn, cs;
         sincospi(2.0 * (double)l / (double)L, &sn, &cs);
         const double rho = pl.pat_rho[p];
         sn *= rho;
         cs *= rho;
-        for (int f = t; f < N * N; f += kMinorThreads) {
-            int i = f / N, j = f - i * N;
-            if (j < i) continue;
-            int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
-            double o = O[(size_t)si * N2 + sj];
-            G[pidx(N, i, j)] = init_entry<R>(i == j, cs, sn, o);
-        }
-        __syncthreads();
-        // symmetric sweep operator on every pivot: G <- -(I - t O_S)^{-1};
-        // Z_S(t) = prod of principal pivot^{-1/2} (pivots are the LDL^T pivots).
-        // Pivot k's column is staged in cb (and cb / pivot in cu) by the previous pivot's
-        // second phase, so an entry update is one complex product of staged values.
-        cx<R> *const cb0 = G + sym(N), *const cb1 = cb0 + N, *const cu0 = cb0 + 2 * N, *const cu1 = cb0 + 3 * N;
-        {
-            const cx<R> inv0 = cinv(G[0]);
-            for (int i = t; i < N; i += kMinorThreads) {
-                const cx<R> v = G[pidx(N, 0, i)];
-                cb0[i] = v;
-                cu0[i] = v * inv0;
-            }
-        }
-        __syncthreads();
-        cx<double> zs = mk<double>(1.0, 0.0);
-        cx<R> dprev = mk<R>(R(1), R(0));
-        const int fw = N + 1, fE = (N >> 1) * fw;  // rows p and N - 1 - p folded: N + 1 entries
-        for (int k = 0; k < N; ++k) {
-            const cx<R> *cb = (k & 1) ? cb1 : cb0, *cu = (k & 1) ? cu1 : cu0;
-            const cx<R> d = cb[k];
-            if (!(d.re > R(0)) && t == 0) s_bad = 1;
-            if ((k & 1) && t == 0) zs = zs * widen(crsqrt(dprev * d));
-            dprev = d;
-            const cx<R> inv = cinv(d);
-            int fp = t / fw, fq = t - fp * fw;
-            const int sp = kMinorThreads / fw, sq = kMinorThreads - sp * fw;
-            for (int f = t; f < fE; f += kMinorThreads) {
-                int i, j;
-                if (fq < N - fp) { i = fp; j = fp + fq; } else { i = N - 1 - fp; j = i + (fq - (N - fp)); }
-                if (i != k && j != k) {
-                    cx<R> &e = G[i * N - (i * (i - 1)) / 2 + (j - i)];
-                    e = e - cb[i] * cu[j];
-                }
-                fq += sq;
-                fp += sp;
-                if (fq >= fw) { fq -= fw; ++fp; }
-            }
-            __syncthreads();
-            // scale pivot k's row and column; stage pivot k + 1's column
-            cx<R> *cbn = (k & 1) ? cb0 : cb1, *cun = (k & 1) ? cu0 : cu1;
-            const bool more = k + 1 < N;
-            const cx<R> invn = more ? cinv(G[pidx(N, k + 1, k + 1)]) : mk<R>(R(0), R(0));
-            for (int i = t; i < N; i += kMinorThreads) {
-                if (i != k) G[pidx_any(N, i, k)] = cu[i];
-                if (more) {
-                    // entry (k, k + 1) is the one just scaled: cu[k + 1]
-                    const cx<R> v = i == k ? cu[k + 1] : G[pidx_any(N, i, k + 1)];
-                    cbn[i] = v;
-                    cun[i] = v * invn;
-                }
-            }
-            if (t == 0) G[pidx(N, k, k)] = mk<R>(R(0), R(0)) - inv;
-            __syncthreads();
-        }
-        if (t == 0) { s_zs[0] = zs.re; s_zs[1] = zs.im; }
-        __syncthreads();
+        sweep_inverse<R>(M, O, modes, n, cs, sn, G, &s_bad, s_zs);
         // entries of G = (I - t O_S)^{-1} are minus the swept matrix
         auto g = [&](int i, int j) -> cx<R> { cx<R> v = G[pidx_any(N, i, j)]; return mk<R>(-v.re, -v.im); };
         GroupAcc<R> acc;
@@ -830,6 +843,465 @@ __global__ void __launch_bounds__(kSumThreads) approx_sum_kernel(int n_pat, cons
     }
 }
 
+// ---- gradient of the approximation (not in the paper) ---------------------------------
+// L = sum_p w_p log P_p; reverse mode through the steps above, per pattern:
+//  * sum:     d log(sum_k part_k rho^-k) / d part_k = rho^-k / sum;
+//  * fit:     implicit derivative of the moment conditions of the fitted exp(-f) on its
+//             support, sum_s x_s^i F(x_s) = mu'_i with mu'_i = mu_i / n^i: at the solution
+//             d part / d mu'_i = e^{-a_0} (Hn^-1)_0i, Hn_il = sum_s x_s^(i+l) e^{-f(x_s)} the
+//             Newton matrix of the normalised fit;
+//  * moments: mu'_i = sum_{w <= i} S(i, w) w! D_w^(k) / n^i;
+//  * DFT:     D_w^(k) = (1/L) sum_{l <= L/2} c_l Re(D_w(t_l) e^{-2 pi i k l / L}), c_l = 1 for
+//             l = 0 and l = L/2, else 2; the adjoint of D_w(t_l) as one complex number
+//             (d/dRe - i d/dIm) is cbar_w(t_l) = (c_l / L) sum_k gamma_w^(k) e^{-2 pi i k l / L};
+//  * minors:  with d det(X)^-1/2 = -1/2 det(X)^-1/2 tr(X^-1 dX) and I - t O = (1 - t) I + t A,
+//             d Z_{S\W}(t) / dA_S = -1/2 t Z_{S\W}(t) [(I - t O_{S\W})^-1 embedded in S], and that
+//             embedded inverse is G - G_{.W} G_WW^-1 G_{W.} (zero on the rows of W), so unit
+//             (S, t_l) adds Re(-1/2 t (s G - G K G)) to dlog P / dA_S, with
+//             s = sum_w cbar_w D_w(t) and K = sum_{W, |W| <= j} cbar_|W| Z_{S\W}(t) embed(G_WW^-1).
+// K is built one 2 x 2 mode block (a, b) per thread (no atomics, a fixed summation order):
+// every W holding a and b is V + {a, b} with V over the other modes; eliminating V first
+// leaves on the rows of a and b the Schur complement of V in G_WW, whose inverse is the
+// (a, b) block of G_WW^-1 and whose pivots complete det(G_WW).
+constexpr int kGradApproxMaxN = 48;  // clicks per pattern on the approximation's gradient
+constexpr int kPanel = 8;            // columns of K G per pass of the G K G product
+
+__device__ __forceinline__ double factorial_small(int w) {
+    const double tab[kMaxOrder + 1] = {1, 1, 2, 6, 24};
+    return tab[w];
+}
+
+// y = Hn^-1 e_0 for the (J + 1) x (J + 1) Newton matrix Hn_il = pw[i + l] (Gaussian
+// elimination with partial pivoting, as the fit's own step); false if singular
+__device__ bool solve_e0(int J, const double *pw, double *y) {
+    const int W = kMaxOrder + 2;
+    double Ab[(kMaxOrder + 1) * (kMaxOrder + 2)];
+    for (int i = 0; i <= J; ++i) {
+        for (int k = 0; k <= J; ++k) Ab[i * W + k] = pw[i + k];
+        Ab[i * W + J + 1] = i == 0 ? 1.0 : 0.0;
+    }
+    for (int c = 0; c <= J; ++c) {
+        int piv = c;
+        for (int i = c + 1; i <= J; ++i)
+            if (fabs(Ab[i * W + c]) > fabs(Ab[piv * W + c])) piv = i;
+        if (Ab[piv * W + c] == 0.0) return false;
+        if (piv != c)
+            for (int k = 0; k <= J + 1; ++k) {
+                const double tmp = Ab[c * W + k];
+                Ab[c * W + k] = Ab[piv * W + k];
+                Ab[piv * W + k] = tmp;
+            }
+        for (int i = c + 1; i <= J; ++i) {
+            const double f = Ab[i * W + c] / Ab[c * W + c];
+            for (int k = c; k <= J + 1; ++k) Ab[i * W + k] -= f * Ab[c * W + k];
+        }
+    }
+    for (int i = J; i >= 0; --i) {
+        double v = Ab[i * W + J + 1];
+        for (int q = i + 1; q <= J; ++q) v -= Ab[i * W + q] * y[q];
+        y[i] = v / Ab[i * W + i];
+    }
+    return true;
+}
+
+// one warp per sector: the forward's fit again (same inputs and code, so the same order
+// and coefficients), then beta_w = d part / d D_w^(k), w = 0..kMaxOrder (0 where unused)
+__global__ void __launch_bounds__(kSecThreads) approx_fit_adjoint_kernel(int n_pat, int order, ApproxPlan pl,
+                                                                       double *__restrict__ sec_B) {
+    const int lane = threadIdx.x & 31;
+    const long long nsec = pl.sec_off[n_pat];
+    const long long nwarps = (long long)gridDim.x * (kSecThreads / 32);
+    if (*pl.overflow) return;
+    for (long long gs = (long long)blockIdx.x * (kSecThreads / 32) + (threadIdx.x >> 5); gs < nsec; gs += nwarps) {
+        int lo = 0, hi = n_pat;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pl.sec_off[mid] <= gs) lo = mid; else hi = mid;
+        }
+        const int p = lo, n = pl.pat_n[p];
+        const int k = (int)(gs - pl.sec_off[p]);
+        const double *Dk = pl.sec_D + (size_t)gs * (kMaxOrder + 1);
+        double beta[kMaxOrder + 1];
+        for (int w = 0; w <= kMaxOrder; ++w) beta[w] = 0.0;
+        // fitted sectors only (k >= n: the support is v = 0..n-1)
+        if (n > 0 && k >= n && pl.sec_part[gs] != 0.0) {
+            const int Jmax = order < n - 1 ? order : n - 1;
+            double mu[kMaxOrder + 1];
+            for (int i = 0; i <= Jmax; ++i) {
+                double s = 0.0, fw = 1.0;
+                for (int w = 0; w <= i; ++w) {
+                    s += stirling2(i, w) * fw * Dk[w];
+                    fw *= (w + 1);
+                }
+                mu[i] = s;
+            }
+            for (int J = Jmax; J >= 0; --J) {
+                double m[kMaxOrder + 1], a[kMaxOrder + 1];
+                double np = 1.0;
+                for (int i = 0; i <= J; ++i) { m[i] = mu[i] / np / mu[0]; np *= n; }
+                if (!maxent_fit_warp(0, n, J, m, a, lane)) continue;
+                double pw[2 * kMaxOrder + 1];
+                for (int q = 0; q <= 2 * J; ++q) pw[q] = 0.0;
+                for (int sp = lane; sp < n; sp += 32) {
+                    const double x = (double)sp / n;
+                    double f = 0.0, xp = 1.0;
+                    for (int i = 0; i <= J; ++i) { f += a[i] * xp; xp *= x; }
+                    const double q = exp(-f);
+                    xp = 1.0;
+                    for (int i = 0; i <= 2 * J; ++i) { pw[i] += xp * q; xp *= x; }
+                }
+                for (int i = 0; i <= 2 * J; ++i) pw[i] = warp_sum_bcast(pw[i]);
+                double y[kMaxOrder + 1];
+                if (solve_e0(J, pw, y)) {
+                    const double e = exp(-a[0]);
+                    for (int w = 0; w <= J; ++w) {
+                        double s = 0.0, ni = 1.0;
+                        for (int i = 0; i <= J; ++i) {
+                            if (i >= w) s += y[i] * stirling2(i, w) * factorial_small(w) / ni;
+                            ni *= n;
+                        }
+                        beta[w] = e * s;
+                    }
+                }
+                break;
+            }
+        }
+        if (lane == 0)
+            for (int w = 0; w <= kMaxOrder; ++w) sec_B[(size_t)gs * (kMaxOrder + 1) + w] = beta[w];
+    }
+}
+
+// one CTA per pattern: gamma_w^(k) = beta_w^(k) rho^-k / sum (in place), then the DFT's
+// adjoint to the units: cbar_w(t_l), l = 0..L/2, interleaved (re, im) like unit_D
+__global__ void __launch_bounds__(kDftThreads) approx_dft_adjoint_kernel(int order, ApproxPlan pl,
+                                                                       double *__restrict__ sec_B,
+                                                                       double *__restrict__ unit_B) {
+    extern __shared__ double tw[];  // cos, sin (2 pi m / L), m < L
+    __shared__ double s_top, s_sum;
+    const int p = blockIdx.x, t = threadIdx.x;
+    const int n = pl.pat_n[p], L = pl.pat_L[p];
+    if (n <= 0 || L <= 0 || *pl.overflow) return;
+    const int H = L / 2;
+    const double *part = pl.sec_part + pl.sec_off[p];
+    const double lr = log(pl.pat_rho[p]);
+    if (t < 32) {
+        // the sum of the tilted last points in logs, as the forward's sum
+        double top = -INFINITY;
+        for (int k = t; k < L; k += 32)
+            if (part[k] != 0.0) top = fmax(top, log(fabs(part[k])) - k * lr);
+        for (int off = 16; off; off >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, off));
+        double s = 0.0;
+        for (int k = t; k < L; k += 32)
+            if (part[k] != 0.0) s += exp(log(fabs(part[k])) - k * lr - top);
+        s = warp_sum_bcast(s);
+        if (t == 0) { s_top = top; s_sum = s; }
+    }
+    for (int m = t; m < L; m += kDftThreads) sincospi(2.0 * (double)m / (double)L, &tw[2 * m + 1], &tw[2 * m]);
+    __syncthreads();
+    const double top = s_top, ssum = s_sum;
+    double *B = sec_B + (size_t)pl.sec_off[p] * (kMaxOrder + 1);
+    for (int k = t; k < L; k += kDftThreads) {
+        const double gk = (part[k] != 0.0 && ssum > 0.0) ? exp(-k * lr - top) / ssum : 0.0;
+        for (int w = 0; w <= kMaxOrder; ++w) B[(size_t)k * (kMaxOrder + 1) + w] *= gk;
+    }
+    __syncthreads();
+    double *Ub = unit_B + (size_t)pl.unit_off[p] * 2 * (kMaxOrder + 1);
+    for (int idx = t; idx < (H + 1) * (kMaxOrder + 1); idx += kDftThreads) {
+        const int l = idx / (kMaxOrder + 1), w = idx - l * (kMaxOrder + 1);
+        double re = 0.0, im = 0.0;
+        if (w <= order) {
+            int m = 0;  // k l mod L
+            for (int k = 0; k < L; ++k) {
+                const double gm = B[(size_t)k * (kMaxOrder + 1) + w];
+                re += gm * tw[2 * m];
+                im -= gm * tw[2 * m + 1];
+                m += l;
+                if (m >= L) m -= L;
+            }
+        }
+        const double c = (l == 0 || 2 * l == L) ? 1.0 : 2.0;
+        Ub[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w] = c * re / L;
+        Ub[(size_t)l * 2 * (kMaxOrder + 1) + 2 * w + 1] = c * im / L;
+    }
+}
+
+// The modes m[0..NV-1] (V) and then the NT tail modes of G_WW (local mode indices, rows
+// 2m and 2m + 1 of G), from the swept matrix Gs (= -G, packed): eliminate V's 2 NV pivots
+// (unpivoted LDL^T) and return det(G_VV)^-1/2 (principal roots of pivot pairs; Re > 0
+// for every pivot of the accretive G) with the Schur complement of V on the tail rows
+// in s (packed 2 NT x 2 NT).
+template <int NV, int NT>
+__device__ __forceinline__ cx<double> schur_tail(const cx<double> *__restrict__ Gs, int N, const int (&m)[NV + NT],
+                                                 cx<double> (&s)[NT * (2 * NT + 1)], bool &bad) {
+    constexpr int K = 2 * (NV + NT);
+    cx<double> a[K * (K + 1) / 2];
+    int rr[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) rr[i] = 2 * m[i >> 1] + (i & 1);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = i; j < K; ++j) {
+            const cx<double> v = Gs[pidx_any(N, rr[i], rr[j])];
+            a[pidx(K, i, j)] = mk<double>(-v.re, -v.im);
+        }
+    cx<double> f = mk<double>(1.0, 0.0), prev = mk<double>(1.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < 2 * NV; ++k) {
+        const cx<double> d = a[pidx(K, k, k)];
+        if (!(d.re > 0.0)) bad = true;
+        if (k & 1) f = f * crsqrt(prev * d);
+        prev = d;
+        const cx<double> inv = cinv(d);
+#pragma unroll
+        for (int i = k + 1; i < K; ++i) {
+            const cx<double> li = a[pidx(K, k, i)] * inv;
+#pragma unroll
+            for (int j = i; j < K; ++j) a[pidx(K, i, j)] = a[pidx(K, i, j)] - li * a[pidx(K, k, j)];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * NT; ++i)
+#pragma unroll
+        for (int j = i; j < 2 * NT; ++j) s[pidx(2 * NT, i, j)] = a[pidx(K, 2 * NV + i, 2 * NV + j)];
+    return f;
+}
+
+// W = V + {a}: adds wz Z-factor det(G_WW)^-1/2 [G_WW^-1]_aa to the diagonal block (k00, k01, k11)
+template <int NV>
+__device__ __forceinline__ void diag_leaf(const cx<double> *__restrict__ Gs, int N, const int (&m)[NV + 1],
+                                          cx<double> wz, cx<double> &k00, cx<double> &k01, cx<double> &k11,
+                                          bool &bad) {
+    cx<double> s[3];
+    const cx<double> f = schur_tail<NV, 1>(Gs, N, m, s, bad);
+    const cx<double> det = s[0] * s[2] - s[1] * s[1];
+    if (!(s[0].re > 0.0) || !(det.re * s[0].re + det.im * s[0].im > 0.0)) bad = true;
+    const cx<double> wgt = wz * f * crsqrt(det) * cinv(det);
+    k00 = k00 + wgt * s[2];
+    k01 = k01 - wgt * s[1];
+    k11 = k11 + wgt * s[0];
+}
+
+// W = V + {a, b}, a < b: adds wz det(G_WW)^-1/2 [G_WW^-1]_ab to the off-diagonal block
+// ko = (00, 01, 10, 11); with the tail S = [[P, Q], [Q^T, R]] (a's rows, b's rows),
+// [S^-1]_ab = -P^-1 Q C^-1, C = R - Q^T P^-1 Q, det S = det P det C
+template <int NV>
+__device__ __forceinline__ void off_leaf(const cx<double> *__restrict__ Gs, int N, const int (&m)[NV + 2],
+                                         cx<double> wz, cx<double> (&ko)[4], bool &bad) {
+    cx<double> s[10];
+    const cx<double> f = schur_tail<NV, 2>(Gs, N, m, s, bad);
+    const cx<double> p00 = s[pidx(4, 0, 0)], p01 = s[pidx(4, 0, 1)], p11 = s[pidx(4, 1, 1)];
+    const cx<double> q00 = s[pidx(4, 0, 2)], q01 = s[pidx(4, 0, 3)], q10 = s[pidx(4, 1, 2)], q11 = s[pidx(4, 1, 3)];
+    const cx<double> r00 = s[pidx(4, 2, 2)], r01 = s[pidx(4, 2, 3)], r11 = s[pidx(4, 3, 3)];
+    const cx<double> detP = p00 * p11 - p01 * p01;
+    const cx<double> iP = cinv(detP);
+    // X = P^-1 Q
+    const cx<double> x00 = (p11 * q00 - p01 * q10) * iP, x01 = (p11 * q01 - p01 * q11) * iP;
+    const cx<double> x10 = (p00 * q10 - p01 * q00) * iP, x11 = (p00 * q11 - p01 * q01) * iP;
+    const cx<double> c00 = r00 - (q00 * x00 + q10 * x10), c01 = r01 - (q00 * x01 + q10 * x11),
+                     c11 = r11 - (q01 * x01 + q11 * x11);
+    const cx<double> detC = c00 * c11 - c01 * c01;
+    const cx<double> iC = cinv(detC);
+    if (!(p00.re > 0.0) || !(detP.re * p00.re + detP.im * p00.im > 0.0) || !(c00.re > 0.0) ||
+        !(detC.re * c00.re + detC.im * c00.im > 0.0))
+        bad = true;
+    const cx<double> ci00 = c11 * iC, ci01 = mk<double>(0.0, 0.0) - c01 * iC, ci11 = c00 * iC;
+    const cx<double> wgt = wz * f * crsqrt(detP) * crsqrt(detC);
+    ko[0] = ko[0] - wgt * (x00 * ci00 + x01 * ci01);
+    ko[1] = ko[1] - wgt * (x00 * ci01 + x01 * ci11);
+    ko[2] = ko[2] - wgt * (x10 * ci00 + x11 * ci01);
+    ko[3] = ko[3] - wgt * (x10 * ci01 + x11 * ci11);
+}
+
+// one CTA per (pattern, chunk of its contour points): per point t_l the inverse G (the
+// forward's sweep), K block by block, then Re(-1/2 t (s G - G K G)) added to the chunk's
+// own slot (packed upper triangle of 2n x 2n; every entry has one owner thread, so the
+// sums over l are in a fixed order)
+__global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel(
+    int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int order, int chunks_per,
+    ApproxPlan pl, const double *__restrict__ unit_B, double *__restrict__ slots, size_t sst,
+    int *__restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int modes[128];
+    __shared__ int s_bad;
+    __shared__ double s_zs[2];
+    const int t = threadIdx.x;
+    const int p = blockIdx.x / chunks_per, c = blockIdx.x - p * chunks_per;
+    const int n = pl.pat_n[p], L = pl.pat_L[p];
+    if (n <= 0 || L <= 0 || *pl.overflow) return;
+    const int N = 2 * n;
+    cx<double> *const Gs = (cx<double> *)smem_raw;      // swept matrix, then four staged columns
+    cx<double> *const Kp = Gs + sym(N) + 4 * N;          // K, packed upper triangle
+    cx<double> *const Tp = Kp + sym(N);                  // N x kPanel columns of K G
+    double *const slot = slots + (size_t)blockIdx.x * sst;
+    for (int f = t; f < sym(N); f += kMinorThreads) slot[f] = 0.0;
+    if (t == 0) {
+        const uint64_t wlo = pats[2 * p], whi = pats[2 * p + 1];
+        int q = 0;
+        for (int i = 0; i < M; ++i) {
+            const uint64_t w = i < 64 ? wlo : whi;
+            if (w >> (i & 63) & 1ull) modes[q++] = i;
+        }
+        s_bad = 0;
+    }
+    __syncthreads();
+    const int U = L / 2 + 1;
+    const int l0 = (int)((long long)c * U / chunks_per), l1 = (int)((long long)(c + 1) * U / chunks_per);
+    const double rho = pl.pat_rho[p];
+    const int nb = n * (n + 1) / 2;
+    bool bad = false;
+    auto gt = [&](int i, int j) -> cx<double> { const cx<double> v = Gs[pidx_any(N, i, j)]; return mk<double>(-v.re, -v.im); };
+    for (int l = l0; l < l1; ++l) {
+        double sn, cs;
+        sincospi(2.0 * (double)l / (double)L, &sn, &cs);
+        sn *= rho;
+        cs *= rho;
+        sweep_inverse<double>(M, O, modes, n, cs, sn, Gs, &s_bad, s_zs);
+        const size_t uo = ((size_t)pl.unit_off[p] + l) * 2 * (kMaxOrder + 1);
+        cx<double> cb[kMaxOrder + 1];
+        cx<double> sl = mk<double>(0.0, 0.0);
+        for (int w = 0; w <= kMaxOrder; ++w) {
+            cb[w] = mk<double>(unit_B[uo + 2 * w], unit_B[uo + 2 * w + 1]);
+            sl = sl + cb[w] * mk<double>(pl.unit_D[uo + 2 * w], pl.unit_D[uo + 2 * w + 1]);
+        }
+        const cx<double> zs = mk<double>(s_zs[0], s_zs[1]);
+        for (int blk = t; blk < nb; blk += kMinorThreads) {
+            int a = 0, rem = blk;
+            while (rem >= n - a) { rem -= n - a; ++a; }
+            const int b = a + rem;
+            const cx<double> z0 = mk<double>(0.0, 0.0);
+            if (a == b) {
+                cx<double> k00 = z0, k01 = z0, k11 = z0;
+                {
+                    const int m0[1] = {a};
+                    diag_leaf<0>(Gs, N, m0, cb[1] * zs, k00, k01, k11, bad);
+                }
+                if (order >= 2) {
+                    const cx<double> wz = cb[2] * zs;
+                    for (int i1 = 0; i1 < n; ++i1) {
+                        if (i1 == a) continue;
+                        const int m1[2] = {i1, a};
+                        diag_leaf<1>(Gs, N, m1, wz, k00, k01, k11, bad);
+                    }
+                }
+                if (order >= 3) {
+                    const cx<double> wz = cb[3] * zs;
+                    for (int i1 = 0; i1 < n; ++i1) {
+                        if (i1 == a) continue;
+                        for (int i2 = i1 + 1; i2 < n; ++i2) {
+                            if (i2 == a) continue;
+                            const int m2[3] = {i1, i2, a};
+                            diag_leaf<2>(Gs, N, m2, wz, k00, k01, k11, bad);
+                        }
+                    }
+                }
+                if (order >= 4) {
+                    const cx<double> wz = cb[4] * zs;
+                    for (int i1 = 0; i1 < n; ++i1) {
+                        if (i1 == a) continue;
+                        for (int i2 = i1 + 1; i2 < n; ++i2) {
+                            if (i2 == a) continue;
+                            for (int i3 = i2 + 1; i3 < n; ++i3) {
+                                if (i3 == a) continue;
+                                const int m3[4] = {i1, i2, i3, a};
+                                diag_leaf<3>(Gs, N, m3, wz, k00, k01, k11, bad);
+                            }
+                        }
+                    }
+                }
+                Kp[pidx(N, 2 * a, 2 * a)] = k00;
+                Kp[pidx(N, 2 * a, 2 * a + 1)] = k01;
+                Kp[pidx(N, 2 * a + 1, 2 * a + 1)] = k11;
+            } else {
+                cx<double> ko[4] = {z0, z0, z0, z0};
+                if (order >= 2) {
+                    const int m0[2] = {a, b};
+                    off_leaf<0>(Gs, N, m0, cb[2] * zs, ko, bad);
+                }
+                if (order >= 3) {
+                    const cx<double> wz = cb[3] * zs;
+                    for (int i1 = 0; i1 < n; ++i1) {
+                        if (i1 == a || i1 == b) continue;
+                        const int m1[3] = {i1, a, b};
+                        off_leaf<1>(Gs, N, m1, wz, ko, bad);
+                    }
+                }
+                if (order >= 4) {
+                    const cx<double> wz = cb[4] * zs;
+                    for (int i1 = 0; i1 < n; ++i1) {
+                        if (i1 == a || i1 == b) continue;
+                        for (int i2 = i1 + 1; i2 < n; ++i2) {
+                            if (i2 == a || i2 == b) continue;
+                            const int m2[4] = {i1, i2, a, b};
+                            off_leaf<2>(Gs, N, m2, wz, ko, bad);
+                        }
+                    }
+                }
+                Kp[pidx(N, 2 * a, 2 * b)] = ko[0];
+                Kp[pidx(N, 2 * a, 2 * b + 1)] = ko[1];
+                Kp[pidx(N, 2 * a + 1, 2 * b)] = ko[2];
+                Kp[pidx(N, 2 * a + 1, 2 * b + 1)] = ko[3];
+            }
+        }
+        __syncthreads();
+        // Re(-1/2 t (s G - G K G)) on the upper triangle, kPanel columns at a time
+        const cx<double> ht = mk<double>(-0.5 * cs, -0.5 * sn);
+        for (int j0 = 0; j0 < N; j0 += kPanel) {
+            for (int f = t; f < N * kPanel; f += kMinorThreads) {
+                const int r = f / kPanel, j = j0 + (f - r * kPanel);
+                cx<double> acc = mk<double>(0.0, 0.0);
+                if (j < N)
+                    for (int q = 0; q < N; ++q) acc = acc + Kp[pidx_any(N, r, q)] * gt(q, j);
+                Tp[f] = acc;
+            }
+            __syncthreads();
+            for (int f = t; f < N * kPanel; f += kMinorThreads) {
+                const int i = f / kPanel, jj = f - i * kPanel, j = j0 + jj;
+                if (j >= N || i > j) continue;
+                cx<double> y = mk<double>(0.0, 0.0);
+                for (int q = 0; q < N; ++q) y = y + gt(i, q) * Tp[q * kPanel + jj];
+                const cx<double> v = ht * (sl * gt(i, j) - y);
+                slot[pidx(N, i, j)] += v.re;
+            }
+            __syncthreads();
+        }
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (t == 0 && s_bad) atomicOr(flags + p, 1);
+}
+
+// per pattern: F_p = w_p * (sum of its chunk slots, in chunk order), dense 2n x 2n at stride
+// fst; zero for a pattern whose forward failed (status other than ok / fit fallback, or no
+// sector) or whose adjoint met a non-positive pivot
+__global__ void approx_grad_finalize_kernel(int chunks_per, ApproxPlan pl, const double *__restrict__ slots,
+                                            size_t sst, const double *__restrict__ w,
+                                            const double *__restrict__ logP, const int32_t *__restrict__ status,
+                                            const int *__restrict__ flags, double *__restrict__ F, size_t fst) {
+    const int p = blockIdx.x;
+    const int n = pl.pat_n[p];
+    if (n <= 0) return;
+    const int D = 2 * n;
+    const int st = status[p];
+    const bool ok = (st == GBS_OK || st == GBS_E_FIT) && !flags[p] && isfinite(logP[p]);
+    for (int f = threadIdx.x; f < D * D; f += blockDim.x) {
+        const int i = f / D, j = f - i * D;
+        double v = 0.0;
+        if (ok) {
+            const int q = pidx_any(D, i, j);
+            for (int c = 0; c < chunks_per; ++c) v += slots[((size_t)p * chunks_per + c) * sst + q];
+            v *= w[p];
+        }
+        F[(size_t)p * fst + f] = v;
+    }
+}
+
+__global__ void approx_grad_status_kernel(int n_pat, const int32_t *__restrict__ st_in,
+                                          const int *__restrict__ flags, int32_t *__restrict__ st_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_pat) st_out[p] = (st_in[p] == GBS_OK || st_in[p] == GBS_E_FIT) && flags[p] ? GBS_E_NOT_SPD : st_in[p];
+}
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct ApproxOffsets {
@@ -880,9 +1352,10 @@ ApproxPlan approx_plan_from(void *ws, int n_pat, long long units = 0, long long 
 template <typename R>
 int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status,
-               double *curves = nullptr, int curve_K = -1, int curve_n = -1) {
-    // patterns up to this size are taken
-    const int nmax_smem = MinorPrec<R>::nmax;
+               double *curves = nullptr, int curve_K = -1, int curve_n = -1, int n_limit = -1) {
+    // patterns up to this size are taken (the packed inverse must fit in shared memory;
+    // a caller may lower it)
+    const int nmax_smem = n_limit > 0 && n_limit < MinorPrec<R>::nmax ? n_limit : MinorPrec<R>::nmax;
     static_assert(kMaxK + 1 <= 4096, "sector table");
     if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
         int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
@@ -988,4 +1461,106 @@ int approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *log
     if (precision == GBS_FF)
         return run_approx<ff>(ctx, M, O, logdet, pattern, 1, order, logP, nullptr, nullptr, status, curves, K, n);
     return gbs_fail(ctx, GBS_E_INVALID, "gbs_approx_sector_curves: the curves run in FP64 or float-float");
+}
+
+int approx_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats, int n_pat,
+                int order, const double *w, double *dsq, double *logP, int32_t *status) {
+    if (order < 1 || order > kMaxOrder)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_grad_approx: order %d not in 1..%d", order, kMaxOrder);
+    // every pattern must be valid with at most kGradApproxMaxN clicks: checked on the host
+    // from a copy of the pattern words (one small readback)
+    const size_t pb = (size_t)n_pat * 16;
+    uint64_t *hp = (uint64_t *)malloc(pb + 16);
+    if (!hp) return gbs_fail(ctx, GBS_E_NOMEM, "gbs_grad_approx: host buffer");
+    cudaError_t ce = cudaMemcpyAsync(hp, pats, pb, cudaMemcpyDeviceToHost, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    if (ce != cudaSuccess) {
+        free(hp);
+        GBS_CUDA(ctx, ce);
+    }
+    int n_max = 0;
+    for (int p = 0; p < n_pat; ++p) {
+        const uint64_t lo = hp[2 * p], hi = hp[2 * p + 1];
+        const int n = __builtin_popcountll(lo) + __builtin_popcountll(hi);
+        const bool out_of_range =
+            (M < 64 && (lo >> M)) || (M <= 64 && hi) || (M > 64 && M < 128 && (hi >> (M - 64)));
+        if (n > kGradApproxMaxN || out_of_range) {
+            free(hp);
+            return gbs_fail(ctx, GBS_E_INVALID,
+                            "gbs_grad_approx: pattern %d has %d clicks (at most %d) or a detector >= M", p, n,
+                            kGradApproxMaxN);
+        }
+        n_max = n > n_max ? n : n_max;
+    }
+    free(hp);
+    // kept across the forward: its log P and status, the adjoint's flags
+    const size_t np_ = (size_t)n_pat;
+    const size_t o_lp = 0, o_st = align256(8 * np_), o_fl = o_st + align256(4 * np_), keep = o_fl + align256(4 * np_);
+    int st = gbs_aux_ensure(ctx, keep, 0);
+    if (st) return st;
+    {
+        char *b = (char *)ctx->aux;
+        st = run_approx<double>(ctx, M, O, logdet, pats, n_pat, order, (double *)(b + o_lp), nullptr, nullptr,
+                                (int32_t *)(b + o_st), nullptr, -1, -1, kGradApproxMaxN);
+        if (st) return st;
+    }
+    // the plan's sizes (units, largest n, largest L, sectors)
+    ApproxPlan pl = approx_plan_from(ctx->ws, n_pat);
+    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.info, 32, cudaMemcpyDeviceToHost, ctx->stream));
+    GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const long long units = ((long long *)ctx->pinned)[0], secs = ((long long *)ctx->pinned)[3];
+    const int Lmax = (int)((long long *)ctx->pinned)[2];
+    pl = approx_plan_from(ctx->ws, n_pat, units, secs);
+    // contour points of a pattern split over chunks_per CTAs: about two CTAs per SM in all
+    const int want = (2 * ctx->num_sms + n_pat - 1) / n_pat;
+    const int chunks_per = want < 1 ? 1 : (want > 64 ? 64 : want);
+    const int Nm = 2 * (n_max > 0 ? n_max : 1);
+    const size_t sst = (size_t)sym(Nm), fst = (size_t)Nm * Nm, N2 = (size_t)(2 * M) * (2 * M);
+    const size_t o_sb = keep, o_ub = o_sb + align256(8 * (kMaxOrder + 1) * (size_t)secs),
+                 o_sl = o_ub + align256(16 * (kMaxOrder + 1) * (size_t)units),
+                 o_F = o_sl + align256(8 * np_ * chunks_per * sst), o_H = o_F + align256(8 * np_ * fst),
+                 o_T1 = o_H + align256(8 * N2), o_T2 = o_T1 + align256(8 * N2), o_sw = o_T2 + align256(8 * N2),
+                 total = o_sw + 256;
+    st = gbs_aux_ensure(ctx, total, keep);
+    if (st) return st;
+    char *b = (char *)ctx->aux;
+    double *lp_i = (double *)(b + o_lp);
+    int32_t *st_i = (int32_t *)(b + o_st);
+    int *flags = (int *)(b + o_fl);
+    double *sec_B = (double *)(b + o_sb), *unit_B = (double *)(b + o_ub), *slots = (double *)(b + o_sl);
+    double *F = (double *)(b + o_F), *H = (double *)(b + o_H), *T1 = (double *)(b + o_T1), *T2 = (double *)(b + o_T2),
+           *sw = (double *)(b + o_sw);
+    GBS_CUDA(ctx, cudaMemsetAsync(flags, 0, 4 * np_, ctx->stream));
+    if (secs > 0) {
+        const long long wsec = (secs + kSecThreads / 32 - 1) / (kSecThreads / 32);
+        const int fit_blocks = (int)(wsec < (long long)ctx->num_sms * 16 ? wsec : ctx->num_sms * 16);
+        approx_fit_adjoint_kernel<<<fit_blocks, kSecThreads, 0, ctx->stream>>>(n_pat, order, pl, sec_B);
+        GBS_CUDA(ctx, cudaGetLastError());
+        const size_t dft_smem = sizeof(double) * 2 * (size_t)(Lmax > 0 ? Lmax : 1);
+        GBS_CUDA(ctx, cudaFuncSetAttribute(approx_dft_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)dft_smem));
+        approx_dft_adjoint_kernel<<<n_pat, kDftThreads, dft_smem, ctx->stream>>>(order, pl, sec_B, unit_B);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    if (n_max > 0) {
+        // swept matrix + four staged columns, K, one panel of K G
+        const size_t smem = sizeof(cx<double>) * (2 * sst + 4 * (size_t)Nm + (size_t)Nm * kPanel);
+        GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        approx_minors_adjoint_kernel<<<(unsigned)(n_pat * chunks_per), kMinorThreads, smem, ctx->stream>>>(
+            M, O, pats, order, chunks_per, pl, unit_B, slots, sst, flags);
+        GBS_CUDA(ctx, cudaGetLastError());
+        approx_grad_finalize_kernel<<<n_pat, 256, 0, ctx->stream>>>(chunks_per, pl, slots, sst, w, lp_i, st_i, flags,
+                                                                   F, fst);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    st = grad_chain_sigma(ctx, M, O, pats, n_pat, F, fst, w, H, T1, T2, sw, dsq);
+    if (st) return st;
+    if (logP) GBS_CUDA(ctx, cudaMemcpyAsync(logP, lp_i, 8 * np_, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (status) {
+        // a pattern the adjoint could not differentiate reports GBS_E_NOT_SPD
+        approx_grad_status_kernel<<<(n_pat + 255) / 256, 256, 0, ctx->stream>>>(n_pat, st_i, flags, status);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    return GBS_OK;
 }

@@ -58,6 +58,9 @@ int gbs_fail(gbs_ctx *ctx, int code, const char *fmt, ...);
 
 // Grow the context workspace to at least `bytes` (synchronises the stream).
 int gbs_ws_ensure(gbs_ctx *ctx, size_t bytes);
+// Grow the auxiliary buffer to at least `bytes`, keeping its first `keep` bytes
+// (synchronises the stream when it grows).
+int gbs_aux_ensure(gbs_ctx *ctx, size_t bytes, size_t keep);
 
 // --- launchers implemented in the kernel translation units ---------------
 int launch_build_state(gbs_ctx *ctx, int M, const double *U, const double *r, double eta,
@@ -85,6 +88,13 @@ int approx_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
                 int32_t *status);
 int approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pattern,
                          int n, int order, int precision, int K, double *curves, double *logP, int32_t *status);
+int approx_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats, int n_pat,
+                int order, const double *w, double *dsq, double *logP, int32_t *status);
+// dL/dsigma_Q = -1/2 (sum w) A - A H A, H the per-pattern F_p (dense 2n x 2n at stride fst,
+// rows in the order of the clicked modes, x and p interleaved) embedded in 2M x 2M;
+// scratch H, T1, T2 (2M x 2M) and sw (one double)
+int grad_chain_sigma(gbs_ctx *ctx, int M, const double *O, const uint64_t *pats, int n_pat, const double *F,
+                     size_t fst, const double *w, double *H, double *T1, double *T2, double *sw, double *dsq);
 int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                 int n_pat, const double *w, double *dsq, double *logP, int32_t *status);
 int grad_params(gbs_ctx *ctx, int M, const double *U, const double *r, double eta, const double *dsq,

@@ -470,7 +470,7 @@ __global__ void grad_finalize_kernel(int M, const uint64_t *__restrict__ pats, i
 
 // H[i][j] = sum_p F_p at the rows of S_p (patterns in order: deterministic); sumw
 __global__ void grad_scatter_kernel(int M, const uint64_t *__restrict__ pats, int n_pat,
-                                    const double *__restrict__ F, const double *__restrict__ w,
+                                    const double *__restrict__ F, size_t fst, const double *__restrict__ w,
                                     double *__restrict__ H, double *__restrict__ sumw) {
     const int N = 2 * M;
     const int i = blockIdx.y * blockDim.y + threadIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,7 +495,7 @@ __global__ void grad_scatter_kernel(int M, const uint64_t *__restrict__ pats, in
         };
         const int n = __popcll(lo) + __popcll(hi);
         const int D = 2 * n;
-        h += F[(size_t)p * kGD * kGD + (2 * rank(mi) + ai) * D + (2 * rank(mj) + aj)];
+        h += F[(size_t)p * fst + (2 * rank(mi) + ai) * D + (2 * rank(mj) + aj)];
     }
     H[(size_t)i * N + j] = h;
 }
@@ -781,8 +781,14 @@ int grad_sigmaQ(gbs_ctx *ctx, int M, const double *O, const double *logdet, cons
     grad_finalize_kernel<<<n_pat, 256, 0, ctx->stream>>>(M, pats, n_pat, chunk_off, pst, phi_, plo, pT, w, logdet, F,
                                                          logP, status, flags);
     GBS_CUDA(ctx, cudaGetLastError());
+    return grad_chain_sigma(ctx, M, O, pats, n_pat, F, (size_t)kGD * kGD, w, H, T1, T2, sw, dsq);
+}
+
+int grad_chain_sigma(gbs_ctx *ctx, int M, const double *O, const uint64_t *pats, int n_pat, const double *F,
+                     size_t fst, const double *w, double *H, double *T1, double *T2, double *sw, double *dsq) {
+    const int N = 2 * M;
     dim3 blk(16, 16), grd((N + 15) / 16, (N + 15) / 16);
-    grad_scatter_kernel<<<grd, blk, 0, ctx->stream>>>(M, pats, n_pat, F, w, H, sw);
+    grad_scatter_kernel<<<grd, blk, 0, ctx->stream>>>(M, pats, n_pat, F, fst, w, H, sw);
     grad_matmul_kernel<<<grd, blk, 0, ctx->stream>>>(N, H, 0, O, 1, T1);    // H A
     grad_matmul_kernel<<<grd, blk, 0, ctx->stream>>>(N, O, 1, T1, 0, T2);   // A (H A)
     grad_sigma_kernel<<<grd, blk, 0, ctx->stream>>>(N, O, T2, sw, dsq);
