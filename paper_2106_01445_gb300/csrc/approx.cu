@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(kSumThreads) approx_sum_kernel(int n_pat, cons
 //             embedded inverse is G - G_{.W} G_WW^-1 G_{W.} (zero on the rows of W), so unit
 //             (S, t_l) adds Re(-1/2 t (s G - G K G)) to dlog P / dA_S, with
 //             s = sum_w cbar_w D_w(t) and K = sum_{W, |W| <= j} cbar_|W| Z_{S\W}(t) embed(G_WW^-1).
-// K is built one 2 x 2 mode block (a, b) per thread (no atomics, a fixed summation order):
+// K is built one 2 x 2 mode block (a, b) per warp (no atomics, a fixed summation order):
 // every W holding a and b is V + {a, b} with V over the other modes; eliminating V first
 // leaves on the rows of a and b the Schur complement of V in G_WW, whose inverse is the
 // (a, b) block of G_WW^-1 and whose pivots complete det(G_WW).
@@ -1067,6 +1067,28 @@ __device__ __forceinline__ cx<double> schur_tail(const cx<double> *__restrict__ 
     return f;
 }
 
+// C(o, v) for v <= 3
+__device__ __forceinline__ int binom_small(int o, int v) {
+    return v == 0 ? 1 : v == 1 ? o : v == 2 ? o * (o - 1) / 2 : o * (o - 1) * (o - 2) / 6;
+}
+// the r-th pair i1 < i2 in colex order (i2 the largest with C(i2, 2) <= r); FP32 estimate,
+// corrected exactly in integers
+__device__ __forceinline__ void unrank_pair(int r, int &i1, int &i2) {
+    int c = (int)sqrtf(2.0f * (float)r);
+    while ((c + 1) * c / 2 <= r) ++c;
+    while (c * (c - 1) / 2 > r) --c;
+    i2 = c;
+    i1 = r - c * (c - 1) / 2;
+}
+// the r-th triple i1 < i2 < i3 in colex order
+__device__ __forceinline__ void unrank_triple(int r, int &i1, int &i2, int &i3) {
+    int c = (int)cbrtf(6.0f * (float)r);
+    while ((c + 1) * c * (c - 1) / 6 <= r) ++c;
+    while (c * (c - 1) * (c - 2) / 6 > r) --c;
+    i3 = c;
+    unrank_pair(r - c * (c - 1) * (c - 2) / 6, i1, i2);
+}
+
 // W = V + {a}: adds wz Z-factor det(G_WW)^-1/2 [G_WW^-1]_aa to the diagonal block (k00, k01, k11)
 template <int NV>
 __device__ __forceinline__ void diag_leaf(const cx<double> *__restrict__ Gs, int N, const int (&m)[NV + 1],
@@ -1114,8 +1136,8 @@ __device__ __forceinline__ void off_leaf(const cx<double> *__restrict__ Gs, int 
 }
 
 // one CTA per (pattern, chunk of its contour points): per point t_l the inverse G (the
-// forward's sweep), K block by block, then Re(-1/2 t (s G - G K G)) added to the chunk's
-// own slot (packed upper triangle of 2n x 2n; every entry has one owner thread, so the
+// forward's sweep), K block by block (a warp per block), then Re(-1/2 t (s G - G K G)) added to
+// the chunk's own slot (packed upper triangle of 2n x 2n; every entry has one owner thread, so the
 // sums over l are in a fixed order)
 __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel(
     int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int order, int chunks_per,
@@ -1125,7 +1147,7 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
     __shared__ int modes[128];
     __shared__ int s_bad;
     __shared__ double s_zs[2];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const int p = blockIdx.x / chunks_per, c = blockIdx.x - p * chunks_per;
     const int n = pl.pat_n[p], L = pl.pat_L[p];
     if (n <= 0 || L <= 0 || *pl.overflow) return;
@@ -1165,82 +1187,82 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
             sl = sl + cb[w] * mk<double>(pl.unit_D[uo + 2 * w], pl.unit_D[uo + 2 * w + 1]);
         }
         const cx<double> zs = mk<double>(s_zs[0], s_zs[1]);
-        for (int blk = t; blk < nb; blk += kMinorThreads) {
+        // one 2 x 2 block (a, b) per warp at a time; its lanes split the groups W = V + {a, b}:
+        // V over the other modes, sizes ascending and each size in colex order (neighbouring
+        // lanes mostly share the size, so the leaf code rarely diverges), partial sums met in
+        // a fixed shuffle tree
+        for (int blk = t >> 5; blk < nb; blk += kMinorThreads / 32) {
             int a = 0, rem = blk;
             while (rem >= n - a) { rem -= n - a; ++a; }
             const int b = a + rem;
+            const bool dg = a == b;
+            const int others = dg ? n - 1 : n - 2, base = dg ? 1 : 2;   // |W| = |V| + base
+            const int vmax = order - base < others ? order - base : others;
+            int cnt[4], total = 0;
+            for (int v = 0; v < 4; ++v) {
+                cnt[v] = v <= vmax ? binom_small(others, v) : 0;
+                total += cnt[v];
+            }
             const cx<double> z0 = mk<double>(0.0, 0.0);
-            if (a == b) {
-                cx<double> k00 = z0, k01 = z0, k11 = z0;
-                {
-                    const int m0[1] = {a};
-                    diag_leaf<0>(Gs, N, m0, cb[1] * zs, k00, k01, k11, bad);
+            cx<double> acc[4] = {z0, z0, z0, z0};
+            for (int q = lane; q < total; q += 32) {
+                int v = 0, r = q;
+                while (r >= cnt[v]) { r -= cnt[v]; ++v; }
+                int x[3] = {r, 0, 0};
+                if (v == 2) unrank_pair(r, x[0], x[1]);
+                else if (v == 3) unrank_triple(r, x[0], x[1], x[2]);
+                // ranks among the other modes -> modes (a, then b, skipped)
+                for (int i = 0; i < v; ++i) {
+                    int y = x[i];
+                    if (y >= a) ++y;
+                    if (!dg && y >= b) ++y;
+                    x[i] = y;
                 }
-                if (order >= 2) {
-                    const cx<double> wz = cb[2] * zs;
-                    for (int i1 = 0; i1 < n; ++i1) {
-                        if (i1 == a) continue;
-                        const int m1[2] = {i1, a};
-                        diag_leaf<1>(Gs, N, m1, wz, k00, k01, k11, bad);
+                const cx<double> wz = cb[v + base] * zs;
+                if (dg) {
+                    if (v == 0) {
+                        const int m[1] = {a};
+                        diag_leaf<0>(Gs, N, m, wz, acc[0], acc[1], acc[2], bad);
+                    } else if (v == 1) {
+                        const int m[2] = {x[0], a};
+                        diag_leaf<1>(Gs, N, m, wz, acc[0], acc[1], acc[2], bad);
+                    } else if (v == 2) {
+                        const int m[3] = {x[0], x[1], a};
+                        diag_leaf<2>(Gs, N, m, wz, acc[0], acc[1], acc[2], bad);
+                    } else {
+                        const int m[4] = {x[0], x[1], x[2], a};
+                        diag_leaf<3>(Gs, N, m, wz, acc[0], acc[1], acc[2], bad);
+                    }
+                } else {
+                    if (v == 0) {
+                        const int m[2] = {a, b};
+                        off_leaf<0>(Gs, N, m, wz, acc, bad);
+                    } else if (v == 1) {
+                        const int m[3] = {x[0], a, b};
+                        off_leaf<1>(Gs, N, m, wz, acc, bad);
+                    } else {
+                        const int m[4] = {x[0], x[1], a, b};
+                        off_leaf<2>(Gs, N, m, wz, acc, bad);
                     }
                 }
-                if (order >= 3) {
-                    const cx<double> wz = cb[3] * zs;
-                    for (int i1 = 0; i1 < n; ++i1) {
-                        if (i1 == a) continue;
-                        for (int i2 = i1 + 1; i2 < n; ++i2) {
-                            if (i2 == a) continue;
-                            const int m2[3] = {i1, i2, a};
-                            diag_leaf<2>(Gs, N, m2, wz, k00, k01, k11, bad);
-                        }
-                    }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                for (int off = 16; off; off >>= 1) {
+                    acc[i].re += __shfl_xor_sync(0xffffffffu, acc[i].re, off);
+                    acc[i].im += __shfl_xor_sync(0xffffffffu, acc[i].im, off);
                 }
-                if (order >= 4) {
-                    const cx<double> wz = cb[4] * zs;
-                    for (int i1 = 0; i1 < n; ++i1) {
-                        if (i1 == a) continue;
-                        for (int i2 = i1 + 1; i2 < n; ++i2) {
-                            if (i2 == a) continue;
-                            for (int i3 = i2 + 1; i3 < n; ++i3) {
-                                if (i3 == a) continue;
-                                const int m3[4] = {i1, i2, i3, a};
-                                diag_leaf<3>(Gs, N, m3, wz, k00, k01, k11, bad);
-                            }
-                        }
-                    }
+            if (lane == 0) {
+                if (dg) {
+                    Kp[pidx(N, 2 * a, 2 * a)] = acc[0];
+                    Kp[pidx(N, 2 * a, 2 * a + 1)] = acc[1];
+                    Kp[pidx(N, 2 * a + 1, 2 * a + 1)] = acc[2];
+                } else {
+                    Kp[pidx(N, 2 * a, 2 * b)] = acc[0];
+                    Kp[pidx(N, 2 * a, 2 * b + 1)] = acc[1];
+                    Kp[pidx(N, 2 * a + 1, 2 * b)] = acc[2];
+                    Kp[pidx(N, 2 * a + 1, 2 * b + 1)] = acc[3];
                 }
-                Kp[pidx(N, 2 * a, 2 * a)] = k00;
-                Kp[pidx(N, 2 * a, 2 * a + 1)] = k01;
-                Kp[pidx(N, 2 * a + 1, 2 * a + 1)] = k11;
-            } else {
-                cx<double> ko[4] = {z0, z0, z0, z0};
-                if (order >= 2) {
-                    const int m0[2] = {a, b};
-                    off_leaf<0>(Gs, N, m0, cb[2] * zs, ko, bad);
-                }
-                if (order >= 3) {
-                    const cx<double> wz = cb[3] * zs;
-                    for (int i1 = 0; i1 < n; ++i1) {
-                        if (i1 == a || i1 == b) continue;
-                        const int m1[3] = {i1, a, b};
-                        off_leaf<1>(Gs, N, m1, wz, ko, bad);
-                    }
-                }
-                if (order >= 4) {
-                    const cx<double> wz = cb[4] * zs;
-                    for (int i1 = 0; i1 < n; ++i1) {
-                        if (i1 == a || i1 == b) continue;
-                        for (int i2 = i1 + 1; i2 < n; ++i2) {
-                            if (i2 == a || i2 == b) continue;
-                            const int m2[4] = {i1, i2, a, b};
-                            off_leaf<2>(Gs, N, m2, wz, ko, bad);
-                        }
-                    }
-                }
-                Kp[pidx(N, 2 * a, 2 * b)] = ko[0];
-                Kp[pidx(N, 2 * a, 2 * b + 1)] = ko[1];
-                Kp[pidx(N, 2 * a + 1, 2 * b)] = ko[2];
-                Kp[pidx(N, 2 * a + 1, 2 * b + 1)] = ko[3];
             }
         }
         __syncthreads();
