@@ -275,6 +275,36 @@ class Context:
         return v.value
 
 
+def grad_sharded(ctx, O: torch.Tensor, logdet: torch.Tensor, patterns, w, order: int = 0, group=None):
+    """dL/dsigma_Q for L = sum_p w_p log P_p over a batch shared by the ranks of a
+    torch.distributed process group (NCCL for CUDA tensors): rank k evaluates
+    patterns k, k + N, k + 2N, ... (round robin, so that the pattern sizes, and with
+    them the work, spread evenly) with ctx.grad (order 0) or ctx.grad_approx (order
+    1..4), and one all-reduce (sum) of the 2M x 2M result combines the ranks: the
+    gradient is linear in w, its -1/2 (sum w) A term included.  Without an
+    initialised process group it is the one-rank case.  Returns (dL/dsigma_Q, this
+    rank's pattern indices, their log P, their status)."""
+    import torch.distributed as dist
+    dist_on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size(group) if dist_on else 1
+    rank = dist.get_rank(group) if dist_on else 0
+    pats = patterns_tensor(patterns, O.device)
+    wt = _dev_f64(w, O.device)
+    idx = torch.arange(rank, pats.shape[0], world, device=O.device)
+    if idx.numel():
+        if order == 0:
+            dsq, logP, status = ctx.grad(O, logdet, pats[idx], wt[idx])
+        else:
+            dsq, logP, status = ctx.grad_approx(O, logdet, pats[idx], wt[idx], order)
+    else:
+        dsq = torch.zeros_like(O)
+        logP = torch.empty(0, dtype=torch.float64, device=O.device)
+        status = torch.empty(0, dtype=torch.int32, device=O.device)
+    if world > 1:
+        dist.all_reduce(dsq, op=dist.ReduceOp.SUM, group=group)
+    return dsq, idx, logP, status
+
+
 def patterns_numpy(t: torch.Tensor) -> np.ndarray:
     """(n, 2) uint64 numpy array from a device pattern tensor."""
     return t.detach().cpu().numpy().view(np.uint64)

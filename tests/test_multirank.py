@@ -1,6 +1,8 @@
-"""The N > 1 host path of bench.py on two gloo ranks (CPU): each rank's shard of the
-weak-scaling batch, and the reductions that make the whole job's number (the slowest
-rank's time, the sum of the ranks' work)."""
+"""The N > 1 host paths on two gloo ranks (CPU): bench.py's shard of the weak-scaling
+batch and the reductions that make the whole job's number (the slowest rank's time, the
+sum of the ranks' work); and the data-parallel gradient (api.grad_sharded: round-robin
+shards, one all-reduce of dL/dsigma_Q), with the per-rank gradient supplied by the
+oracle in place of the GPU context."""
 import os
 import socket
 
@@ -55,3 +57,82 @@ def test_two_ranks_shard_and_reduce():
     for k in range(world):
         assert got[k][2] == 3.0                                   # the slowest rank's time
         assert got[k][3] == float(got[0][1].sum() + got[1][1].sum())  # the job's work
+
+
+class _OracleCtx:
+    """Stands in for the GPU context in grad_sharded: the same grad / grad_approx calls,
+    answered by the oracle on the CPU."""
+
+    def __init__(self, state):
+        self.state = state
+
+    def grad(self, O, logdet, pats, w):
+        import torch
+        from oracle import grad as og
+        from paper_2106_01445_gb300.api import patterns_numpy
+        d = og.grad_sigmaQ(self.state, patterns_numpy(pats), w.numpy())
+        return torch.from_numpy(d), torch.zeros(len(pats), dtype=torch.float64), torch.zeros(len(pats),
+                                                                                             dtype=torch.int32)
+
+    def grad_approx(self, O, logdet, pats, w, order):
+        import torch
+        from oracle import grad as og
+        from paper_2106_01445_gb300.api import patterns_numpy
+        d, lp = og.grad_sigmaQ_approx(self.state, patterns_numpy(pats), w.numpy(), order)
+        return torch.from_numpy(d), torch.from_numpy(lp), torch.zeros(len(pats), dtype=torch.int32)
+
+
+def _grad_case():
+    import oracle
+    M = 8
+    U = g.haar_unitary(M, 6)
+    r = g.squeezing(M, 4, 0.6, 1.0, 6)
+    st = oracle.build_state(U, r, 0.7)
+    pats = g.gen_patterns(6, M, 1, 5, 7)          # 7 patterns: uneven shards over 2 ranks
+    w = np.linspace(-1.0, 1.5, 7)
+    return st, pats, w
+
+
+def _grad_rank(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2106_01445_gb300.api import grad_sharded
+        st, pats, w = _grad_case()
+        out = {}
+        for order in (0, 2):
+            dsq, idx, _, _ = grad_sharded(_OracleCtx(st), torch.from_numpy(st.O), torch.tensor([st.logdet]),
+                                          pats, w, order=order)
+            out[order] = (dsq.numpy(), idx.numpy())
+        q.put((rank, out))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gradient_all_reduce():
+    from oracle import grad as og
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_rank, args=(k, world, port, q)) for k in range(world)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in range(world):
+        rank, out = q.get(timeout=300)
+        got[rank] = out
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    st, pats, w = _grad_case()
+    full = {0: og.grad_sigmaQ(st, pats, w), 2: og.grad_sigmaQ_approx(st, pats, w, 2)[0]}
+    for order in (0, 2):
+        # round-robin shards: every pattern on exactly one rank
+        assert sorted(np.concatenate([got[0][order][1], got[1][order][1]]).tolist()) == list(range(len(pats)))
+        for k in range(world):
+            d = got[k][order][0]
+            assert np.abs(d - full[order]).max() < 1e-12 * np.abs(full[order]).max(), (order, k)
