@@ -1136,7 +1136,7 @@ __device__ __forceinline__ void off_leaf(const cx<double> *__restrict__ Gs, int 
 }
 
 // one CTA per (pattern, chunk of its contour points): per point t_l the inverse G (the
-// forward's sweep), K block by block (a warp per block), then Re(-1/2 t (s G - G K G)) added to
+// forward's sweep), K block by block (a thread or a warp per block), then Re(-1/2 t (s G - G K G)) added to
 // the chunk's own slot (packed upper triangle of 2n x 2n; every entry has one owner thread, so the
 // sums over l are in a fixed order)
 __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel(
@@ -1147,7 +1147,7 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
     __shared__ int modes[128];
     __shared__ int s_bad;
     __shared__ double s_zs[2];
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x;
     const int p = blockIdx.x / chunks_per, c = blockIdx.x - p * chunks_per;
     const int n = pl.pat_n[p], L = pl.pat_L[p];
     if (n <= 0 || L <= 0 || *pl.overflow) return;
@@ -1187,12 +1187,19 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
             sl = sl + cb[w] * mk<double>(pl.unit_D[uo + 2 * w], pl.unit_D[uo + 2 * w + 1]);
         }
         const cx<double> zs = mk<double>(s_zs[0], s_zs[1]);
-        // one 2 x 2 block (a, b) per warp at a time; its lanes split the groups W = V + {a, b}:
-        // V over the other modes, sizes ascending and each size in colex order (neighbouring
-        // lanes mostly share the size, so the leaf code rarely diverges), partial sums met in
-        // a fixed shuffle tree
-        for (int blk = t >> 5; blk < nb; blk += kMinorThreads / 32) {
-            int a = 0, rem = blk;
+        // one 2 x 2 block (a, b) per segment of gw lanes at a time: a thread at orders <= 2,
+        // where a block holds few groups (an off-diagonal one a single group at order 2), a
+        // warp above.  The segment's lanes split the block's groups W = V + {a, b}: V over the
+        // other modes, sizes ascending and each size in colex order (neighbouring lanes mostly
+        // share the size, so the leaf code rarely diverges); partial sums meet in a fixed
+        // shuffle tree.  Every thread runs every round (the shuffles take the whole warp).
+        const int gw = order <= 2 ? 1 : 32;
+        const int seg = t / gw, sg = t - seg * gw, nseg = kMinorThreads / gw;
+        const int rounds = (nb + nseg - 1) / nseg;
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int blk = rd * nseg + seg;
+            const bool live = blk < nb;
+            int a = 0, rem = live ? blk : 0;
             while (rem >= n - a) { rem -= n - a; ++a; }
             const int b = a + rem;
             const bool dg = a == b;
@@ -1200,12 +1207,12 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
             const int vmax = order - base < others ? order - base : others;
             int cnt[4], total = 0;
             for (int v = 0; v < 4; ++v) {
-                cnt[v] = v <= vmax ? binom_small(others, v) : 0;
+                cnt[v] = live && v <= vmax ? binom_small(others, v) : 0;
                 total += cnt[v];
             }
             const cx<double> z0 = mk<double>(0.0, 0.0);
             cx<double> acc[4] = {z0, z0, z0, z0};
-            for (int q = lane; q < total; q += 32) {
+            for (int q = sg; q < total; q += gw) {
                 int v = 0, r = q;
                 while (r >= cnt[v]) { r -= cnt[v]; ++v; }
                 int x[3] = {r, 0, 0};
@@ -1248,11 +1255,11 @@ __global__ void __launch_bounds__(kMinorThreads, 1) approx_minors_adjoint_kernel
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                for (int off = 16; off; off >>= 1) {
+                for (int off = gw >> 1; off; off >>= 1) {
                     acc[i].re += __shfl_xor_sync(0xffffffffu, acc[i].re, off);
                     acc[i].im += __shfl_xor_sync(0xffffffffu, acc[i].im, off);
                 }
-            if (lane == 0) {
+            if (live && sg == 0) {
                 if (dg) {
                     Kp[pidx(N, 2 * a, 2 * a)] = acc[0];
                     Kp[pidx(N, 2 * a, 2 * a + 1)] = acc[1];
