@@ -77,7 +77,11 @@ int gbs_version(void);
 
 /* Pre-size the workspace for up to n_pat patterns of up to n_max clicks so
  * that later gbs_prob calls within those limits allocate nothing and never
- * synchronise (needed for CUDA-graph capture).  Synchronous. */
+ * synchronise (needed for CUDA-graph capture).  Synchronous.  The reservation
+ * covers the exact sum (order 0).  The approximation, the whole-device
+ * distributions and the gradients may grow the context's buffers, which frees
+ * the ones a graph captured earlier refers to: capture after such calls, or make
+ * them on a second context. */
 int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max);
 
 /* Autotuner (not in the paper): runs the exact sweep of these patterns with every
@@ -238,14 +242,14 @@ int gbs_grad(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
  * and every group minor, through d Z_{S\W}(t)/dA_S = -1/2 t Z_{S\W}(t)
  * (G - G_{.W} G_WW^-1 G_{W.}), G = (I - t O_S)^-1.  The contour radius, the sector
  * range and the order each sector's fit used are those of the forward pass (held
- * fixed: log P is piecewise smooth in them).  Per pattern, O(C(n, j) n^2) work per
- * contour point.  w: n_pat doubles (device).  dsigmaQ: 2M x 2M out (device).  logP,
+ * fixed: log P is piecewise smooth in them).  Per pattern and contour point,
+ * (j + j(j-1)/2) C(n, j) eliminations of at most 8 x 8 plus O(n^3).  w: n_pat doubles (device).  dsigmaQ: 2M x 2M out (device).  logP,
  * status: optional per-pattern outputs of the forward pass (as gbs_prob with
  * GBS_FP64; GBS_E_NOT_SPD also when the adjoint met a non-positive pivot).  A
  * pattern whose status is not GBS_OK or GBS_E_FIT adds nothing to H.  Synchronises
  * (pattern sizes are checked on the host); GBS_E_INVALID for a pattern with more
  * than 48 clicks or a detector >= M, or an order outside 1..4.  May grow the
- * context's buffers: re-capture a CUDA graph of gbs_prob taken before it. */
+ * context's buffers (see gbs_reserve). */
 int gbs_grad_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
                     const uint64_t *patterns, int n_pat, int order, const double *w, double *dsigmaQ,
                     double *logP, int32_t *status);
