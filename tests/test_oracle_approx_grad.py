@@ -71,3 +71,44 @@ def test_empty_pattern_has_only_the_normalisation_term():
     dA, lp = og.grad_sigmaQ_approx(st, pats, [2.0], 3)
     assert abs(lp[0] + 0.5 * st.logdet) < 1e-14
     assert np.max(np.abs(dA + st.A)) < 1e-14       # -1/2 * 2 * A
+
+
+def test_fit_adjoint_against_differences():
+    # d part / d D_w of one fitted sector (order 3 on 6 support points) against central
+    # differences of the fit itself
+    M = 8
+    st = _state(M, 4, 2, 0.7)
+    modes = [0, 1, 3, 4, 6, 7]
+    n, j = len(modes), 3
+    rho = oa.choose_tilt(st.O, M, modes)
+    K = oa.choose_kmax(st.O, M, modes, rho)
+    D = oa.factorial_moment_tables(st.O, M, modes, j, K, rho)
+    k = int(np.argmax(D[0, n:])) + n                     # the heaviest sector that is fitted
+    val, flag, a, J = oa.sector_fit(D[:, k], n, k, j)
+    assert flag == 0 and J == j
+    beta = oa.fit_last_point_adjoint(n, a, J, j)
+    for w in range(j + 1):
+        h = 1e-6 * D[w, k]
+        Dp, Dm = D[:, k].copy(), D[:, k].copy()
+        Dp[w] += h
+        Dm[w] -= h
+        fd = (oa.sector_fit(Dp, n, k, j)[0] - oa.sector_fit(Dm, n, k, j)[0]) / (2 * h)
+        assert abs(fd - beta[w]) < 1e-6 * max(abs(beta).max(), 1e-300), (w, fd, beta[w])
+
+
+def test_series_adjoint_against_differences():
+    # sum_k gam_k d c_k[X] / dX for a symmetric X against central differences
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((6, 6))
+    X = 0.3 * (B + B.T) / np.abs(np.linalg.eigvalsh(B + B.T)).max()
+    gam = rng.standard_normal(12)
+    dX = oa.series_coeffs_adjoint(X, gam)
+    h = 1e-6
+    for i, k in [(0, 0), (1, 4), (5, 2), (3, 3)]:
+        E = np.zeros_like(X)
+        E[i, k] += h
+        if i != k:
+            E[k, i] += h
+        fd = (gam @ oa.series_coeffs(X + E, 11) - gam @ oa.series_coeffs(X - E, 11)) / (2 * h)
+        an = dX[i, k] + (dX[k, i] if i != k else 0.0)
+        assert abs(fd - an) < 1e-8, (i, k, fd, an)
