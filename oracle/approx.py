@@ -22,7 +22,7 @@ the covariance form.  For a click pattern S with n modes:
 4. The all-clicked point v = 0 of every sector is summed:
         P(S) ~ det(sigma_Q)^{-1/2} sum_k exp(-f_k(0)).
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
 * the fit variable is v = n - c (same polynomial family as the click count c);
 * sector k >= 1 lives on v in [max(0, n-k), n-1]; sectors k < n add nothing;
 * the polynomial degree is min(j, |support| - 1), so the fit is exact when
