@@ -57,3 +57,18 @@ def test_null_context_is_rejected(so_path):
     L = _lib.load(so_path)
     assert L.gbs_prob(None, 4, None, None, None, 1, 0, 0, None, None, None, None) == _lib.GBS_E_INVALID
     assert L.gbs_build_state(None, 4, None, None, 1.0, None, None, None, None) == _lib.GBS_E_INVALID
+    assert L.gbs_grad(None, 4, None, None, None, 1, None, None, None, None) == _lib.GBS_E_INVALID
+    assert L.gbs_grad_approx(None, 4, None, None, None, 1, 2, None, None, None, None) == _lib.GBS_E_INVALID
+
+
+def test_missing_library_is_an_error(tmp_path):
+    # no fallback: without libgbs.so the binding refuses to load (the loaded-library
+    # cache is set aside for the check and put back)
+    from paper_2106_01445_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(ImportError):
+            _lib.load(str(tmp_path / "libgbs.so"))
+    finally:
+        _lib._lib = saved
