@@ -38,14 +38,31 @@ METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
 DRAM_TRAFFIC = {"fp32": None, "dd": 222976.0, "fp64": None, "fx": 160256.0}
 UNIT = "subset logdets/s"
+# 32-bit multiply-adds of one fixed-point update entry: two 128 x 128-bit products
+# truncated to their top 128 bits, 23 IMAD each (3 + 5 + 7 + 8 over the four rows)
+FX_IMAD_PER_ENTRY = 46
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
 
 def schur_flops(n: int) -> float:
-    """Algorithmic flops of the include/exclude Schur recursion over n modes:
-    every internal node at depth k includes its next mode with r = n-1-k modes
-    left: pivot det 3, rsqrt 1, inverse 4, tau 1, W = B Q 12 r, rank-2 update
-    4 r (2r + 1); plus one add per leaf."""
+    """Algorithmic flops of the include/exclude Schur recursion over n modes, counted
+    as the method must do them: every internal node at depth k includes its next mode
+    with r = n-1-k modes left, costing u(r) = 8 r^2 + 10 r + 10 (2x2 Cholesky ~10,
+    triangular solve of the 2 x 2r pivot rows ~6r, rank-2 symmetric update of the
+    2r x 2r rest 4r(2r+1)); F(n) = sum_k 2^k u(n-1-k), which tends to 44 flops per
+    subset (8 * 3 + 10 * 1 + 10 * 1, from sum_r r^2/2^(r+1) = 3, sum_r r/2^(r+1) = 1
+    and sum_r 1/2^(r+1) = 1)."""
+    tot = 0.0
+    for k in range(n):
+        r = n - 1 - k
+        tot += (1 << k) * (8 * r * r + 10 * r + 10)
+    return tot
+
+
+def schur_flops_executed(n: int) -> float:
+    """The same recursion counted as the kernels execute it: pivot det 3, rsqrt 1,
+    inverse 4, tau 1, W = B Q 12 r, rank-2 update 4 r (2r + 1), plus one add per leaf
+    (tends to 50 flops per subset)."""
     tot = float(1 << n)
     for k in range(n):
         r = n - 1 - k
@@ -169,37 +186,55 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(U, r, eta, pats, n, budget_s: float = 12.0):
-    """The FP64 oracle as it stands on this host's cores, on a bounded sample of
-    the workload's patterns (in order, until the time budget is used)."""
+def oracle_rate(U, r, eta, pats, n, budget_s: float = 12.0, start: int = 0):
+    """The double-double oracle as it stands on this host's cores: patterns taken in
+    batch order from `start` (wrapping), each one's 2^n subsets split into mask ranges
+    over every core, until the time budget is used.  Returns (subsets/s, detail)."""
     import oracle
     st = oracle.build_state(U, r, eta)
+    nt = oracle.max_threads()
     t0 = time.perf_counter()
-    done, subsets, logp = 0, 0, []
+    done, subsets = 0, 0
     while done < len(pats) and time.perf_counter() - t0 < budget_s:
-        chunk = pats[done:done + 16]
-        res = oracle.prob_exact(st, chunk)
-        logp.append(res["logP"])
-        subsets += int(sum(1 << int(k) for k in n[done:done + len(chunk)]))
-        done += len(chunk)
+        i = (start + done) % len(pats)
+        oracle.subset_sum(st.A, st.M, g.pattern_modes(pats[i]), nchunk=4 * nt, dd=True)
+        subsets += 1 << int(n[i])
+        done += 1
     el = time.perf_counter() - t0
-    return dict(value=subsets / el, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
-                sample="first %d of %d patterns (%d subsets) in %.1f s" % (done, len(pats), subsets, el),
-                patterns=done, logP=np.concatenate(logp) if logp else np.zeros(0))
+    return subsets / el, dict(cores=nt, patterns=done, subsets=subsets, seconds=el)
+
+
+def cpu_baseline(U, r, eta, pats, n, budget_s: float = 12.0):
+    """The oracle on the host cores, on a bounded sample of the workload (the
+    double-double oracle: on these improbable patterns it is the CPU code that meets
+    1e-10 in log P, like the GPU path it is compared with)."""
+    val, d = oracle_rate(U, r, eta, pats, n, budget_s)
+    return dict(value=val, unit=UNIT, cores=d["cores"], kind="oracle",
+                sample="double-double oracle, the first %d of %d patterns in batch order (%d subsets, "
+                       "mask ranges over %d threads) in %.1f s" % (d["patterns"], len(pats), d["subsets"],
+                                                                    d["cores"], d["seconds"]))
 
 
 def run_reference(args):
+    """The oracle on the host cores: each step evaluates the next `per_step` patterns of
+    the batch (rotating) with the double-double oracle, every pattern's subsets split
+    into mask ranges over all cores.  Rank 0 alone runs it."""
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
     c, U, r, pats, n = workload(args.workload, 0, 1)
     import oracle
     st = oracle.build_state(U, r, c.eta)
-    per_step = 4                                   # patterns per step, rotating through the batch
+    nt = oracle.max_threads()
+    per_step = 1
+
     def step(i):
-        sel = [(i * per_step + j) % len(pats) for j in range(per_step)]
-        oracle.prob_exact(st, pats[sel])
-        return int(sum(1 << int(n[s]) for s in sel))
+        tot = 0
+        for j in range(per_step):
+            k = (i * per_step + j) % len(pats)
+            oracle.subset_sum(st.A, st.M, g.pattern_modes(pats[k]), nchunk=4 * nt, dd=True)
+            tot += 1 << int(n[k])
+        return tot
     for i in range(args.warmup):
         step(i)
     t0 = time.perf_counter()
@@ -208,15 +243,40 @@ def run_reference(args):
     val = subsets / el
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2",
             "data": "synthetic", "config": {"workload": c.name, "M": c.M, "n_pat_per_step": per_step,
-                                            "clicks": [c.n_lo, c.n_hi], "eta": c.eta},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "%d patterns per step, rotating through the %d-pattern batch"
-                                       % (per_step, len(pats))},
+                                            "clicks": [c.n_lo, c.n_hi], "eta": c.eta,
+                                            "oracle": "double-double (1e-10 in log P on this workload)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": "%d patterns per step, rotating through the %d-pattern batch; each "
+                                       "pattern's subsets in mask ranges over %d threads"
+                                       % (per_step, len(pats), nt)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def write_detail(args, detail):
+    """The long per-workload study goes to a side file; the headline line stays short."""
+    path = args.detail_out
+    try:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(detail, f, indent=1, default=float)
+        return os.path.relpath(os.path.abspath(path), ROOT)
+    except OSError as e:
+        return "not written: %s" % e
+
+
+def compact(x, digits=5):
+    """Round floats for the headline line (keeps it short)."""
+    if isinstance(x, float):
+        return float("%.*g" % (digits, x)) if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: compact(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, digits) for v in x]
+    return x
 
 
 def run_gpu(args):
@@ -263,6 +323,7 @@ def run_gpu(args):
     subsets = float(sum(2.0 ** k for k in n))
     subsets_all = sum_over_ranks(subsets, world, dev)   # the whole job's units per step
     flops = float(sum(schur_flops(int(k)) for k in n))
+    flops_exec = float(sum(schur_flops_executed(int(k)) for k in n))
     prec = args.precision
 
     def timed(prec, K, W, clocks=None):
@@ -293,39 +354,26 @@ def run_gpu(args):
 
     clocks = ClockSampler(local)
     ms, sweep_ms, launches, ck = timed(prec, args.steps, args.warmup, clocks)
-    # the other precisions, for the comparison (shorter runs)
-    others = {}
-    for other in ("fx", "dd", "fp64", "fp32"):
-        if other == prec:
-            continue
-        Ko = max(3, args.steps // 20)
-        ms_o, sweep_o, launches_o, _ = timed(other, Ko, 2)
-        step(other)
-        torch.cuda.synchronize()
-        others[other] = dict(ms_per_step=ms_o / Ko, kernel_ms=sweep_o / max(launches_o, 1),
-                             value=subsets_all * Ko / (ms_o * 1e-3),
-                             logP=out["logP"].cpu().numpy().copy(),
-                             status=out["status"].cpu().numpy().copy())
-
-    # correctness of this exact launch shape against the oracle (untimed)
+    res_main = None
     step(prec)
     torch.cuda.synchronize()
-    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res_main = {k: v.cpu().numpy().copy() for k, v in out.items()}
+    # the other precisions, for the comparison (shorter runs)
+    others = {}
+    if args.compare:
+        for other in ("fx", "dd", "fp64", "fp32"):
+            if other == prec:
+                continue
+            Ko = max(3, args.steps // 20)
+            ms_o, sweep_o, launches_o, _ = timed(other, Ko, 2)
+            step(other)
+            torch.cuda.synchronize()
+            others[other] = dict(ms_per_step=ms_o / Ko, kernel_ms=sweep_o / max(launches_o, 1),
+                                 value=subsets_all * Ko / (ms_o * 1e-3),
+                                 logP=out["logP"].cpu().numpy().copy(),
+                                 status=out["status"].cpu().numpy().copy())
     value = subsets_all * args.steps / (ms * 1e-3)
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "dd": "f64x2", "fx": "i128"}[prec],
-            "data": "synthetic",
-            "config": {"workload": c.name, "M": c.M, "squeezed": c.K, "r": [c.r_lo, c.r_hi], "eta": c.eta,
-                       "interferometer": c.interferometer, "n_pat": len(pats), "clicks": [c.n_lo, c.n_hi],
-                       "subsets_per_step": subsets_all, "subsets_per_step_per_rank": subsets,
-                       "precision": prec,
-                       "l2": "flushed between timed steps (512 MB write)"},
-            "patterns_per_s": len(pats) * world * args.steps / (ms * 1e-3),
-            "autotune": tuned,
-            "gpu_launches": 4 * args.steps}
     # end to end through the public host-buffer entry point (copies inside the region),
     # every rank at once: the whole job's subsets over the slowest rank's time
     K2 = max(3, min(args.steps, 50))
@@ -335,56 +383,54 @@ def run_gpu(args):
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(K2):
-        hres = ctx.run_host(U, r, c.eta, pats, precision=prec)
+        ctx.run_host(U, r, c.eta, pats, precision=prec)
     el = max_over_ranks(time.perf_counter() - t0, world, dev)
-    line["e2e"] = {"value": subsets_all * K2 / el, "unit": UNIT,
-                   "h2d_bytes_per_step": 16 * M * M + 8 * M + 16 * len(pats),
-                   "d2h_bytes_per_step": len(pats) * (8 + 8 + 8 + 4) + 4}
+    e2e = {"value": subsets_all * K2 / el, "unit": UNIT,
+           "h2d_bytes_per_step": 16 * M * M + 8 * M + 16 * len(pats),
+           "d2h_bytes_per_step": len(pats) * (8 + 8 + 8 + 4) + 4}
     if rank != 0:
         return 0
     # roofline of the dominant kernel (the subset sweep): plain ALU pipes, no tensor
     # cores, no DRAM traffic to speak of.  FP32: algorithmic flops against SMs x 128
     # lanes x 2 x max clock.  FP64: against the measured FP64 FMA loop.  Double-double
-    # and fixed point: against the measured loop of the fused rank-2 update entry
-    # c - w0 b0 - w1 b1 in that arithmetic (4 flops per entry), i.e. the rate the
-    # sweep would reach if every algorithmic flop cost what its main update costs.
+    # and fixed point: against the measured loop of the sweep's own update entry in that
+    # arithmetic (4 flops per entry), i.e. the rate the sweep would reach if every
+    # algorithmic flop cost what its main update costs.
     props = torch.cuda.get_device_properties(dev)
     smax = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6
-    meas = {k: ctx.peak_flops(k) for k in ("fp32", "fp64", "dd", "fx")}
-    peak = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["dd"], "fx": meas["fx"]}[prec]
-    achieved = flops / (sweep_ms / max(launches, 1) * 1e-3)
-    line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get(prec),
-                        "kernel": "sweep_kernel<%s>" % {"fp32": "float", "fp64": "double", "dd": "dd", "fx": "fx"}[prec],
-                        "kernel_ms": sweep_ms / max(launches, 1), "flops_per_launch": flops,
-                        "peak_basis": {"fp32": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
-                                       "fp64": "measured FP64 FMA loop",
-                                       "dd": "measured double-double update-entry loop (4 flops per entry)",
-                                       "fx": "measured fixed-point update-entry loop (4 flops per entry)"}[prec],
-                        "loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()}}
-    line["other_precisions"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
-                                for k, v in others.items()}
-    # each precision's sweep against its own pipe: FP32 (derived peak), FP64 (measured FMA
-    # loop), double-double and fixed point (measured update-entry loops)
+    meas = {k: ctx.peak_flops(k) for k in ("fp32", "fp64", "dd", "fx", "imad")}
     all_peaks = {"fp32": fp32_peak, "fp64": meas["fp64"], "dd": meas["dd"], "fx": meas["fx"]}
-    for k, v in line["other_precisions"].items():
-        ach = flops / (v["kernel_ms"] * 1e-3)
-        v["roofline"] = {"achieved_tflops": ach / 1e12, "peak_tflops": all_peaks[k] / 1e12,
-                         "frac": ach / all_peaks[k]}
-    line["clocks"] = ck
-    # oracle on the host cores: baseline (FP64 oracle as it stands) and the stated
-    # error of every precision against the double-double oracle on a sample
+    peak = all_peaks[prec]
+    kms = sweep_ms / max(launches, 1)
+    achieved = flops / (kms * 1e-3)
+    kname = {"fp32": "float", "fp64": "double", "dd": "dd", "fx": "fx"}[prec]
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": DRAM_TRAFFIC.get(prec),
+                "kernel": "sweep_kernel<%s>" % kname, "kernel_ms": kms, "flops_per_launch": flops,
+                "flop_count": "8r^2+10r+10 per include step (44/subset)",
+                "frac_executed_count": flops_exec / (kms * 1e-3) / peak,
+                "peak_basis": {"fp32": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
+                               "fp64": "measured FP64 FMA loop",
+                               "dd": "measured loop of the sweep's double-double update entry, 4 flops",
+                               "fx": "measured loop of the sweep's fixed-point update entry, 4 flops"}[prec]}
+    if prec == "fx":
+        # the integer pipe: each fixed-point update entry is two truncated 128-bit products of
+        # 23 IMAD each (FX_IMAD_PER_ENTRY); at the measured IMAD issue rate that bounds the
+        # entry rate, and so the sweep's flops, from above
+        imad_bound = meas["imad"] / FX_IMAD_PER_ENTRY * 4.0
+        roofline["int_pipe"] = {"imad_per_s": meas["imad"], "imad_per_entry": FX_IMAD_PER_ENTRY,
+                                "entry_loop_frac_of_imad_bound": meas["fx"] / imad_bound,
+                                "frac_of_imad_bound": achieved / imad_bound}
+    # oracle on the host cores: baseline, and the stated error of every precision
+    # against the double-double oracle on a sample
     cb = cpu_baseline(U, r, c.eta, pats, n, budget_s=args.cpu_budget)
-    cb.pop("patterns")
-    cb.pop("logP")
-    line["cpu_baseline"] = cb
     import oracle
     sample = np.nonzero(n <= args.dd_sample_nmax)[0][: args.dd_sample]
     ref = oracle.prob_exact(oracle.build_state(U, r, c.eta), pats[sample], dd=True)["logP"]
     errs = {}
     allres = dict(others)
-    allres[prec] = dict(logP=res["logP"], status=res["status"])
+    allres[prec] = dict(logP=res_main["logP"], status=res_main["status"])
     for pk, rv in allres.items():
         lp, stt = rv["logP"][sample], rv["status"][sample]
         okm = stt == 0
@@ -392,13 +438,38 @@ def run_gpu(args):
         errs[pk] = {"max_abs_dlogP": float(d.max()) if d.size else None,
                     "median_abs_dlogP": float(np.median(d)) if d.size else None,
                     "status_ok_fraction_all_patterns": float((rv["status"] == 0).mean())}
+    other_prec = {}
+    for k, v in others.items():
+        ach = flops / (v["kernel_ms"] * 1e-3)
+        other_prec[k] = {kk: vv for kk, vv in v.items() if kk not in ("logP", "status")}
+        other_prec[k]["roofline"] = {"achieved_tflops": ach / 1e12, "peak_tflops": all_peaks[k] / 1e12,
+                                     "frac": ach / all_peaks[k]}
+        other_prec[k]["max_abs_dlogP_vs_dd_oracle"] = errs[k]["max_abs_dlogP"]
+    detail = {"workload": c.name, "autotune": tuned, "other_precisions": other_prec,
+              "loop_measured_tflops": {k: v / 1e12 for k, v in meas.items()},
+              "error_vs_oracle": {"reference": "double-double oracle", "patterns_checked": int(sample.size),
+                                  "clicks_checked": [int(n[sample].min()), int(n[sample].max())]
+                                  if sample.size else None, "per_precision": errs}}
     if args.workloads == "all":
-        line["workloads"] = run_workloads(dev, stream, meas, fp32_peak)
-    line["error_vs_oracle"] = {"reference": "double-double oracle",
-                               "patterns_checked": int(sample.size),
-                               "clicks_checked": [int(n[sample].min()), int(n[sample].max())] if sample.size else None,
-                               "per_precision": errs}
-    print(json.dumps(line))
+        detail["workloads"] = run_workloads(dev, stream, meas, fp32_peak)
+    detail["note"] = ("other_precisions: the same batch with the other sweeps; workloads: one pass of "
+                      "the other workloads (timings, rooflines, accuracy against the oracle)")
+    where = write_detail(args, detail)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "dd": "f64x2", "fx": "i128"}[prec],
+            "data": "synthetic",
+            "config": {"workload": c.name, "M": c.M, "squeezed": c.K, "eta": c.eta, "n_pat": len(pats),
+                       "clicks": [c.n_lo, c.n_hi], "subsets_per_step": subsets_all, "precision": prec,
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "patterns_per_s": len(pats) * world * args.steps / (ms * 1e-3),
+            "gpu_launches": 4 * args.steps,
+            "max_abs_dlogP_vs_dd_oracle": errs[prec]["max_abs_dlogP"],
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": ck,
+            "other_precisions_subsets_per_s": {k: v["value"] for k, v in others.items()},
+            "detail": where}
+    print(json.dumps(compact(line)), flush=True)
     return 0
 
 
@@ -717,6 +788,10 @@ def main():
     ap.add_argument("--workloads", choices=["all", "none"], default="all",
                     help="also run one pass of the other four workloads (on rank 0)")
     ap.add_argument("--npat", type=int, default=128)
+    ap.add_argument("--compare", type=int, default=1,
+                    help="also time the other three precisions of the exact sweep (short runs)")
+    ap.add_argument("--detail-out", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
+                    help="side file for the per-workload study (the headline line stays short)")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

@@ -39,7 +39,11 @@ typedef enum {
     GBS_E_NOMEM = 3,       /* workspace too small (reserve more) or allocation failed */
     GBS_E_NONPOSITIVE = 4, /* signed sum T <= its error bound: log P undefined */
     GBS_E_NOT_SPD = 5,     /* a pivot of an SPD factorisation was not positive */
-    GBS_E_TIMEOUT = 6,     /* a bounded device loop ran out of iterations */
+    GBS_E_TIMEOUT = 6,     /* reserved: no entry point of this version returns it.  Every device
+                              loop here is bounded by its own work count (persistent loops end
+                              when their ticket passes the unit count; Newton fits stop after a
+                              fixed number of steps and report GBS_E_FIT), and no kernel waits
+                              on another */
     GBS_E_FIT = 7,         /* approximation: a sector fit fell back to a lower order */
     GBS_E_RANGE = 8        /* GBS_FX: a pivot determinant below 2^-8 or an entry of O beyond
                               4 left the fixed-point range (evaluate in GBS_DD instead) */
@@ -211,7 +215,10 @@ int gbs_approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double 
  * call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the array:
  * calls that overlap on the GPU (other streams, other threads) race and must
- * be serialised by the caller.  No allocation, no synchronisation. */
+ * be serialised by the caller.  precision: GBS_FX, GBS_DD, GBS_FP64 or GBS_FP32_SPLIT
+ * (GBS_AUTO is not taken: its double-double rerun needs buffers of its own); a GBS_FX
+ * pattern outside the fixed-point range reports GBS_E_RANGE and is not rerun, so
+ * evaluate such patterns again with GBS_DD.  No allocation, no synchronisation. */
 int gbs_prob_noalloc(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
                      const uint64_t *patterns, int n_pat, int n_max, int precision, double *logP,
                      double *kappa, double *err_bound, int32_t *status);
@@ -292,10 +299,13 @@ int gbs_timing_read(gbs_ctx *ctx, int reset, double *sweep_ms, long long *sweep_
 /*
  * Peak arithmetic throughput of this GPU at the clocks of the run, in FLOP/s.
  * kind 0 / 1: the FP32 / FP64 FMA pipes from a register-resident dependent-FMA
- * loop (one FMA = 2 FLOP).  kind 2 / 3: the fused Schur-update entry
- * c - w0 b0 - w1 b1 (4 FLOP) in double-double / in 128-bit fixed point, from a
- * loop of independent entries: the ceiling of the sweep in those precisions.
- * Synchronous.  The scratch buffer it writes is the context's own. */
+ * loop (one FMA = 2 FLOP).  kind 2 / 3: the sweep's own fused Schur-update entry
+ * (4 FLOP: c - w0 b0 - w1 b1 in double-double; c + t_i + t_j - (u'_i0 u'_j0 +
+ * u'_i1 u'_j1) with two unsigned 128-bit products in fixed point), from a loop of
+ * independent entries: the ceiling of the sweep in those precisions.  kind 4: 32-bit
+ * integer multiply-adds per second (IMAD, eight independent chains per thread; one
+ * per multiply-add, not 2), the issue rate of the pipe that carries the fixed-point
+ * products.  Synchronous.  The scratch buffer it writes is the context's own. */
 int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops);
 
 #ifdef __cplusplus

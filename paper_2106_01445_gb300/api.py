@@ -268,9 +268,10 @@ class Context:
 
     def peak_flops(self, kind: str = "fp32") -> float:
         """FLOP/s of the FP32 / FP64 FMA loops ("fp32", "fp64") or of the fused
-        Schur-update loops in double-double / fixed point ("dd", "fx")."""
+        Schur-update loops in double-double / fixed point ("dd", "fx"); "imad": 32-bit
+        integer multiply-adds per second."""
         v = ctypes.c_double()
-        code = {"fp32": 0, "fp64": 1, "dd": 2, "fx": 3}[kind]
+        code = {"fp32": 0, "fp64": 1, "dd": 2, "fx": 3, "imad": 4}[kind]
         self._check(self.lib.gbs_peak_flops(self.h, code, ctypes.byref(v)))
         return v.value
 

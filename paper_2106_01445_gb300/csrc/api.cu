@@ -430,7 +430,7 @@ int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_
 }
 
 int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops) {
-    if (!ctx || !flops || kind < 0 || kind > 3) return GBS_E_INVALID;
+    if (!ctx || !flops || kind < 0 || kind > 4) return GBS_E_INVALID;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     return peak_flops(ctx, kind, flops);
 }
