@@ -38,8 +38,8 @@ Readings where the paper is silent:
   stay positive definite (the largest excluded) of log Z_S(rho) - n log rho,
   so that the sectors carrying the all-clicked point sit near the peak of
   c_k rho^k (for improbable patterns they lie far in the upper tail);
-* the sector sum stops at K_max, the first K whose partial sum of c_k rho^k
-  reaches (1 - 1e-14) Z_S(rho);
+* the sector sum stops at K_max, the first K whose tail sum_{k>K} c_k rho^k is
+  below 1e-14 Z_S(rho);
 * a sector whose tilted mass D_0^(k) rho^k is below eps_sector = 1e-12 of the
   largest contributes nothing: such sectors are rounding noise (e.g. the odd
   sectors of a lossless state, exactly zero).
@@ -90,8 +90,8 @@ def _pd_logdet(X: np.ndarray):
     return 2.0 * np.log(np.diag(L)).sum()
 
 
-def choose_tilt(O: np.ndarray, M: int, modes) -> float:
-    """rho = argmin_{rho in RHOS, valid, not the largest valid} log Z_S(rho) - n log rho."""
+def choose_tilt(O: np.ndarray, M: int, modes, rhos=RHOS) -> float:
+    """rho = argmin_{rho in rhos, valid, not the largest valid} log Z_S(rho) - n log rho."""
     rows = sub_rows(modes, M)
     Os = O[np.ix_(rows, rows)]
     n = len(modes)
@@ -99,7 +99,7 @@ def choose_tilt(O: np.ndarray, M: int, modes) -> float:
         return 1.0
     I = np.eye(len(rows))
     valid = []
-    for rho in RHOS:
+    for rho in rhos:
         l_minus = _pd_logdet(I - rho * Os)
         if l_minus is None or (rho > 1.0 and _pd_logdet(I + rho * Os) is None):
             break
@@ -110,7 +110,12 @@ def choose_tilt(O: np.ndarray, M: int, modes) -> float:
 
 
 def choose_kmax(O: np.ndarray, M: int, modes, rho: float = 1.0) -> int:
-    """Smallest K with sum_{k<=K} c_k rho^k >= (1 - TAIL_EPS) Z_S(rho)."""
+    """Smallest K whose tail sum_{k>K} c_k rho^k is below TAIL_EPS Z_S(rho).
+
+    The tail is summed from the series itself (every c_k rho^k is positive), far
+    enough out that the terms left are below 1e-30 of Z_S(rho); Z_S(rho) minus a
+    partial sum would cancel to the rounding of Z_S(rho), ~1e-16 relative, which is
+    too close to TAIL_EPS to decide K reliably."""
     rows = sub_rows(modes, M)
     Os = O[np.ix_(rows, rows)] * rho
     if Os.size == 0:
@@ -119,10 +124,9 @@ def choose_kmax(O: np.ndarray, M: int, modes, rho: float = 1.0) -> int:
     K = 64
     while True:
         c = series_coeffs(Os, K)
-        cs = np.cumsum(c)
-        hit = np.nonzero(cs >= (1.0 - TAIL_EPS) * total)[0]
-        if hit.size:
-            return int(hit[0])
+        if c[-1] < 1e-30 * total and c[-1] <= c[-2]:
+            tail = np.cumsum(c[::-1])[::-1]            # tail[k] = sum_{k' >= k} c_k'
+            return int(np.nonzero(tail[1:] < TAIL_EPS * total)[0][0])
         if K > 1 << 16:
             raise RuntimeError("sector series does not converge")
         K *= 2
@@ -156,9 +160,11 @@ def raw_moments(Dk: np.ndarray, j: int) -> np.ndarray:
                      for i in range(j + 1)])
 
 
-def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter: int = 200):
+def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter: int = 200,
+               stall_accept: float = 1e3):
     """Coefficients a of q(x) = exp(-sum_i a_i x^i) on the support points x with
-    sum_x x^i q(x) = m_i (i = 0..J, m_0 = 1).  Returns (a, converged)."""
+    sum_x x^i q(x) = m_i (i = 0..J, m_0 = 1).  Returns (a, converged).  A fit whose line
+    search stalls stands if its residual is within stall_accept * tol."""
     J = m.size - 1
     X = np.vander(support, J + 1, increasing=True)            # X[s, i] = x_s^i
     a = np.zeros(J + 1)
@@ -198,13 +204,13 @@ def maxent_fit(support: np.ndarray, m: np.ndarray, tol: float = 1e-13, max_iter:
                 # no further decrease: the moments sit on the boundary of the moment
                 # cone (a support point of vanishing weight) up to their rounding;
                 # the fit stands if the residual is at that level
-                return a, bool(gmax <= 1e3 * tol)
+                return a, bool(gmax <= stall_accept * tol)
         a, f = an, fn
     q = np.exp(-X @ a)
-    return a, bool(np.max(np.abs(m - X.T @ q)) <= 1e3 * tol)
+    return a, bool(np.max(np.abs(m - X.T @ q)) <= stall_accept * tol)
 
 
-def sector_fit(Dk: np.ndarray, n: int, k: int, j: int):
+def sector_fit(Dk: np.ndarray, n: int, k: int, j: int, stall_accept: float = 1e3):
     """The fit behind sector_last_point: (value, flag, a, J) with a the coefficients of
     the normalised fit exp(-sum_i a_i x^i), x = v / n, of degree J (None when no fit)."""
     if k < n or Dk[0] <= 0.0:
@@ -217,30 +223,33 @@ def sector_fit(Dk: np.ndarray, n: int, k: int, j: int):
     x = v / n
     for J in range(Jmax, -1, -1):
         mnorm = np.array([mu[i] / n ** i for i in range(J + 1)]) / mu[0]
-        a, ok = maxent_fit(x, mnorm)
+        a, ok = maxent_fit(x, mnorm, stall_accept=stall_accept)
         if ok:
             return mu[0] * math.exp(-a[0]), 0 if J == Jmax else 1, a, J
     return 0.0, 2, None, -1
 
 
-def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int):
+def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int, stall_accept: float = 1e3):
     """Estimate of q_k(v = 0) from the factorial moments D_0..D_j of sector k.
 
     Returns (value, flag) with flag 0 = fitted at order j' = min(j, |V|-1),
     1 = fell back to a lower order, 2 = no fit possible (value 0)."""
-    val, flag, _, _ = sector_fit(Dk, n, k, j)
+    val, flag, _, _ = sector_fit(Dk, n, k, j, stall_accept)
     return val, flag
 
 
 def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
-                   K: int | None = None, eps_sector: float = EPS_SECTOR, rho: float | None = None):
+                   K: int | None = None, eps_sector: float = EPS_SECTOR, rho: float | None = None,
+                   rhos=RHOS, flag_share: float = FLAG_SHARE, stall_accept: float = 1e3):
     """log P(S) by the order-j approximation.  Returns (logP, info dict).  K and rho
-    default to choose_kmax and choose_tilt; fixing them makes log P a smooth function
-    of O (for derivatives by differences)."""
+    default to choose_kmax and choose_tilt (over the radii rhos); fixing them makes log P
+    a smooth function of O (for derivatives by differences).  eps_sector, flag_share and
+    stall_accept are the readings' constants (the tests vary them to show log P does not
+    depend on them)."""
     modes = list(modes)
     n = len(modes)
     if rho is None:
-        rho = choose_tilt(O, M, modes)
+        rho = choose_tilt(O, M, modes, rhos)
     if K is None:
         K = choose_kmax(O, M, modes, rho)
     D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
@@ -250,7 +259,7 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
     for k in range(K + 1):
         if D[0, k] < floor:
             continue
-        val, fl = sector_last_point(D[:, k], n, k, j)
+        val, fl = sector_last_point(D[:, k], n, k, j, stall_accept)
         parts[k] = val
         fell[k] = fl > 0
     # sum_k parts[k] rho^{-k}, in logs (rho^{-k} can leave the double range)
@@ -262,7 +271,7 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
         w = np.exp(lg - top)
         logsum = top + math.log(w.sum())
         # a fallback is reported when the sectors that fell back carry >= FLAG_SHARE of the sum
-        if w[fell[nz]].sum() >= FLAG_SHARE * w.sum():
+        if w[fell[nz]].sum() >= flag_share * w.sum():
             flags = 1
     else:
         logsum = -math.inf
