@@ -746,6 +746,11 @@ def run_profile_case(args):
     from paper_2106_01445_gb300 import build as b
     b.build()
     from paper_2106_01445_gb300.api import Context
+    if args.profile == "peak":
+        ctx = Context(0)
+        for k in ("fx", "imad", "fp64", "fp32", "dd"):
+            print("peak loop %s: %.4g per s" % (k, ctx.peak_flops(k)))
+        return 0
     if args.profile == "grad":
         c = g.CONFIGS["m32_grad"]
         ctx = Context(0)
@@ -782,7 +787,7 @@ def main():
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["sweep", "approx", "grad"], default=None,
+    ap.add_argument("--profile", choices=["sweep", "approx", "grad", "peak"], default=None,
                     help="run one kernel path twice (for ncu) instead of the benchmark")
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--workloads", choices=["all", "none"], default="all",

@@ -203,6 +203,31 @@ int gbs_approx_sector_curves(gbs_ctx *ctx, int M, const double *O, const double 
                              const uint64_t *pattern, int n, int order, int precision, int K, double *curves,
                              double *logP, int32_t *status);
 
+/* One batch split across GPUs (not in the paper; Methods, "Probability of any sample" is
+ * the sum these slices partition).  The exact sum's work units -- (pattern, include /
+ * exclude choice of the pattern's first modes), each 2^(s + 9) subsets in GBS_FX, 2^(s + 10)
+ * or more in the other precisions once n is large enough -- are numbered over the batch
+ * (patterns by decreasing n); slice `part` of `nparts` is the units
+ * [U part / nparts, U (part + 1) / nparts) of the U in all, so equal unit counts give
+ * equal work and a large pattern may be cut by its subset prefix.  gbs_prob_partial sweeps
+ * one slice and writes, per pattern, the slice's partial sum as partial[3p..3p+2] =
+ * (T_hi, T_lo, sum of |terms|) (zeros where the slice holds none of the pattern's units) and
+ * pflag[p] (-1 invalid pattern; else bits 1 a pivot was not positive, 2 a pivot left the
+ * fixed-point range, 4 the batch did not fit the reserved workspace).  Every rank runs it on
+ * the same batch with its own part; the slices' outputs (24 + 4 bytes per pattern) are then
+ * gathered in part order and gbs_prob_combine sums them per pattern in that order (TwoSum)
+ * and returns what gbs_prob returns for the batch: logP, kappa, err_bound, status (outputs
+ * may be NULL except logP).  partials: nparts x n_pat x 3 doubles, pflags: nparts x n_pat
+ * int32, part-major (device).  precision: GBS_FX, GBS_DD, GBS_FP64 or GBS_FP32_SPLIT, the
+ * same in both calls (GBS_FX patterns out of range come back GBS_E_RANGE: run them again
+ * in GBS_DD).  gbs_prob_partial may synchronise and grow the workspace as gbs_prob does.
+ * Errors: GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM. */
+int gbs_prob_partial(gbs_ctx *ctx, int M, const double *O, const uint64_t *patterns, int n_pat, int precision,
+                     int part, int nparts, double *partial, int32_t *pflag);
+int gbs_prob_combine(gbs_ctx *ctx, const double *logdet_sigmaQ, const uint64_t *patterns, int n_pat, int precision,
+                     int nparts, const double *partials, const int32_t *pflags, double *logP, double *kappa,
+                     double *err_bound, int32_t *status);
+
 /* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
  * has no counterpart: this serves callers that cannot call cudaMalloc (code
  * running under another owner's stream capture, processes whose device memory

@@ -36,6 +36,8 @@ SIGNATURES = {
     "gbs_prob": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_run_host": (_i, [_vp, _i, _vp, _vp, _d, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "gbs_prob_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "gbs_prob_partial": (_i, [_vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp]),
+    "gbs_prob_combine": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gbs_gen_patterns": (_i, [_vp, _u64, _u32, _i, _i, _i, _i, _vp]),
     "gbs_grad": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gbs_grad_approx": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp]),

@@ -177,6 +177,36 @@ class Context:
                                               _ptr(out["err_bound"]), _ptr(out["status"])))
         return out
 
+    def prob_partial(self, O: torch.Tensor, patterns, part: int, nparts: int, precision="fx"):
+        """Slice `part` of `nparts` of the batch's exact-sum work units: per pattern the
+        slice's partial sum (T_hi, T_lo, sum |terms|) as an (n_pat, 3) tensor and its flags
+        (n_pat int32)."""
+        M = O.shape[0] // 2
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        partial = torch.empty((n_pat, 3), dtype=torch.float64, device=self.device)
+        pflag = torch.empty(n_pat, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gbs_prob_partial(self.h, M, _ptr(O), _ptr(pats), n_pat, PRECISIONS[precision],
+                                              part, nparts, _ptr(partial), _ptr(pflag)))
+        return partial, pflag
+
+    def prob_combine(self, logdet: torch.Tensor, patterns, partials: torch.Tensor, pflags: torch.Tensor,
+                     precision="fx"):
+        """The slices' partial sums (nparts, n_pat, 3) and flags (nparts, n_pat), in part
+        order, combined into what prob() returns for the batch."""
+        pats = patterns_tensor(patterns, self.device)
+        n_pat = pats.shape[0]
+        parts = partials.to(device=self.device, dtype=torch.float64).contiguous()
+        flags = pflags.to(device=self.device, dtype=torch.int32).contiguous()
+        out = dict(logP=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                   kappa=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                   err_bound=torch.empty(n_pat, dtype=torch.float64, device=self.device),
+                   status=torch.empty(n_pat, dtype=torch.int32, device=self.device))
+        self._check(self.lib.gbs_prob_combine(self.h, _ptr(logdet), _ptr(pats), n_pat, PRECISIONS[precision],
+                                              parts.shape[0], _ptr(parts), _ptr(flags), _ptr(out["logP"]),
+                                              _ptr(out["kappa"]), _ptr(out["err_bound"]), _ptr(out["status"])))
+        return out
+
     def run_host(self, U, r, eta: float, patterns, order: int = 0, precision="auto", out=None):
         """The whole path from host (numpy) buffers; returns numpy arrays."""
         U = np.ascontiguousarray(U, dtype=np.complex128)
@@ -304,6 +334,30 @@ def grad_sharded(ctx, O: torch.Tensor, logdet: torch.Tensor, patterns, w, order:
     if world > 1:
         dist.all_reduce(dsq, op=dist.ReduceOp.SUM, group=group)
     return dsq, idx, logP, status
+
+
+def prob_sharded(ctx, O: torch.Tensor, logdet: torch.Tensor, patterns, precision="fx", group=None):
+    """Exact log P of one batch evaluated by all ranks of a torch.distributed process group
+    together (the strong-scaling split): rank k sweeps slice k of N of the batch's work
+    units with ctx.prob_partial (equal unit counts, a large pattern cut by its subset
+    prefix where the slices fall), one all_gather exchanges the slices' per-pattern
+    partial sums (24 bytes and one flag per pattern and rank), and every rank combines
+    them in rank order with ctx.prob_combine, so every rank holds the same result,
+    bit for bit.  Without an initialised process group it is the one-rank case."""
+    import torch.distributed as dist
+    dist_on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size(group) if dist_on else 1
+    rank = dist.get_rank(group) if dist_on else 0
+    partial, pflag = ctx.prob_partial(O, patterns, rank, world, precision=precision)
+    if world > 1:
+        parts = [torch.empty_like(partial) for _ in range(world)]
+        flags = [torch.empty_like(pflag) for _ in range(world)]
+        dist.all_gather(parts, partial, group=group)
+        dist.all_gather(flags, pflag, group=group)
+        partials, pflags = torch.stack(parts), torch.stack(flags)
+    else:
+        partials, pflags = partial[None], pflag[None]
+    return ctx.prob_combine(logdet, patterns, partials, pflags, precision=precision)
 
 
 def patterns_numpy(t: torch.Tensor) -> np.ndarray:

@@ -315,6 +315,35 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
                        logP, kappa, err_bound, status);
 }
 
+int gbs_prob_partial(gbs_ctx *ctx, int M, const double *O, const uint64_t *patterns, int n_pat, int precision,
+                     int part, int nparts, double *partial, int32_t *pflag) {
+    if (!ctx) return GBS_E_INVALID;
+    if (M < 1 || M > 128 || n_pat < 0 || !O || (n_pat && (!patterns || !partial || !pflag)) || nparts < 1 ||
+        nparts > 65536 || part < 0 || part >= nparts)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_partial: bad arguments (M=%d, n_pat=%d, part %d of %d)", M,
+                        n_pat, part, nparts);
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_partial: precision %d (FP64, FP32 split, DD or FX)", precision);
+    if (n_pat == 0) return GBS_OK;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return sweep_slice(ctx, M, O, patterns, n_pat, precision, part, nparts, partial, pflag);
+}
+
+int gbs_prob_combine(gbs_ctx *ctx, const double *logdet_sigmaQ, const uint64_t *patterns, int n_pat, int precision,
+                     int nparts, const double *partials, const int32_t *pflags, double *logP, double *kappa,
+                     double *err_bound, int32_t *status) {
+    if (!ctx) return GBS_E_INVALID;
+    if (n_pat < 0 || !logdet_sigmaQ || nparts < 1 || nparts > 65536 ||
+        (n_pat && (!patterns || !partials || !pflags || !logP)))
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_combine: bad arguments (n_pat=%d, nparts=%d)", n_pat, nparts);
+    if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_combine: precision %d (FP64, FP32 split, DD or FX)", precision);
+    if (n_pat == 0) return GBS_OK;
+    GBS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return sweep_combine(ctx, logdet_sigmaQ, patterns, n_pat, precision, nparts, partials, pflags, logP, kappa,
+                         err_bound, status);
+}
+
 int gbs_run_host(gbs_ctx *ctx, int M, const double *U_host, const double *r_host, double eta,
                  const uint64_t *patterns_host, int n_pat, int order, int precision,
                  double *logP_host, double *kappa_host, double *err_host, int32_t *status_host) {

@@ -74,6 +74,11 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
                    const double *logdet, const uint64_t *patterns, int n_pat, int precision,
                    double *logP, double *kappa, double *err_bound, int32_t *status);
 size_t sweep_workspace_bytes(int n_pat, long long units);
+int sweep_slice(gbs_ctx *ctx, int M, const double *O, const uint64_t *patterns, int n_pat, int precision,
+                int part, int nparts, double *partial, int32_t *pflag);
+int sweep_combine(gbs_ctx *ctx, const double *logdet, const uint64_t *patterns, int n_pat, int precision,
+                  int nparts, const double *partials, const int32_t *pflags, double *logP, double *kappa,
+                  double *err_bound, int32_t *status);
 long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split);
 int sweep_split_of(const gbs_ctx *ctx, int precision);
 int sweep_auto(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns, int n_pat,

@@ -959,29 +959,55 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     }
 }
 
-// ---- per-pattern result: sum of the pattern's unit partials in unit order -------------
+// ---- per-pattern result ---------------------------------------------------------------
+// log P, kappa, the a-posteriori bound and the status of one pattern from its signed sum
+// (h, l) and sum of |terms| a.  flags: pivot bits of its units (1 not positive, 2 outside
+// the fixed-point range); n < 0: invalid pattern; over: the batch did not fit.
 template <typename T>
-__global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Plan pl,
-                                double *__restrict__ logP, double *__restrict__ kappa,
-                                double *__restrict__ err_bound, int32_t *__restrict__ status) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= n_pat) return;
-    const int sp = warp;
-    const int p = pl.perm[sp];
-    const int n = pl.pat_n[p];
-    const bool batch_over = *pl.overflow != 0;
-    const long long u0 = pl.unit_off[sp], u1 = pl.unit_off[sp + 1];
-    double h = 0.0, l = 0.0, a = 0.0;
-    if (!batch_over)
-        for (long long u = u0 + lane; u < u1; u += 32) {
-            const double *q = pl.partials + 3 * u;
-            double s, e;
-            two_sum(h, q[0], s, e);
-            h = s;
-            l += q[1] + e;
-            a += q[2];
+__device__ __forceinline__ void finish_pattern(int n, bool over, int flags, double h, double l, double a,
+                                               double logdet, double &lp, double &kap, double &eb, int &st) {
+    const double Tv = h + l;
+    st = GBS_OK;
+    lp = nan("");
+    kap = nan("");
+    eb = nan("");
+    if (n < 0) {
+        st = GBS_E_INVALID;
+    } else if (over) {
+        st = GBS_E_NOMEM;
+    } else if (flags != 0) {
+        st = (flags & 1) ? GBS_E_NOT_SPD : GBS_E_RANGE;
+    } else {
+        // a-posteriori bound: every term carries a relative error of at most
+        // c (2n + 4) u from its chain of 2x2 pivots; the signed sum amplifies by kappa.
+        const double uu = Prec<T>::u;
+        kap = a / fabs(Tv);
+        const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * Prec<T>::u_sum;
+        if (!(Tv > 0.0)) {
+            st = GBS_E_NONPOSITIVE;
+        } else {
+            lp = -0.5 * logdet + log(h) + log1p(l / h);
+            eb = rel < 1.0 ? -log1p(-rel) : INFINITY;
         }
-    for (int off = 1; off < 32; off <<= 1) {  // fixed pairing order: deterministic
+    }
+}
+
+// the unit partials u0 <= u < u1 of one pattern summed in unit order by one warp (lanes
+// stride the units, then a fixed pairing tree: deterministic); the result on lane 0
+__device__ __forceinline__ void warp_unit_sum(const double *__restrict__ partials, long long u0, long long u1,
+                                              int lane, double &h, double &l, double &a) {
+    h = 0.0;
+    l = 0.0;
+    a = 0.0;
+    for (long long u = u0 + lane; u < u1; u += 32) {
+        const double *q = partials + 3 * u;
+        double s, e;
+        two_sum(h, q[0], s, e);
+        h = s;
+        l += q[1] + e;
+        a += q[2];
+    }
+    for (int off = 1; off < 32; off <<= 1) {
         double oh = __shfl_down_sync(0xffffffffu, h, off);
         double ol = __shfl_down_sync(0xffffffffu, l, off);
         double oa = __shfl_down_sync(0xffffffffu, a, off);
@@ -993,29 +1019,96 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
             a += oa;
         }
     }
+}
+
+// ---- per-pattern result: sum of the pattern's unit partials in unit order -------------
+template <typename T>
+__global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Plan pl,
+                                double *__restrict__ logP, double *__restrict__ kappa,
+                                double *__restrict__ err_bound, int32_t *__restrict__ status) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_pat) return;
+    const int sp = warp;
+    const int p = pl.perm[sp];
+    const int n = pl.pat_n[p];
+    const bool batch_over = *pl.overflow != 0;
+    double h, l, a;
+    warp_unit_sum(pl.partials, pl.unit_off[sp], batch_over ? pl.unit_off[sp] : pl.unit_off[sp + 1], lane, h, l, a);
     if (lane) return;
-    const double Tv = h + l;
-    int st = GBS_OK;
-    double lp = nan(""), kap = nan(""), eb = nan("");
-    if (n < 0) {
-        st = GBS_E_INVALID;
-    } else if (batch_over) {
-        st = GBS_E_NOMEM;
-    } else if (pl.pflags[sp] != 0) {
-        st = (pl.pflags[sp] & 1) ? GBS_E_NOT_SPD : GBS_E_RANGE;
-    } else {
-        // a-posteriori bound: every term carries a relative error of at most
-        // c (2n + 4) u from its chain of 2x2 pivots; the signed sum amplifies by kappa.
-        const double uu = Prec<T>::u;
-        kap = a / fabs(Tv);
-        const double rel = 4.0 * kap * (2.0 * n + 4.0) * uu + 4.0 * kap * Prec<T>::u_sum;
-        if (!(Tv > 0.0)) {
-            st = GBS_E_NONPOSITIVE;
-        } else {
-            lp = -0.5 * (*logdet) + log(h) + log1p(l / h);
-            eb = rel < 1.0 ? -log1p(-rel) : INFINITY;
-        }
+    double lp, kap, eb;
+    int st;
+    finish_pattern<T>(n, batch_over, pl.pflags[sp], h, l, a, *logdet, lp, kap, eb, st);
+    logP[p] = lp;
+    if (kappa) kappa[p] = kap;
+    if (err_bound) err_bound[p] = eb;
+    if (status) status[p] = st;
+}
+
+// ---- one slice of a batch's work units (the batch split across GPUs) ------------------
+// After the plan: the sweep evaluates only units [total part / nparts, total (part + 1) /
+// nparts) (units of one precision and split carry equal numbers of subsets once n >= B + L
+// + s, so equal unit counts balance the cost; a slice may cut a large pattern by prefix).
+__global__ void slice_kernel(Plan pl, int part, int nparts, long long *range) {
+    const long long total = *pl.total_units;  // 0 when the batch did not fit
+    const long long b = total * part / nparts, e = total * (part + 1) / nparts;
+    range[0] = b;
+    range[1] = e;
+    *pl.counter = (unsigned long long)b;
+    *pl.total_units = e;
+}
+
+// per pattern: the slice's units of the pattern summed in unit order -> (T_hi, T_lo,
+// sum |terms|) and its flags (-1 invalid pattern; else bits 1 not positive, 2 outside the
+// fixed-point range, 4 the batch did not fit)
+__global__ void slice_partial_kernel(int n_pat, Plan pl, const long long *__restrict__ range,
+                                     double *__restrict__ part, int32_t *__restrict__ pflag) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_pat) return;
+    const int sp = warp;
+    const int p = pl.perm[sp];
+    const int n = pl.pat_n[p];
+    const bool over = *pl.overflow != 0;
+    long long u0 = pl.unit_off[sp], u1 = pl.unit_off[sp + 1];
+    u0 = u0 > range[0] ? u0 : range[0];
+    u1 = u1 < range[1] ? u1 : range[1];
+    if (over || u1 < u0) u1 = u0;
+    double h, l, a;
+    warp_unit_sum(pl.partials, u0, u1, lane, h, l, a);
+    if (lane) return;
+    part[3 * p] = h;
+    part[3 * p + 1] = l;
+    part[3 * p + 2] = a;
+    pflag[p] = n < 0 ? -1 : ((u1 > u0 ? pl.pflags[sp] : 0) | (over ? 4 : 0));
+}
+
+// the slices' partial sums of every pattern combined in slice order (TwoSum), then the
+// result as gbs_prob's; n from the pattern's bits
+template <typename T>
+__global__ void combine_kernel(int n_pat, int nparts, const uint64_t *__restrict__ pats,
+                               const double *__restrict__ logdet, const double *__restrict__ parts,
+                               const int32_t *__restrict__ pflags, double *__restrict__ logP,
+                               double *__restrict__ kappa, double *__restrict__ err_bound,
+                               int32_t *__restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pat) return;
+    double h = 0.0, l = 0.0, a = 0.0;
+    int flags = 0;
+    bool invalid = false;
+    for (int q = 0; q < nparts; ++q) {
+        const size_t i = (size_t)q * n_pat + p;
+        const int f = pflags[i];
+        if (f < 0) invalid = true;
+        else flags |= f;
+        double s, e;
+        two_sum(h, parts[3 * i], s, e);
+        h = s;
+        l += parts[3 * i + 1] + e;
+        a += parts[3 * i + 2];
     }
+    const int n = invalid ? -1 : __popcll(pats[2 * p]) + __popcll(pats[2 * p + 1]);
+    double lp, kap, eb;
+    int st;
+    finish_pattern<T>(n, (flags & 4) != 0, flags & 3, h, l, a, *logdet, lp, kap, eb, st);
     logP[p] = lp;
     if (kappa) kappa[p] = kap;
     if (err_bound) err_bound[p] = eb;
@@ -1025,7 +1118,7 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct WsOffsets {
-    size_t counter, total, overflow, perm, pat_n, unit_off, pflags, partials, end;
+    size_t counter, total, overflow, range, perm, pat_n, unit_off, pflags, partials, end;
 };
 
 WsOffsets ws_offsets(int n_pat, long long units) {
@@ -1033,7 +1126,8 @@ WsOffsets ws_offsets(int n_pat, long long units) {
     o.counter = 0;
     o.total = 8;
     o.overflow = 16;
-    o.perm = align256(20);
+    o.range = 24;  // two long long: the unit slice of gbs_prob_partial
+    o.perm = align256(40);
     o.pat_n = align256(o.perm + 4 * (size_t)n_pat);
     o.unit_off = align256(o.pat_n + 4 * (size_t)n_pat);
     o.pflags = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
@@ -1150,6 +1244,64 @@ int run_sweep_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double *O
     const int fthreads = 256, fblocks = (n_pat * 32 + fthreads - 1) / fthreads;
     finalize_kernel<T><<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa,
                                                              err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
+}
+
+// One slice of the batch's work units (gbs_prob_partial): the plan of the whole batch,
+// then only this slice's units swept, and per-pattern partial sums of the slice.
+template <typename T>
+int run_sweep_slice(gbs_ctx *ctx, int M, const double *O, const uint64_t *pats, int n_pat, int part,
+                    int nparts, double *partial, int32_t *pflag) {
+    using Lay = Layout<T>;
+    const int pi = Prec<T>::idx;
+    if (ctx->reserved && n_pat > ctx->cap_pat)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob_partial: %d patterns exceed the reservation of %d",
+                        n_pat, ctx->cap_pat);
+    if (ctx->sweep_blocks_per_sm[pi] == 0) {
+        GBS_CUDA(ctx, cudaFuncSetAttribute(sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Lay::bytes));
+        int nb = 0;
+        GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T>, kThreads,
+                                                                    Lay::bytes));
+        if (nb < 1) return gbs_fail(ctx, GBS_E_CUDA, "sweep kernel does not fit on an SM");
+        ctx->sweep_blocks_per_sm[pi] = nb;
+    }
+    if (!ctx->reserved) {
+        int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, 0).end);
+        if (st) return st;
+    }
+    long long cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+    Plan pl = plan_from(ctx->ws, n_pat);
+    pl.split = sweep_split_of(ctx, pi);
+    plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    if (!ctx->reserved) {
+        GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.unit_off + n_pat, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const long long need = *(long long *)ctx->pinned;
+        if (need > cap) {
+            int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, need).end);
+            if (st) return st;
+            cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+            pl = plan_from(ctx->ws, n_pat);
+            pl.split = sweep_split_of(ctx, pi);
+            plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
+            GBS_CUDA(ctx, cudaGetLastError());
+        }
+    }
+    long long *range = (long long *)((char *)ctx->ws + ws_offsets(n_pat, 0).range);
+    slice_kernel<<<1, 1, 0, ctx->stream>>>(pl, part, nparts, range);
+    GBS_CUDA(ctx, cudaGetLastError());
+    const int grid = ctx->num_sms * ctx->sweep_blocks_per_sm[pi];
+    int st = gbs_timing_begin(ctx);
+    if (st) return st;
+    sweep_kernel<T><<<grid, kThreads, Lay::bytes, ctx->stream>>>(M, O, pats, n_pat, pl);
+    GBS_CUDA(ctx, cudaGetLastError());
+    st = gbs_timing_end(ctx);
+    if (st) return st;
+    const int fthreads = 256, fblocks = (n_pat * 32 + fthreads - 1) / fthreads;
+    slice_partial_kernel<<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, pl, range, partial, pflag);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }
@@ -1412,6 +1564,37 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
     if (precision == GBS_FX)
         return run_sweep<fx>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+}
+
+int sweep_slice(gbs_ctx *ctx, int M, const double *O, const uint64_t *patterns, int n_pat, int precision,
+                int part, int nparts, double *partial, int32_t *pflag) {
+    if (precision == GBS_FP64)
+        return run_sweep_slice<double>(ctx, M, O, patterns, n_pat, part, nparts, partial, pflag);
+    if (precision == GBS_DD)
+        return run_sweep_slice<dd>(ctx, M, O, patterns, n_pat, part, nparts, partial, pflag);
+    if (precision == GBS_FX)
+        return run_sweep_slice<fx>(ctx, M, O, patterns, n_pat, part, nparts, partial, pflag);
+    return run_sweep_slice<float>(ctx, M, O, patterns, n_pat, part, nparts, partial, pflag);
+}
+
+int sweep_combine(gbs_ctx *ctx, const double *logdet, const uint64_t *patterns, int n_pat, int precision,
+                  int nparts, const double *partials, const int32_t *pflags, double *logP, double *kappa,
+                  double *err_bound, int32_t *status) {
+    const unsigned g = (unsigned)((n_pat + 127) / 128);
+    if (precision == GBS_FP64)
+        combine_kernel<double><<<g, 128, 0, ctx->stream>>>(n_pat, nparts, patterns, logdet, partials, pflags,
+                                                             logP, kappa, err_bound, status);
+    else if (precision == GBS_DD)
+        combine_kernel<dd><<<g, 128, 0, ctx->stream>>>(n_pat, nparts, patterns, logdet, partials, pflags, logP,
+                                                         kappa, err_bound, status);
+    else if (precision == GBS_FX)
+        combine_kernel<fx><<<g, 128, 0, ctx->stream>>>(n_pat, nparts, patterns, logdet, partials, pflags, logP,
+                                                         kappa, err_bound, status);
+    else
+        combine_kernel<float><<<g, 128, 0, ctx->stream>>>(n_pat, nparts, patterns, logdet, partials, pflags,
+                                                            logP, kappa, err_bound, status);
+    GBS_CUDA(ctx, cudaGetLastError());
+    return GBS_OK;
 }
 
 namespace {

@@ -136,3 +136,91 @@ def test_two_ranks_gradient_all_reduce():
         for k in range(world):
             d = got[k][order][0]
             assert np.abs(d - full[order]).max() < 1e-12 * np.abs(full[order]).max(), (order, k)
+
+
+class _OracleSliceCtx:
+    """Stands in for the GPU context in prob_sharded: slice k of N of every pattern's
+    subsets (the mask range [2^n k / N, 2^n (k + 1) / N)) summed by the double-double
+    oracle, and the slices combined in order with TwoSum, as the library's combine does."""
+
+    def __init__(self, state):
+        self.state = state
+
+    def prob_partial(self, O, patterns, part, nparts, precision="fx"):
+        import torch
+        import oracle
+        pats = np.asarray(patterns, dtype=np.uint64).reshape(-1, 2)
+        out = np.zeros((len(pats), 3))
+        for p, pat in enumerate(pats):
+            modes = g.pattern_modes(pat)
+            b, e = (1 << len(modes)) * part // nparts, (1 << len(modes)) * (part + 1) // nparts
+            if e > b:
+                out[p] = oracle.subset_sum(self.state.A, self.state.M, modes, b, e, dd=True)
+        return torch.from_numpy(out), torch.zeros(len(pats), dtype=torch.int32)
+
+    def prob_combine(self, logdet, patterns, partials, pflags, precision="fx"):
+        import math
+        import torch
+        P = partials.numpy()
+        logP = np.zeros(P.shape[1])
+        for p in range(P.shape[1]):
+            h = l = 0.0
+            for q in range(P.shape[0]):
+                s = h + P[q, p, 0]
+                bp = s - h
+                e = (h - (s - bp)) + (P[q, p, 0] - bp)
+                h, l = s, l + P[q, p, 1] + e
+            logP[p] = -0.5 * float(logdet[0]) + math.log(h) + math.log1p(l / h)
+        return dict(logP=torch.from_numpy(logP), status=torch.zeros(P.shape[1], dtype=torch.int32))
+
+
+def _strong_case():
+    import oracle
+    M = 14
+    U = g.haar_unitary(M, 21)
+    r = g.squeezing(M, 7, 0.6, 1.1, 21)
+    st = oracle.build_state(U, r, 0.6)
+    pats = g.gen_patterns(21, M, 3, 13, 9)
+    return st, pats
+
+
+def _strong_rank(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2106_01445_gb300.api import prob_sharded
+        st, pats = _strong_case()
+        out = prob_sharded(_OracleSliceCtx(st), torch.from_numpy(st.O),
+                           torch.tensor([st.logdet], dtype=torch.float64), pats)
+        q.put((rank, out["logP"].numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_strong_split_combines_to_one_rank():
+    """One batch evaluated by two ranks together: each sweeps its slice of every pattern's
+    subsets, one all_gather exchanges the per-pattern double-double partial sums, and each
+    rank combines them in rank order.  Both ranks hold the same log P, bit for bit, and it
+    equals the one-rank (whole-batch) double-double result."""
+    import oracle
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_strong_rank, args=(k, world, port, q)) for k in range(world)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in range(world):
+        rank, lp = q.get(timeout=300)
+        got[rank] = lp
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    st, pats = _strong_case()
+    one = oracle.prob_exact(st, pats, dd=True)["logP"]
+    assert np.array_equal(got[0], got[1])
+    assert np.abs(got[0] - one).max() < 1e-12
