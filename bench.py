@@ -767,11 +767,19 @@ def run_profile_case(args):
     st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
     pats = c.patterns() if args.profile == "sweep" else c.patterns()[:args.npat]
     order = 0 if args.profile == "sweep" else args.order
-    for _ in range(2):
-        out = ctx.prob(st["O"], st["logdet"], pats, order=order, precision=args.precision)
+    out = ctx.prob(st["O"], st["logdet"], pats, order=order, precision=args.precision)
     torch.cuda.synchronize()
-    print("profile case %s %s: %d patterns, %d ok" % (args.profile, args.precision, len(pats),
-                                                      int((out["status"] == 0).sum().item())))
+    ctx.timing(True)
+    ctx.timing_read(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = ctx.prob(st["O"], st["logdet"], pats, order=order, precision=args.precision)
+    e1.record()
+    torch.cuda.synchronize()
+    kms, launches = ctx.timing_read(reset=True)
+    print("profile case %s %s order %d: %d patterns, %d ok, %d fit fallbacks; call %.3f ms, timed kernel %.3f ms"
+          % (args.profile, args.precision, order, len(pats), int((out["status"] == 0).sum().item()),
+             int((out["status"] == 7).sum().item()), e0.elapsed_time(e1), kms / max(launches, 1)))
     return 0
 
 
