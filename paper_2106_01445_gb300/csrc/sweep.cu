@@ -442,11 +442,37 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
         }
     }
     __syncthreads();
-    for (int p = t; p < n_pat; p += kPlanThreads) {
-        int pos = atomicAdd(&hist[pl.pat_n[p] + 1], 1);
-        pl.perm[pos] = p;
+    // stable placement: inside a bin the patterns keep their batch order, so the unit
+    // numbering is the same on every call (the batch split of gbs_prob_partial numbers the
+    // units of one batch on every rank and relies on it).  Rounds of kPlanThreads patterns:
+    // rank inside the warp by __match_any_sync, then per bin an exclusive scan over warps.
+    constexpr int kBins = kMaxN + 2;  // keys -1 (invalid) .. kMaxN
+    __shared__ int wcnt[kPlanThreads / 32][kBins];
+    __shared__ int s_roundtot[kBins];
+    for (int base = 0; base < n_pat; base += kPlanThreads) {
+        const int p = base + t;
+        const int key = p < n_pat ? pl.pat_n[p] + 1 : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int rank_w = __popc(grp & ((1u << (t & 31)) - 1u));
+        for (int i = t; i < (kPlanThreads / 32) * kBins; i += kPlanThreads) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        if (key >= 0 && rank_w == 0) wcnt[t >> 5][key] = __popc(grp);
+        __syncthreads();
+        if (t < kBins) {
+            int run = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const int c = wcnt[w][t];
+                wcnt[w][t] = run;
+                run += c;
+            }
+            s_roundtot[t] = run;
+        }
+        __syncthreads();
+        if (key >= 0) pl.perm[hist[key] + wcnt[t >> 5][key] + rank_w] = p;
+        __syncthreads();
+        if (t < kBins) hist[t] += s_roundtot[t];
+        __syncthreads();
     }
-    __syncthreads();
     // unit counts in sorted order, exclusive scan
     const int per = (n_pat + kPlanThreads - 1) / kPlanThreads;
     long long s = 0;
