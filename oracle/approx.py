@@ -238,21 +238,12 @@ def sector_last_point(Dk: np.ndarray, n: int, k: int, j: int, stall_accept: floa
     return val, flag
 
 
-def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
-                   K: int | None = None, eps_sector: float = EPS_SECTOR, rho: float | None = None,
-                   rhos=RHOS, flag_share: float = FLAG_SHARE, stall_accept: float = 1e3):
-    """log P(S) by the order-j approximation.  Returns (logP, info dict).  K and rho
-    default to choose_kmax and choose_tilt (over the radii rhos); fixing them makes log P
-    a smooth function of O (for derivatives by differences).  eps_sector, flag_share and
-    stall_accept are the readings' constants (the tests vary them to show log P does not
-    depend on them)."""
-    modes = list(modes)
-    n = len(modes)
-    if rho is None:
-        rho = choose_tilt(O, M, modes, rhos)
-    if K is None:
-        K = choose_kmax(O, M, modes, rho)
-    D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
+def logprob_from_tables(D: np.ndarray, n: int, j: int, rho: float, logdet_sigmaQ: float,
+                        eps_sector: float = EPS_SECTOR, flag_share: float = FLAG_SHARE,
+                        stall_accept: float = 1e3):
+    """Steps 3 and 4 from the tilted moment tables D[w, k] = D_w^(k) rho^k: each sector's
+    fit, its all-clicked point, and their sum.  Returns (logP, parts, flag)."""
+    K = D.shape[1] - 1
     parts = np.zeros(K + 1)                                  # tilted last points
     fell = np.zeros(K + 1, dtype=bool)
     floor = eps_sector * D[0].max()
@@ -275,7 +266,25 @@ def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
             flags = 1
     else:
         logsum = -math.inf
-    logP = -0.5 * logdet_sigmaQ + logsum
+    return -0.5 * logdet_sigmaQ + logsum, parts, flags
+
+
+def approx_logprob(O: np.ndarray, logdet_sigmaQ: float, M: int, modes, j: int,
+                   K: int | None = None, eps_sector: float = EPS_SECTOR, rho: float | None = None,
+                   rhos=RHOS, flag_share: float = FLAG_SHARE, stall_accept: float = 1e3):
+    """log P(S) by the order-j approximation.  Returns (logP, info dict).  K and rho
+    default to choose_kmax and choose_tilt (over the radii rhos); fixing them makes log P
+    a smooth function of O (for derivatives by differences).  eps_sector, flag_share and
+    stall_accept are the readings' constants (the tests vary them to show log P does not
+    depend on them)."""
+    modes = list(modes)
+    n = len(modes)
+    if rho is None:
+        rho = choose_tilt(O, M, modes, rhos)
+    if K is None:
+        K = choose_kmax(O, M, modes, rho)
+    D = factorial_moment_tables(O, M, modes, j, K, rho)     # tilted: D_w^(k) rho^k
+    logP, parts, flags = logprob_from_tables(D, n, j, rho, logdet_sigmaQ, eps_sector, flag_share, stall_accept)
     return logP, dict(K=K, D=D, parts=parts, flag=flags, rho=rho)
 
 

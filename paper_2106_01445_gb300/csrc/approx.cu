@@ -20,10 +20,18 @@
 // index with tilted tail < 1e-14 Z_S(rho) from Chernoff's inequality; DFT length
 // L = K + 1), approx_minors (one CTA per (pattern, nu_l), l <= L/2 by conjugate
 // symmetry), approx_fit (one CTA per pattern: inverse DFT, fits, sum).
+#include <cooperative_groups.h>
+#include <type_traits>
 #include <math.h>
 
 #include "ff.cuh"
 #include "gbs_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+#ifndef GBS_FF_FMS_INLINE
+#define GBS_FF_FMS_INLINE __noinline__
+#endif
 
 namespace {
 
@@ -74,7 +82,14 @@ template <typename R> __device__ __forceinline__ cx<R> crsqrt(cx<R> p) {
 // float-float complex products, reciprocals and roots as shared (non-inlined) calls (the
 // overloads win over the templates): inlined everywhere they overflowed the instruction
 // cache (-33% time on the order-4 minors with these three out of line)
-static __device__ __noinline__ cx<ff> operator*(cx<ff> a, cx<ff> b) { return operator*<ff>(a, b); }
+static __device__ __noinline__ cx<ff> operator*(cx<ff> a, cx<ff> b) {
+    return {ff_dot2(a.re, b.re, -a.im, b.im), ff_dot2(a.re, b.im, a.im, b.re)};
+}
+// e - a b: one fused form per part for float-float (see ff_fms2)
+template <typename R> __device__ __forceinline__ cx<R> cfms(cx<R> e, cx<R> a, cx<R> b) { return e - a * b; }
+static __device__ GBS_FF_FMS_INLINE cx<ff> cfms(cx<ff> e, cx<ff> a, cx<ff> b) {
+    return {ff_fms2(e.re, a.re, b.re, -a.im, b.im), ff_fms2(e.im, a.re, b.im, a.im, b.re)};
+}
 static __device__ __noinline__ cx<ff> cinv(cx<ff> a) { return cinv<ff>(a); }
 static __device__ __noinline__ cx<ff> crsqrt(cx<ff> p) { return crsqrt<ff>(p); }
 __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
@@ -93,6 +108,7 @@ template <typename R> struct MinorPrec;
 template <> struct MinorPrec<double> {
     static constexpr int min_blocks = 1;
     static constexpr int nmax = 79;
+    static constexpr bool pair = true;  // n in (nmax, 112] on a CTA pair
     static constexpr double sector_eps = 1e-12;  // tilted sectors below this share of the largest: noise
 };
 template <> struct MinorPrec<ff> {
@@ -100,11 +116,13 @@ template <> struct MinorPrec<ff> {
     // CTA of 255-register threads
     static constexpr int min_blocks = 2;
     static constexpr int nmax = 79;
+    static constexpr bool pair = true;
     static constexpr double sector_eps = 1e-12;
 };
 template <> struct MinorPrec<float> {
     static constexpr int min_blocks = 2;  // 127 registers: two CTAs per SM
     static constexpr int nmax = 112;
+    static constexpr bool pair = false;
     static constexpr double sector_eps = 1e-6;  // moments resolved to ~1e-7 K
 };
 
@@ -222,7 +240,7 @@ __global__ void __launch_bounds__(kPlanThreads) approx_plan_kernel(int M, const 
     (void)order;
 }
 
-__global__ void approx_scan_kernel(int n_pat, long long cap, ApproxPlan pl) {
+__global__ void approx_scan_kernel(int n_pat, long long cap, int n_single, ApproxPlan pl) {
     // one thread: patterns are few thousand at most per call
     if (threadIdx.x || blockIdx.x) return;
     long long run = 0;
@@ -234,10 +252,11 @@ __global__ void approx_scan_kernel(int n_pat, long long cap, ApproxPlan pl) {
     pl.unit_off[n_pat] = run;
     *pl.overflow = run > cap ? 1 : 0;
     *pl.total = run > cap ? 0 : run;
-    int nmax = 0, Lmax = 1;
+    int nmax = 0, Lmax = 1, nsmall = 0;
     long long secs = 0;
     for (int p = 0; p < n_pat; ++p) {
         nmax = pl.pat_n[p] > nmax ? pl.pat_n[p] : nmax;
+        if (pl.pat_n[p] <= n_single && pl.pat_n[p] > nsmall) nsmall = pl.pat_n[p];
         Lmax = pl.pat_L[p] > Lmax ? pl.pat_L[p] : Lmax;
         pl.sec_off[p] = secs;
         secs += pl.pat_L[p] > 0 ? pl.pat_L[p] : 0;
@@ -247,6 +266,7 @@ __global__ void approx_scan_kernel(int n_pat, long long cap, ApproxPlan pl) {
     pl.info[1] = nmax;
     pl.info[2] = Lmax;
     pl.info[3] = secs;
+    pl.info[4] = nsmall;  // largest n of the one-CTA minors kernel
 }
 
 // ---- minors at one nu point ------------------------------------------------------
@@ -269,7 +289,7 @@ __device__ __forceinline__ cx<R> ldl_rsqrt_prod(cx<R> (&a)[K * (K + 1) / 2], boo
             for (int i = k + 1; i < K; ++i) {
                 cx<R> li = a[pidx(K, k, i)] * inv;
 #pragma unroll
-                for (int j = i; j < K; ++j) a[pidx(K, i, j)] = a[pidx(K, i, j)] - li * a[pidx(K, k, j)];
+                for (int j = i; j < K; ++j) a[pidx(K, i, j)] = cfms(a[pidx(K, i, j)], li, a[pidx(K, k, j)]);
             }
         }
     }
@@ -367,7 +387,7 @@ __device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ 
             if (fq < N - fp) { i = fp; j = fp + fq; } else { i = N - 1 - fp; j = i + (fq - (N - fp)); }
             if (i != k && j != k) {
                 cx<R> &e = G[i * N - (i * (i - 1)) / 2 + (j - i)];
-                e = e - cb[i] * cu[j];
+                e = cfms(e, cb[i], cu[j]);
             }
             fq += sq;
             fp += sp;
@@ -394,10 +414,191 @@ __device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ 
     __syncthreads();
 }
 
+// Read-only view of the swept matrix -G, G = (I - t O_S)^{-1}, packed upper triangle of
+// N x N: rows [0, rsplit) at b0, rows [rsplit, N) at b1 (whose first entry is packed
+// entry off1).  One CTA: rsplit = N.  A CTA pair (cluster): each half in one CTA's shared
+// memory, the other half reached through distributed shared memory.
+template <typename R> struct GView {
+    const cx<R> *b0, *b1;
+    int N, rsplit, off1;
+    __device__ __forceinline__ int rowoff(int r) const { return r * N - (r * (r - 1)) / 2 - r; }
+    // p with p[col] = swept entry (r, col), col >= r
+    __device__ __forceinline__ const cx<R> *row(int r) const {
+        return r < rsplit ? b0 + rowoff(r) : b1 + (rowoff(r) - off1);
+    }
+    __device__ __forceinline__ cx<R> g(int i, int j) const {  // G(i, j) = -swept(i, j)
+        const cx<R> v = i <= j ? row(i)[j] : row(j)[i];
+        return mk<R>(-v.re, -v.im);
+    }
+};
+
+// The group terms det(G_WW)^{-1/2} of every W with |W| <= order, summed per |W| into
+// acc; worker `tid` of `nthr` takes every nthr-th group of each size.
+template <typename R>
+__device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order, int tid, int nthr,
+                                            GroupAcc<R> &acc, bool &bad) {
+    // w = 1: det of the 2x2 block, one root
+    if (order >= 1)
+        for (int a = tid; a < n; a += nthr) {
+            cx<R> m[3] = {V.g(2 * a, 2 * a), V.g(2 * a, 2 * a + 1), V.g(2 * a + 1, 2 * a + 1)};
+            acc.add(1, ldl_rsqrt_prod<R, 2>(m, bad));
+        }
+    // w = 2
+    if (order >= 2)
+        for (int idx = tid; idx < n * (n - 1) / 2; idx += nthr) {
+            int a = 0, rem = idx;
+            while (rem >= n - 1 - a) { rem -= n - 1 - a; ++a; }
+            int b = a + 1 + rem;
+            int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
+            cx<R> m[10];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = i; j < 4; ++j) m[pidx(4, i, j)] = V.g(rr[i], rr[j]);
+            acc.add(2, ldl_rsqrt_prod<R, 4>(m, bad));
+        }
+    // w = 3, and w = 4 from each triple's factorisation.  Triples in order of their
+    // largest detector c (then b, a), so the lanes of a warp share c and with it the
+    // number n - 1 - c of fourth detectors d > c.
+    if (order >= 3) {
+        const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
+        for (long long idx = tid; idx < ntri; idx += nthr) {
+            // c: the largest with C(c, 3) <= idx; then b: the largest with C(b, 2) <= rem
+            // (FP32 estimates on the MUFU pipe, corrected exactly in integers)
+            int c = (int)cbrtf(6.0f * (float)idx);
+            while ((long long)(c + 1) * c * (c - 1) / 6 <= idx) ++c;
+            while ((long long)c * (c - 1) * (c - 2) / 6 > idx) --c;
+            const long long rem = idx - (long long)c * (c - 1) * (c - 2) / 6;
+            int b = (int)sqrtf(2.0f * (float)rem);
+            while ((long long)(b + 1) * b / 2 <= rem) ++b;
+            while ((long long)b * (b - 1) / 2 > rem) --b;
+            const int a = (int)(rem - (long long)b * (b - 1) / 2);
+            const int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
+            // rows of the triple: entry (rr[i], col) with rr[i] <= col at rp[i][col]
+            const cx<R> *rp[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) rp[i] = V.row(rr[i]);
+            auto gr = [&](int i, int col) -> cx<R> { const cx<R> v = rp[i][col]; return mk<R>(-v.re, -v.im); };
+            cx<R> w6[21];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = gr(i, rr[j]);
+            // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
+            cx<R> Lf[15], Dinv[6];
+            cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                cx<R> d = w6[pidx(6, k, k)];
+                if (!(d.re > R(0))) bad = true;
+                if (k & 1) f3 = f3 * crsqrt(prev * d);
+                prev = d;
+                cx<R> inv = cinv(d);
+                Dinv[k] = inv;
+#pragma unroll
+                for (int i = k + 1; i < 6; ++i) {
+                    cx<R> li = w6[pidx(6, k, i)] * inv;
+                    Lf[pidx(5, k, i - 1)] = li;
+#pragma unroll
+                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = cfms(w6[pidx(6, i, j)], li, w6[pidx(6, k, j)]);
+                }
+            }
+            acc.add(3, f3);
+            // float-float: this triple's quads summed in float-float first, then one FP64
+            // addition (keeps the FP64 pipe, 1/64 of FP32 here, out of the quad loop)
+            constexpr bool kTriplePartial = std::is_same<R, ff>::value;
+            cx<R> q4 = mk<R>(R(0), R(0));
+            if (order >= 4)
+                for (int d4 = c + 1; d4 < n; ++d4) {
+                    // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2); det S^{-1/2}
+                    cx<R> y0[6], y1[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        cx<R> v0 = gr(i, 2 * d4), v1 = gr(i, 2 * d4 + 1);
+#pragma unroll
+                        for (int k = 0; k < i; ++k) {
+                            v0 = cfms(v0, Lf[pidx(5, k, i - 1)], y0[k]);
+                            v1 = cfms(v1, Lf[pidx(5, k, i - 1)], y1[k]);
+                        }
+                        y0[i] = v0;
+                        y1[i] = v1;
+                    }
+                    const cx<R> *r0 = V.row(2 * d4), *r1 = V.row(2 * d4 + 1);
+                    const cx<R> e00 = r0[2 * d4], e01 = r0[2 * d4 + 1], e11 = r1[2 * d4 + 1];
+                    cx<R> s00 = mk<R>(-e00.re, -e00.im), s01 = mk<R>(-e01.re, -e01.im),
+                          s11 = mk<R>(-e11.re, -e11.im);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
+                        s00 = cfms(s00, z0, y0[k]);
+                        s01 = cfms(s01, z0, y1[k]);
+                        s11 = cfms(s11, z1, y1[k]);
+                    }
+                    // pivots s00 and det / s00 of the accretive block: Re > 0 each
+                    const cx<R> det = cfms(s00 * s11, s01, s01);
+                    if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
+                    const cx<R> term = f3 * crsqrt(det);
+                    if constexpr (kTriplePartial) q4 = q4 + term;
+                    else acc.add(4, term);
+                }
+            if constexpr (kTriplePartial)
+                if (order >= 4) acc.add(4, q4);
+        }
+    }
+}
+
+// a warp's sums of the group terms (lanes combined by a fixed butterfly) into red[warp]
+template <typename R>
+__device__ __forceinline__ void warp_group_sums(const GroupAcc<R> &acc, double *red_row) {
+    double accd[2 * (kMaxOrder + 1)];
+#pragma unroll
+    for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) accd[w] = w < 2 ? 0.0 : acc.get(w);
+#pragma unroll
+    for (int w = 2; w < 2 * (kMaxOrder + 1); ++w)
+        for (int off = 16; off; off >>= 1) accd[w] += __shfl_xor_sync(0xffffffffu, accd[w], off);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) red_row[w] = accd[w];
+}
+
+// the unit's D_w(t_l) = Z_S(t_l) sum_{|W| = w} det(G_WW)^{-1/2}, from the warp sums in
+// warp order (deterministic)
+__device__ __forceinline__ void write_unit(const ApproxPlan &pl, long long u, int order, const double *zs,
+                                           const double (*red)[2 * (kMaxOrder + 1)], int nwarps) {
+    const cx<double> z = mk<double>(zs[0], zs[1]);
+    double *out = pl.unit_D + (size_t)u * 2 * (kMaxOrder + 1);
+    out[0] = z.re;
+    out[1] = z.im;
+    for (int w = 1; w <= kMaxOrder; ++w) {
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < nwarps; ++q) {
+            re += red[q][2 * w];
+            im += red[q][2 * w + 1];
+        }
+        cx<double> v = z * mk<double>(re, im);
+        out[2 * w] = w <= order ? v.re : 0.0;
+        out[2 * w + 1] = w <= order ? v.im : 0.0;
+    }
+}
+
+// the pattern of unit u (skipping patterns without units: equal offsets)
+__device__ __forceinline__ int unit_pattern(const ApproxPlan &pl, int n_pat, long long u) {
+    int lo_ = 0, hi_ = n_pat;
+    while (hi_ - lo_ > 1) {
+        int mid = (lo_ + hi_) >> 1;
+        if (pl.unit_off[mid] <= u) lo_ = mid; else hi_ = mid;
+    }
+    int p = lo_;
+    while (p + 1 < n_pat && pl.unit_off[p + 1] <= u) ++p;
+    return p;
+}
+
+// One CTA per (pattern, nu_l) unit, for patterns of up to n_single clicks (the packed
+// inverse in this CTA's shared memory); larger patterns are left to the cluster kernel.
 template <typename R>
 __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) approx_minors_kernel(int M, const double *__restrict__ O,
                                                                     const uint64_t *__restrict__ pats,
-                                                                    int n_pat, int order,
+                                                                    int n_pat, int order, int n_single,
                                                                     unsigned long long *counter,
                                                                     ApproxPlan pl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -414,17 +615,13 @@ __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) appro
         __syncthreads();
         const long long u = s_u;
         if (u >= total) break;
-        int lo_ = 0, hi_ = n_pat;
-        while (hi_ - lo_ > 1) {
-            int mid = (lo_ + hi_) >> 1;
-            if (pl.unit_off[mid] <= u) lo_ = mid; else hi_ = mid;
-        }
-        // skip patterns without units (equal offsets): take the last pattern whose
-        // offset is <= u and whose range contains u
-        int p = lo_;
-        while (p + 1 < n_pat && pl.unit_off[p + 1] <= u) ++p;
+        const int p = unit_pattern(pl, n_pat, u);
         const int l = (int)(u - pl.unit_off[p]);
         const int n = pl.pat_n[p], L = pl.pat_L[p];
+        if (n > n_single) {   // a pattern for the CTA pairs
+            __syncthreads();
+            continue;
+        }
         const uint64_t wlo = pats[2 * p], whi = pats[2 * p + 1];
         if (t == 0) {
             int c = 0;
@@ -443,142 +640,198 @@ __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) appro
         sn *= rho;
         cs *= rho;
         sweep_inverse<R>(M, O, modes, n, cs, sn, G, &s_bad, s_zs);
-        // entries of G = (I - t O_S)^{-1} are minus the swept matrix
-        auto g = [&](int i, int j) -> cx<R> { cx<R> v = G[pidx_any(N, i, j)]; return mk<R>(-v.re, -v.im); };
         GroupAcc<R> acc;
         acc.zero();
         bool bad = false;
-        // w = 1: det of the 2x2 block, one root
-        if (order >= 1)
-            for (int a = t; a < n; a += kMinorThreads) {
-                cx<R> m[3] = {g(2 * a, 2 * a), g(2 * a, 2 * a + 1), g(2 * a + 1, 2 * a + 1)};
-                acc.add(1, ldl_rsqrt_prod<R, 2>(m, bad));
-            }
-        // w = 2
-        if (order >= 2)
-            for (int idx = t; idx < n * (n - 1) / 2; idx += kMinorThreads) {
-                int a = 0, rem = idx;
-                while (rem >= n - 1 - a) { rem -= n - 1 - a; ++a; }
-                int b = a + 1 + rem;
-                int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
-                cx<R> m[10];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = i; j < 4; ++j) m[pidx(4, i, j)] = g(rr[i], rr[j]);
-                acc.add(2, ldl_rsqrt_prod<R, 4>(m, bad));
-            }
-        // w = 3, and w = 4 from each triple's factorisation.  Triples in order of their
-        // largest detector c (then b, a), so the lanes of a warp share c and with it the
-        // number n - 1 - c of fourth detectors d > c.
-        if (order >= 3) {
-            const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
-            for (long long idx = t; idx < ntri; idx += kMinorThreads) {
-                // c: the largest with C(c, 3) <= idx; then b: the largest with C(b, 2) <= rem
-                // (FP32 estimates on the MUFU pipe, corrected exactly in integers)
-                int c = (int)cbrtf(6.0f * (float)idx);
-                while ((long long)(c + 1) * c * (c - 1) / 6 <= idx) ++c;
-                while ((long long)c * (c - 1) * (c - 2) / 6 > idx) --c;
-                const long long rem = idx - (long long)c * (c - 1) * (c - 2) / 6;
-                int b = (int)sqrtf(2.0f * (float)rem);
-                while ((long long)(b + 1) * b / 2 <= rem) ++b;
-                while ((long long)b * (b - 1) / 2 > rem) --b;
-                const int a = (int)(rem - (long long)b * (b - 1) / 2);
-                const int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
-                // row offsets: entry (rr[i], col) with rr[i] <= col sits at ro[i] + col
-                int ro[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) ro[i] = rr[i] * N - (rr[i] * (rr[i] - 1)) / 2 - rr[i];
-                auto gr = [&](int i, int col) -> cx<R> { const cx<R> v = G[ro[i] + col]; return mk<R>(-v.re, -v.im); };
-                cx<R> w6[21];
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-#pragma unroll
-                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = gr(i, rr[j]);
-                // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
-                cx<R> Lf[15], Dinv[6];
-                cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    cx<R> d = w6[pidx(6, k, k)];
-                    if (!(d.re > R(0))) bad = true;
-                    if (k & 1) f3 = f3 * crsqrt(prev * d);
-                    prev = d;
-                    cx<R> inv = cinv(d);
-                    Dinv[k] = inv;
-#pragma unroll
-                    for (int i = k + 1; i < 6; ++i) {
-                        cx<R> li = w6[pidx(6, k, i)] * inv;
-                        Lf[pidx(5, k, i - 1)] = li;
-#pragma unroll
-                        for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = w6[pidx(6, i, j)] - li * w6[pidx(6, k, j)];
-                    }
-                }
-                acc.add(3, f3);
-                if (order >= 4)
-                    for (int d4 = c + 1; d4 < n; ++d4) {
-                        // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2); det S^{-1/2}
-                        cx<R> y0[6], y1[6];
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) {
-                            cx<R> v0 = gr(i, 2 * d4), v1 = gr(i, 2 * d4 + 1);
-#pragma unroll
-                            for (int k = 0; k < i; ++k) {
-                                v0 = v0 - Lf[pidx(5, k, i - 1)] * y0[k];
-                                v1 = v1 - Lf[pidx(5, k, i - 1)] * y1[k];
-                            }
-                            y0[i] = v0;
-                            y1[i] = v1;
-                        }
-                        const int dg = 2 * d4 * N - (2 * d4 * (2 * d4 - 1)) / 2;  // (2 d4, 2 d4)
-                        const cx<R> e00 = G[dg], e01 = G[dg + 1], e11 = G[dg + N - 2 * d4];
-                        cx<R> s00 = mk<R>(-e00.re, -e00.im), s01 = mk<R>(-e01.re, -e01.im),
-                              s11 = mk<R>(-e11.re, -e11.im);
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) {
-                            const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
-                            s00 = s00 - z0 * y0[k];
-                            s01 = s01 - z0 * y1[k];
-                            s11 = s11 - z1 * y1[k];
-                        }
-                        // pivots s00 and det / s00 of the accretive block: Re > 0 each
-                        const cx<R> det = s00 * s11 - s01 * s01;
-                        if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
-                        acc.add(4, f3 * crsqrt(det));
-                    }
-            }
-        }
+        const GView<R> V{G, G, N, N, 0};
+        group_terms<R>(V, n, order, t, kMinorThreads, acc, bad);
         if (bad) s_bad = 1;
-        // deterministic block reduction of the (j + 1) complex sums
-        double accd[2 * (kMaxOrder + 1)];
-#pragma unroll
-        for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) accd[w] = w < 2 ? 0.0 : acc.get(w);
-#pragma unroll
-        for (int w = 2; w < 2 * (kMaxOrder + 1); ++w)
-            for (int off = 16; off; off >>= 1) accd[w] += __shfl_xor_sync(0xffffffffu, accd[w], off);
-        if ((t & 31) == 0)
-#pragma unroll
-            for (int w = 0; w < 2 * (kMaxOrder + 1); ++w) red[t >> 5][w] = accd[w];
+        warp_group_sums<R>(acc, red[t >> 5]);
         __syncthreads();
         if (t == 0) {
-            const cx<double> z = mk<double>(s_zs[0], s_zs[1]);
-            double *out = pl.unit_D + (size_t)u * 2 * (kMaxOrder + 1);
-            out[0] = z.re;
-            out[1] = z.im;
-            for (int w = 1; w <= kMaxOrder; ++w) {
-                double re = 0.0, im = 0.0;
-                for (int q = 0; q < kMinorThreads / 32; ++q) {
-                    re += red[q][2 * w];
-                    im += red[q][2 * w + 1];
-                }
-                cx<double> v = z * mk<double>(re, im);
-                out[2 * w] = w <= order ? v.re : 0.0;
-                out[2 * w + 1] = w <= order ? v.im : 0.0;
-            }
+            write_unit(pl, u, order, s_zs, red, kMinorThreads / 32);
             if (s_bad) atomicOr(pl.unit_flag + p, 1);
         }
         __syncthreads();
     }
+}
+
+// ---- the same for large patterns on a CTA pair (thread-block cluster of two) ----------
+// The packed 2n x 2n inverse of a pattern with n up to 112 clicks (403 KB in FP64 or
+// float-float) exceeds one SM's shared memory: the two CTAs of a cluster hold half of its
+// rows each and reach the other half through distributed shared memory.  The sweep
+// operator runs on both halves at once (each CTA updates its own entries; the pivot
+// columns are staged into both CTAs, one cluster barrier per pivot); the group terms are
+// split over the 512 threads of the pair.
+constexpr int kPairMaxN = kApproxMaxN;
+
+// rows [0, rsplit) hold about half of the packed entries of an N x N upper triangle
+__host__ __device__ inline int pair_split_row(int N) {
+    const int half = (N * (N + 1) / 2 + 1) / 2;
+    int r = 0, acc = 0;
+    while (r < N && acc + (N - r) <= half) { acc += N - r; ++r; }
+    return r > 0 ? r : 1;
+}
+__host__ __device__ inline int pair_part_entries(int N) {  // the larger half
+    const int r = pair_split_row(N), lo = r * N - r * (r - 1) / 2, tot = N * (N + 1) / 2;
+    return lo > tot - lo ? lo : tot - lo;
+}
+
+template <typename R>
+__device__ void sweep_inverse_pair(cg::cluster_group &cl, int rank, int M, const double *__restrict__ O,
+                                   const int *modes, int n, double cs, double sn, cx<R> *Gl, cx<R> *stage,
+                                   cx<R> *stage_peer, int rsplit, int off1, int *s_bad, double *s_zs) {
+    const int t = threadIdx.x;
+    const int N = 2 * n, N2 = 2 * M;
+    const int r_lo = rank ? rsplit : 0, r_hi = rank ? N : rsplit;
+    const int base = rank ? off1 : 0;
+    auto lidx = [&](int i, int j) { return i * N - (i * (i - 1)) / 2 + (j - i) - base; };  // own row i <= j
+    for (int f = t; f < (r_hi - r_lo) * N; f += kMinorThreads) {
+        const int i = r_lo + f / N, j = f - (f / N) * N;
+        if (j < i) continue;
+        const int si = modes[i >> 1] + (i & 1) * M, sj = modes[j >> 1] + (j & 1) * M;
+        Gl[lidx(i, j)] = init_entry<R>(i == j, cs, sn, O[(size_t)si * N2 + sj]);
+    }
+    cx<R> *const cb0 = stage, *const cb1 = stage + N, *const cu = stage + 2 * N;
+    cx<R> *const pb0 = stage_peer, *const pb1 = stage_peer + N;
+    __syncthreads();
+    // pivot 0's column is row 0: rank 0's
+    if (rank == 0)
+        for (int i = t; i < N; i += kMinorThreads) {
+            const cx<R> v = Gl[lidx(0, i)];
+            cb0[i] = v;
+            pb0[i] = v;
+        }
+    cl.sync();
+    cx<double> zs = mk<double>(1.0, 0.0);
+    cx<R> dprev = mk<R>(R(1), R(0));
+    // own rows folded in pairs (r_lo + q, r_hi - 1 - q): fw entries per pair
+    const int nrows = r_hi - r_lo, npair = nrows >> 1, fw = 2 * N - r_lo - r_hi + 1, fE = npair * fw;
+    const int sp = kMinorThreads / fw, sq = kMinorThreads - sp * fw;
+    const int rmid = r_lo + npair;  // the unpaired middle row when nrows is odd
+    for (int k = 0; k < N; ++k) {
+        const cx<R> *cb = (k & 1) ? cb1 : cb0;
+        cx<R> *cbn = (k & 1) ? cb0 : cb1, *pbn = (k & 1) ? pb0 : pb1;
+        const cx<R> d = cb[k];
+        if (!(d.re > R(0)) && t == 0) *s_bad = 1;
+        if ((k & 1) && t == 0) zs = zs * widen(crsqrt(dprev * d));
+        dprev = d;
+        const cx<R> inv = cinv(d);
+        for (int i = t; i < N; i += kMinorThreads) cu[i] = cb[i] * inv;
+        __syncthreads();
+        // entries (i, j), i, j != k, of the own rows: e -= cb_i cu_j
+        int fp = t / fw, fq = t - fp * fw;
+        for (int f = t; f < fE; f += kMinorThreads) {
+            int i, j;
+            const int a = r_lo + fp;
+            if (fq < N - a) { i = a; j = a + fq; } else { i = r_hi - 1 - fp; j = i + (fq - (N - a)); }
+            if (i != k && j != k) {
+                cx<R> &e = Gl[lidx(i, j)];
+                e = cfms(e, cb[i], cu[j]);
+            }
+            fq += sq;
+            fp += sp;
+            if (fq >= fw) { fq -= fw; ++fp; }
+        }
+        if (nrows & 1)
+            for (int j = rmid + t; j < N; j += kMinorThreads)
+                if (rmid != k && j != k) {
+                    cx<R> &e = Gl[lidx(rmid, j)];
+                    e = cfms(e, cb[rmid], cu[j]);
+                }
+        __syncthreads();
+        // scale pivot k's row and column (own entries), stage pivot k + 1's column into
+        // both CTAs (the owner of each entry writes it)
+        const bool more = k + 1 < N;
+        for (int i = t; i < N; i += kMinorThreads) {
+            const int lo = i < k ? i : k, hi = i < k ? k : i;
+            if (i != k && lo >= r_lo && lo < r_hi) Gl[lidx(lo, hi)] = cu[i];
+            if (more) {
+                const int l2 = i < k + 1 ? i : k + 1, h2 = i < k + 1 ? k + 1 : i;
+                if (l2 >= r_lo && l2 < r_hi) {
+                    // entry (k, k + 1) is the one just scaled: cu[k + 1]
+                    const cx<R> v = i == k ? cu[k + 1] : Gl[lidx(l2, h2)];
+                    cbn[i] = v;
+                    pbn[i] = v;
+                }
+            }
+        }
+        if (t == 0 && k >= r_lo && k < r_hi) Gl[lidx(k, k)] = mk<R>(R(0), R(0)) - inv;
+        cl.sync();
+    }
+    if (t == 0) { s_zs[0] = zs.re; s_zs[1] = zs.im; }
+}
+
+template <typename R>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMinorThreads, 1)
+approx_minors_pair_kernel(int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int n_pat,
+                          int order, int n_single, unsigned long long *counter, ApproxPlan pl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int modes[128];
+    __shared__ long long s_u;
+    __shared__ int s_bad;
+    __shared__ double red[2 * (kMinorThreads / 32)][2 * (kMaxOrder + 1)];
+    __shared__ double s_zs[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), t = threadIdx.x;
+    const long long total = *pl.total;
+    for (;;) {
+        if (rank == 0 && t == 0) {
+            const long long v = (long long)atomicAdd(counter, 1ull);
+            s_u = v;
+            *cl.map_shared_rank(&s_u, 1) = v;
+        }
+        cl.sync();
+        const long long u = s_u;
+        if (u >= total) break;
+        const int p = unit_pattern(pl, n_pat, u);
+        const int n = pl.pat_n[p];
+        if (n <= n_single) {  // a pattern for the one-CTA kernel: both CTAs skip it
+            cl.sync();        // (every thread has read s_u before rank 0 writes the next)
+            continue;
+        }
+        const int l = (int)(u - pl.unit_off[p]), L = pl.pat_L[p];
+        const uint64_t wlo = pats[2 * p], whi = pats[2 * p + 1];
+        if (t == 0) {
+            int c = 0;
+            for (int i = 0; i < M; ++i) {
+                uint64_t w = i < 64 ? wlo : whi;
+                if (w >> (i & 63) & 1ull) modes[c++] = i;
+            }
+            s_bad = 0;
+        }
+        __syncthreads();
+        const int N = 2 * n, rsplit = pair_split_row(N), off1 = rsplit * N - rsplit * (rsplit - 1) / 2;
+        cx<R> *Gl = (cx<R> *)smem_raw;
+        cx<R> *stage = Gl + pair_part_entries(N);
+        cx<R> *stage_peer = cl.map_shared_rank(stage, rank ^ 1);
+        double sn, cs;
+        sincospi(2.0 * (double)l / (double)L, &sn, &cs);
+        const double rho = pl.pat_rho[p];
+        sn *= rho;
+        cs *= rho;
+        sweep_inverse_pair<R>(cl, rank, M, O, modes, n, cs, sn, Gl, stage, stage_peer, rsplit, off1, &s_bad, s_zs);
+        cx<R> *G0 = rank == 0 ? Gl : cl.map_shared_rank(Gl, 0);
+        cx<R> *G1 = rank == 1 ? Gl : cl.map_shared_rank(Gl, 1);
+        const GView<R> V{G0, G1, N, rsplit, off1};
+        GroupAcc<R> acc;
+        acc.zero();
+        bool bad = false;
+        group_terms<R>(V, n, order, rank * kMinorThreads + t, 2 * kMinorThreads, acc, bad);
+        if (bad) s_bad = 1;
+        // warp sums: rank 1's into rank 0's table (rows 8..15), then rank 0 writes the unit
+        double (*red0)[2 * (kMaxOrder + 1)] = rank == 0 ? red : cl.map_shared_rank(red, 0);
+        warp_group_sums<R>(acc, red0[rank * (kMinorThreads / 32) + (t >> 5)]);
+        __syncthreads();
+        if (rank == 1 && t == 0 && s_bad) atomicOr(cl.map_shared_rank(&s_bad, 0), 1);
+        cl.sync();
+        if (rank == 0 && t == 0) {
+            write_unit(pl, u, order, s_zs, red, 2 * (kMinorThreads / 32));
+            if (s_bad) atomicOr(pl.unit_flag + p, 1);
+        }
+        // the next ticket's barrier keeps both CTAs' shared memory live until the peer is done
+    }
+    cl.sync();
 }
 
 // ---- per-sector fit (maximum-entropy dual, damped Newton) ----------------------------
@@ -1334,7 +1587,7 @@ __global__ void approx_grad_status_kernel(int n_pat, const int32_t *__restrict__
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct ApproxOffsets {
-    size_t counter, total, overflow, info, pat_n, pat_L, pat_rho, unit_off, unit_flag, sec_off, pat_max,
+    size_t counter, total, overflow, info, counter2, pat_n, pat_L, pat_rho, unit_off, unit_flag, sec_off, pat_max,
         unit_D, sec_D, sec_part, end;
 };
 
@@ -1343,8 +1596,9 @@ ApproxOffsets approx_offsets(int n_pat, long long units, long long secs = 0) {
     o.counter = 0;
     o.total = 8;
     o.overflow = 16;
-    o.info = 24;
-    o.pat_n = align256(56);
+    o.info = 24;       // 6 long long
+    o.counter2 = 72;   // the CTA-pair minors kernel's work counter
+    o.pat_n = align256(80);
     o.pat_L = align256(o.pat_n + 4 * (size_t)n_pat);
     o.pat_rho = align256(o.pat_L + 4 * (size_t)n_pat);
     o.unit_off = align256(o.pat_rho + 8 * (size_t)n_pat);
@@ -1382,9 +1636,11 @@ template <typename R>
 int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *pats,
                int n_pat, int order, double *logP, double *kappa, double *err_bound, int32_t *status,
                double *curves = nullptr, int curve_K = -1, int curve_n = -1, int n_limit = -1) {
-    // patterns up to this size are taken (the packed inverse must fit in shared memory;
-    // a caller may lower it)
-    const int nmax_smem = n_limit > 0 && n_limit < MinorPrec<R>::nmax ? n_limit : MinorPrec<R>::nmax;
+    // patterns up to this size are taken: the packed inverse must fit in one CTA's shared
+    // memory, or (FP64 and float-float) in a CTA pair's; a caller may lower it
+    const int n_cap = MinorPrec<R>::pair ? kPairMaxN : MinorPrec<R>::nmax;
+    const int nmax_smem = n_limit > 0 && n_limit < n_cap ? n_limit : n_cap;
+    const int n_single = MinorPrec<R>::nmax;
     static_assert(kMaxK + 1 <= 4096, "sector table");
     if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
         int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
@@ -1398,14 +1654,15 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
                                                                         nmax_smem, pl);
     GBS_CUDA(ctx, cudaGetLastError());
-    approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, pl);
+    approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, n_single, pl);
     GBS_CUDA(ctx, cudaGetLastError());
     // size the workspace and the kernels' shared memory from one readback (units,
     // largest n, largest L, sectors); re-plan if the workspace had to grow
-    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.info, 32, cudaMemcpyDeviceToHost, ctx->stream));
+    GBS_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, pl.info, 40, cudaMemcpyDeviceToHost, ctx->stream));
     GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const long long units = ((long long *)ctx->pinned)[0], secs = ((long long *)ctx->pinned)[3];
     const int nmax = (int)((long long *)ctx->pinned)[1], Lmax = (int)((long long *)ctx->pinned)[2];
+    const int nsmall = (int)((long long *)ctx->pinned)[4];
     const size_t need = approx_offsets(n_pat, units, secs).end;
     if (need > ctx->ws_bytes) {
         int st = gbs_ws_ensure(ctx, need);
@@ -1413,24 +1670,37 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
         pl = approx_plan_from(ctx->ws, n_pat);
         approx_plan_kernel<<<n_pat, kPlanThreads, plan_smem, ctx->stream>>>(M, O, pats, n_pat, order,
                                                                             nmax_smem, pl);
-        approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, pl);
+        approx_scan_kernel<<<1, 32, 0, ctx->stream>>>(n_pat, nocap, n_single, pl);
         GBS_CUDA(ctx, cudaGetLastError());
     }
     pl = approx_plan_from(ctx->ws, n_pat, units, secs);
-    GBS_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, 8, ctx->stream));  // work counter
-    // the packed inverse and four staged pivot columns
-    const size_t minor_smem = sizeof(cx<R>) * ((size_t)sym(2 * (nmax > 0 ? nmax : 1)) + 8 * (size_t)(nmax > 0 ? nmax : 1));
-    GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)minor_smem));
-    int nb = 0;
-    GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, approx_minors_kernel<R>, kMinorThreads,
-                                                                minor_smem));
-    if (nb < 1) nb = 1;
+    GBS_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, 8, ctx->stream));  // work counters
+    GBS_CUDA(ctx, cudaMemsetAsync((char *)ctx->ws + approx_offsets(n_pat, 0).counter2, 0, 8, ctx->stream));
     int st = gbs_timing_begin(ctx);
     if (st) return st;
-    approx_minors_kernel<R><<<ctx->num_sms * nb, kMinorThreads, minor_smem, ctx->stream>>>(
-        M, O, pats, n_pat, order, (unsigned long long *)ctx->ws, pl);
-    GBS_CUDA(ctx, cudaGetLastError());
+    if (nsmall > 0) {
+        // the packed inverse and four staged pivot columns
+        const size_t minor_smem = sizeof(cx<R>) * ((size_t)sym(2 * nsmall) + 8 * (size_t)nsmall);
+        GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)minor_smem));
+        int nb = 0;
+        GBS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, approx_minors_kernel<R>, kMinorThreads,
+                                                                    minor_smem));
+        if (nb < 1) nb = 1;
+        approx_minors_kernel<R><<<ctx->num_sms * nb, kMinorThreads, minor_smem, ctx->stream>>>(
+            M, O, pats, n_pat, order, n_single, (unsigned long long *)ctx->ws, pl);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
+    if constexpr (MinorPrec<R>::pair) if (nmax > n_single) {
+        // half of the packed inverse and three staged columns per CTA of a pair
+        const size_t pair_smem = sizeof(cx<R>) * ((size_t)pair_part_entries(2 * nmax) + 6 * (size_t)nmax);
+        GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_pair_kernel<R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
+        approx_minors_pair_kernel<R><<<(ctx->num_sms / 2) * 2, kMinorThreads, pair_smem, ctx->stream>>>(
+            M, O, pats, n_pat, order, n_single,
+            (unsigned long long *)((char *)ctx->ws + approx_offsets(n_pat, 0).counter2), pl);
+        GBS_CUDA(ctx, cudaGetLastError());
+    }
     st = gbs_timing_end(ctx);
     if (st) return st;
     const size_t dft_smem = sizeof(double) * 2 * (size_t)Lmax;

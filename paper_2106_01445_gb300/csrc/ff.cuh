@@ -48,3 +48,31 @@ __device__ __forceinline__ ff ff_rsqrt(ff x) {
     return ff_quick_two_sum(y, 0.5f * y * r.hi);
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// Fused forms for complex products (FMA error-free products of the high parts, the sum of
+// the high parts by TwoSum, every low-order term in one FMA chain, one renormalisation):
+// x0 y0 + x1 y1 in 19 FP32 operations and e - x0 y0 - x1 y1 in 27, against 46 and 68 for
+// the same through separate products and sums; error ~2^-46 of the terms' magnitudes.
+__device__ __forceinline__ ff ff_dot2(ff x0, ff y0, ff x1, ff y1) {
+    const float p0 = x0.hi * y0.hi, q0 = fmaf(x0.hi, y0.hi, -p0);
+    const float p1 = x1.hi * y1.hi, q1 = fmaf(x1.hi, y1.hi, -p1);
+    const ff s = ff_two_sum(p0, p1);
+    float lo = s.lo + (q0 + q1);
+    lo = fmaf(x0.hi, y0.lo, lo);
+    lo = fmaf(x0.lo, y0.hi, lo);
+    lo = fmaf(x1.hi, y1.lo, lo);
+    lo = fmaf(x1.lo, y1.hi, lo);
+    return ff_quick_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_fms2(ff e, ff x0, ff y0, ff x1, ff y1) {
+    const float p0 = x0.hi * y0.hi, q0 = fmaf(x0.hi, y0.hi, -p0);
+    const float p1 = x1.hi * y1.hi, q1 = fmaf(x1.hi, y1.hi, -p1);
+    const ff s1 = ff_two_sum(e.hi, -p0);
+    const ff s2 = ff_two_sum(s1.hi, -p1);
+    float lo = e.lo + (s1.lo + s2.lo) - (q0 + q1);
+    lo = fmaf(-x0.hi, y0.lo, lo);
+    lo = fmaf(-x0.lo, y0.hi, lo);
+    lo = fmaf(-x1.hi, y1.lo, lo);
+    lo = fmaf(-x1.lo, y1.hi, lo);
+    return ff_quick_two_sum(s2.hi, lo);
+}

@@ -2,10 +2,17 @@
 50-mode and 100-mode workloads (Methods, "Approximation method"), for the GPU parity
 tests that the oracle is too slow to run inline.
 
-Only the oracle is called.  Every entry also records the oracle's own spread: how far
-its log P moves when the contour radius is moved by -3% and +0.5% (the estimate does
-not depend on the radius mathematically, so the spread measures the rounding of the
-ill-conditioned extrapolation to the all-clicked point at this pattern).
+Only the oracle is called.  Every entry also records two measures of how sharply the
+estimate depends on rounding at that pattern (each sector's fit extrapolates to the
+all-clicked point, which is ill-conditioned at large n and order 4):
+  spread   -- how far the oracle's log P moves when its contour radius is moved by -3%
+              (or +0.5% near rho = 1): the estimate does not depend on the radius
+              mathematically;
+  sens     -- for relative table noise delta = 1e-12 (the rounding of FP64 minors), 3e-11
+              (float-float: its unit roundoff ~2^-48 is 32 times FP64's) and 1e-5 (FP32
+              minors): the largest change of log P when every entry
+              of the oracle's moment tables D_w^(k) is multiplied by (1 + delta u), u
+              uniform in [-1, 1] (four seeds), and the fits are run again.
 
     python tests/golden/make_approx_large.py [--workers 8]
 """
@@ -33,6 +40,7 @@ PLAN = [
 def job(args):
     name, idx, order = args
     sys.path.insert(0, ROOT)
+    import numpy as np
     import gbs_inputs as g
     import oracle
     from oracle import approx as ap
@@ -41,15 +49,19 @@ def job(args):
     modes = g.pattern_modes(c.patterns()[idx])
     t0 = time.time()
     lp, info = ap.approx_logprob(st.O, st.logdet, c.M, modes, order)
-    rho = info["rho"]
-    spread = 0.0
-    for f in (0.97, 1.005):
-        if rho * f < 1.0:
-            continue
-        lp2, _ = ap.approx_logprob(st.O, st.logdet, c.M, modes, order, rho=rho * f)
-        spread = max(spread, abs(lp2 - lp))
+    rho, D = info["rho"], info["D"]
+    f = 0.97 if rho * 0.97 >= 1.0 else 1.005
+    lp2, _ = ap.approx_logprob(st.O, st.logdet, c.M, modes, order, rho=rho * f)
+    sens = {}
+    for delta in (1e-12, 3e-11, 1e-5):
+        worst = 0.0
+        for seed in range(4):
+            u = np.random.default_rng(seed).uniform(-1.0, 1.0, size=D.shape)
+            lpn, _, _ = ap.logprob_from_tables(D * (1.0 + delta * u), len(modes), order, rho, st.logdet)
+            worst = max(worst, abs(lpn - lp))
+        sens["%g" % delta] = worst
     return dict(workload=name, index=int(idx), n=len(modes), order=order, logP=lp, rho=rho, K=int(info["K"]),
-                flag=int(info["flag"]), spread=spread, seconds=time.time() - t0)
+                flag=int(info["flag"]), spread=abs(lp2 - lp), sens=sens, seconds=time.time() - t0)
 
 
 def main():
