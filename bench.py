@@ -645,22 +645,25 @@ def run_workloads(dev, stream, meas, fp32_peak):
                                   "status_ok_fraction": float((exa["status"] == 0).mean()),
                                   "max_err_bound": float(np.nanmax(exa["err_bound"]))}}
     for order in (2, 3, 4):
-        ms, kms, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, order=order, precision="fp32"))
-        a = host(out)
-        units = (a["kappa"].astype(np.int64) + 1) // 2 + 1
-        fl = float(sum(u * approx_unit_flops(int(k), order) for u, k in zip(units, n)))
-        # the anchors against the exact sum: float-float minors (n = 30 <= 79)
-        aa = host(ctx.prob(st["O"], st["logdet"], ad, order=order, precision="ff"))
-        ok = (exa["status"] == 0) & np.isin(aa["status"], (0, 7))
-        rel = np.abs(np.expm1(aa["logP"][ok] - exa["logP"][ok]))
-        entry["order%d_fp32" % order] = {
-            "ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
-            "status_ok_fraction": float((a["status"] == 0).mean()),
-            "fit_fallback_fraction": float((a["status"] == 7).mean()),
-            "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<float>", "kernel_ms": kms,
-                                "flops": fl, "achieved_tflops": fl / (kms * 1e-3) / 1e12,
-                                "peak_tflops": fp32_peak / 1e12, "frac": fl / (kms * 1e-3) / fp32_peak},
-            "anchors_ff_vs_exact": {"median_rel_dP": float(np.median(rel)), "max_rel_dP": float(rel.max())}}
+        for prec in ("fp32", "auto"):
+            ms, kms, out = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, order=order, precision=prec))
+            a = host(out)
+            units = (a["kappa"].astype(np.int64) + 1) // 2 + 1
+            fl = float(sum(u * approx_unit_flops(int(k), order) for u, k in zip(units, n)))
+            e = {"ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
+                 "status_ok_fraction": float((a["status"] == 0).mean()),
+                 "fit_fallback_fraction": float((a["status"] == 7).mean()),
+                 "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<%s>%s" % (
+                     "float" if prec == "fp32" else "ff", "" if prec == "fp32" else " and approx_minors_pair_kernel<ff>"),
+                     "kernel_ms": kms, "flops": fl, "achieved_tflops": fl / (kms * 1e-3) / 1e12,
+                     "peak_tflops": fp32_peak / 1e12, "frac": fl / (kms * 1e-3) / fp32_peak}}
+            if prec == "auto":
+                # the anchors against the exact sum: float-float minors (n = 30)
+                aa = host(ctx.prob(st["O"], st["logdet"], ad, order=order, precision="ff"))
+                ok = (exa["status"] == 0) & np.isin(aa["status"], (0, 7))
+                rel = np.abs(np.expm1(aa["logP"][ok] - exa["logP"][ok]))
+                e["anchors_ff_vs_exact"] = {"median_rel_dP": float(np.median(rel)), "max_rel_dP": float(rel.max())}
+            entry["order%d_%s" % (order, "fp32" if prec == "fp32" else "auto_ff")] = e
     res["m100_approx"] = entry
 
     # ---- the paper's device shape (30 modes, 15 inputs squeezed r = 1.4, lossless): the
@@ -740,6 +743,52 @@ def run_workloads(dev, stream, meas, fp32_peak):
     return res
 
 
+def run_m100(args):
+    """The 100-mode workload's approximation at orders 2, 3 and 4 in the automatic
+    precision (float-float minors; patterns above 79 clicks on CTA pairs) over its first
+    --m100-npat patterns (all 16384 by default), one timed call per order (CUDA events on
+    the library's stream); the fit-fallback fraction and the status counts per order.
+    Written to the side file; the printed line is a summary."""
+    import torch
+    from paper_2106_01445_gb300 import build as b
+    b.build()
+    from paper_2106_01445_gb300.api import Context, patterns_tensor
+    c = g.CONFIGS["m100_approx"]
+    U, r = c.unitary(), c.squeezing()
+    pats = c.patterns()[:args.m100_npat]
+    n = np.array([len(g.pattern_modes(p)) for p in pats])
+    ctx = Context(0)
+    stream = torch.cuda.current_stream()
+    st = ctx.build_state(U, r, c.eta)
+    pd = patterns_tensor(pats, ctx.device)
+    res = {"workload": c.name, "patterns": int(len(pats)), "clicks": [int(n.min()), int(n.max())],
+           "patterns_above_79_clicks": int((n > 79).sum()), "precision": "auto (float-float minors)"}
+    for order in args.m100_orders:
+        torch.cuda.synchronize()
+        ctx.timing(True)
+        ctx.timing_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = ctx.prob(st["O"], st["logdet"], pd, order=order, precision="auto")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, nl = ctx.timing_read(reset=True)
+        ctx.timing(False)
+        stt = out["status"].cpu().numpy()
+        lp = out["logP"].cpu().numpy()
+        res["order%d" % order] = {"ms": e0.elapsed_time(e1), "minors_kernel_ms": kms,
+                                  "patterns_per_s": len(pats) / (e0.elapsed_time(e1) * 1e-3),
+                                  "status_counts": {str(k): int(v) for k, v in zip(*np.unique(stt, return_counts=True))},
+                                  "fit_fallback_fraction": float((stt == 7).mean()),
+                                  "fit_fallback_fraction_above_79": float((stt[n > 79] == 7).mean()) if (n > 79).any() else None,
+                                  "finite_logP_fraction": float(np.isfinite(lp).mean())}
+        print(json.dumps({"order": order, **res["order%d" % order]}), flush=True)
+    args.detail_out = args.detail_out.replace("bench_detail", "bench_m100")
+    where = write_detail(args, res)
+    print(json.dumps({"m100": {k: v for k, v in res.items() if not k.startswith("order")}, "detail": where}))
+    return 0
+
+
 def run_profile_case(args):
     """One warm-up and one measured call of a kernel path, for ncu captures."""
     import torch
@@ -798,8 +847,11 @@ def main():
     ap.add_argument("--profile", choices=["sweep", "approx", "grad", "peak"], default=None,
                     help="run one kernel path twice (for ncu) instead of the benchmark")
     ap.add_argument("--order", type=int, default=4)
-    ap.add_argument("--workloads", choices=["all", "none"], default="all",
-                    help="also run one pass of the other four workloads (on rank 0)")
+    ap.add_argument("--workloads", choices=["all", "none", "m100"], default="all",
+                    help="also run one pass of the other four workloads (on rank 0); m100: only the "
+                         "100-mode approximation at orders 2-4 over --m100-npat patterns")
+    ap.add_argument("--m100-npat", type=int, default=16384)
+    ap.add_argument("--m100-orders", type=int, nargs="+", default=[2, 3, 4])
     ap.add_argument("--npat", type=int, default=128)
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other three precisions of the exact sweep (short runs)")
@@ -808,6 +860,8 @@ def main():
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)
+    if args.workloads == "m100":
+        return run_m100(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
