@@ -555,6 +555,7 @@ def run_workloads(dev, stream, meas, fp32_peak):
                 "ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
                 "status_ok_fraction": float((a["status"] == 0).mean()),
                 "fit_fallback_fraction": float((a["status"] == 7).mean()),
+                "below_fp32_floor_fraction": float((a["status"] == 9).mean()),
                 "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<%s>" % (
                     {"fp32": "float", "ff": "ff", "fp64": "double"}[prec]), "kernel_ms": kms, "flops": fl,
                     "achieved_tflops": fl / (kms * 1e-3) / 1e12, "peak_tflops": peak / 1e12,
@@ -653,6 +654,7 @@ def run_workloads(dev, stream, meas, fp32_peak):
             e = {"ms": ms, "patterns_per_s": len(pats) / (ms * 1e-3),
                  "status_ok_fraction": float((a["status"] == 0).mean()),
                  "fit_fallback_fraction": float((a["status"] == 7).mean()),
+                 "below_fp32_floor_fraction": float((a["status"] == 9).mean()),
                  "roofline_minors": {"bound": "alu", "kernel": "approx_minors_kernel<%s>%s" % (
                      "float" if prec == "fp32" else "ff", "" if prec == "fp32" else " and approx_minors_pair_kernel<ff>"),
                      "kernel_ms": kms, "flops": fl, "achieved_tflops": fl / (kms * 1e-3) / 1e12,

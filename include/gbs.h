@@ -45,8 +45,12 @@ typedef enum {
                               fixed number of steps and report GBS_E_FIT), and no kernel waits
                               on another */
     GBS_E_FIT = 7,         /* approximation: a sector fit fell back to a lower order */
-    GBS_E_RANGE = 8        /* GBS_FX: a pivot determinant below 2^-8 or an entry of O beyond
+    GBS_E_RANGE = 8,       /* GBS_FX: a pivot determinant below 2^-8 or an entry of O beyond
                               4 left the fixed-point range (evaluate in GBS_DD instead) */
+    GBS_E_FLOOR = 9        /* approximation with FP32 minors: sectors below the FP32 noise floor
+                              (1e-6 of the largest tilted sector) could carry 1e-4 or more of the
+                              estimate, which FP32 moments cannot resolve; logP is returned but
+                              unreliable: evaluate with GBS_FF or GBS_FP64 instead */
 } gbs_status;
 
 typedef enum {

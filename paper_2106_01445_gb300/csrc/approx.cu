@@ -109,7 +109,8 @@ template <> struct MinorPrec<double> {
     static constexpr int min_blocks = 1;
     static constexpr int nmax = 79;
     static constexpr bool pair = true;  // n in (nmax, 112] on a CTA pair
-    static constexpr double sector_eps = 1e-12;  // tilted sectors below this share of the largest: noise
+    static constexpr double sector_eps = 1e-12;
+    static constexpr bool floor_flag = false;  // below the floor: the oracle's own reading of negligible sectors
 };
 template <> struct MinorPrec<ff> {
     // two CTAs per SM: capped at 128 registers (a few spills) it runs 14% faster than one
@@ -118,12 +119,14 @@ template <> struct MinorPrec<ff> {
     static constexpr int nmax = 79;
     static constexpr bool pair = true;
     static constexpr double sector_eps = 1e-12;
+    static constexpr bool floor_flag = false;
 };
 template <> struct MinorPrec<float> {
     static constexpr int min_blocks = 2;  // 127 registers: two CTAs per SM
     static constexpr int nmax = 112;
     static constexpr bool pair = false;
     static constexpr double sector_eps = 1e-6;  // moments resolved to ~1e-7 K
+    static constexpr bool floor_flag = true;    // below it: unresolved, reported (GBS_E_FLOOR)
 };
 
 // ---- plan: sector bound and DFT length per pattern ---------------------------------
@@ -1053,7 +1056,12 @@ __global__ void approx_curve_scale_kernel(int curve_K, int n, const double *__re
 }
 
 // per pattern (one warp): sum_k part_k rho^{-k} in logs (the tables are tilted by rho^k)
+// floor_eps > 0 (FP32 minors, whose moments resolve sectors only down to that share of the
+// largest): a sector k >= n below the floor carries at most floor_eps * (largest) of tilted
+// mass, so its all-clicked point at most that; when those bounds add up to kFlagShare of the
+// estimate, the estimate may be missing what the precision cannot resolve: GBS_E_FLOOR
 __global__ void __launch_bounds__(kSumThreads) approx_sum_kernel(int n_pat, const double *__restrict__ logdet,
+                                                               double floor_eps,
                                                                ApproxPlan pl, double *__restrict__ logP,
                                                                double *__restrict__ kappa,
                                                                double *__restrict__ err_bound,
@@ -1076,21 +1084,26 @@ __global__ void __launch_bounds__(kSumThreads) approx_sum_kernel(int n_pat, cons
     for (int k = lane; k < L; k += 32)
         if (part[k] != 0.0) top = fmax(top, log(fabs(part[k])) - k * lr);
     for (int off = 16; off; off >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, off));
-    double s = 0.0, sf = 0.0;
+    double s = 0.0, sf = 0.0, sd = 0.0;
+    const double lfloor = floor_eps > 0.0 && pl.pat_max[p] > 0.0 ? log(floor_eps * pl.pat_max[p]) : -INFINITY;
     for (int k = lane; k < L; k += 32)
         if (part[k] != 0.0) {
             const double w = exp(log(fabs(part[k])) - k * lr - top);
             s += w;
             if (part[k] < 0.0) sf += w;
+        } else if (k >= n && n > 0 && isfinite(lfloor)) {
+            sd += exp(lfloor - k * lr - (isfinite(top) ? top : lfloor));
         }
     s = warp_sum_bcast(s);
     sf = warp_sum_bcast(sf);
+    sd = warp_sum_bcast(sd);
     if (lane == 0) {
         logP[p] = s > 0.0 ? -0.5 * (*logdet) + top + log(s) : -INFINITY;
         if (kappa) kappa[p] = (double)(L - 1);
         if (err_bound) err_bound[p] = nan("");
         int st = GBS_OK;
         if (pl.unit_flag[p]) st = GBS_E_NOT_SPD;
+        else if (sd > 0.0 && (!(s > 0.0) || sd >= kFlagShare * s)) st = GBS_E_FLOOR;
         else if (sf >= kFlagShare * s) st = GBS_E_FIT;
         if (status) status[p] = st;
     }
@@ -1728,7 +1741,7 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
         GBS_CUDA(ctx, cudaGetLastError());
     }
     approx_sum_kernel<<<(n_pat + kSumThreads / 32 - 1) / (kSumThreads / 32), kSumThreads, 0, ctx->stream>>>(
-        n_pat, logdet, pl, logP, kappa, err_bound, status);
+        n_pat, logdet, MinorPrec<R>::floor_flag ? MinorPrec<R>::sector_eps : 0.0, pl, logP, kappa, err_bound, status);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }
