@@ -10,7 +10,7 @@ SO_PATH = os.path.join(_PKG, "libgbs.so")
 
 GBS_OK, GBS_E_INVALID, GBS_E_CUDA, GBS_E_NOMEM, GBS_E_NONPOSITIVE, GBS_E_NOT_SPD, GBS_E_TIMEOUT, \
     GBS_E_FIT, GBS_E_RANGE, GBS_E_FLOOR = range(10)
-GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF, GBS_AUTO = 0, 1, 2, 3, 4, 5
+GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF, GBS_AUTO, GBS_FX192 = 0, 1, 2, 3, 4, 5, 6
 STATUS_NAMES = {0: "ok", 1: "invalid", 2: "cuda", 3: "nomem", 4: "nonpositive", 5: "not_spd",
                 6: "timeout", 7: "fit", 8: "range", 9: "floor"}
 

@@ -11,11 +11,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF, GBS_AUTO
+from ._lib import GbsError, GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FF, GBS_AUTO, GBS_FX192
 
 PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32_SPLIT, "dd": GBS_DD, "fx": GBS_FX, "ff": GBS_FF,
-              "auto": GBS_AUTO, GBS_FP64: GBS_FP64, GBS_FP32_SPLIT: GBS_FP32_SPLIT, GBS_DD: GBS_DD, GBS_FX: GBS_FX,
-              GBS_FF: GBS_FF, GBS_AUTO: GBS_AUTO}
+              "auto": GBS_AUTO, "fx192": GBS_FX192, GBS_FP64: GBS_FP64, GBS_FP32_SPLIT: GBS_FP32_SPLIT,
+              GBS_DD: GBS_DD, GBS_FX: GBS_FX, GBS_FF: GBS_FF, GBS_AUTO: GBS_AUTO, GBS_FX192: GBS_FX192}
 
 
 def _ptr(t) -> ctypes.c_void_p:

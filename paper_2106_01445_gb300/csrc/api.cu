@@ -300,10 +300,12 @@ int gbs_prob(gbs_ctx *ctx, int M, const double *O, const double *logdet_sigmaQ,
     if (M < 1 || M > 128 || n_pat < 0 || !O || !logdet_sigmaQ || (n_pat && (!patterns || !logP)))
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: bad arguments (M=%d, n_pat=%d)", M, n_pat);
     if (precision != GBS_FP64 && precision != GBS_FP32_SPLIT && precision != GBS_DD && precision != GBS_FX &&
-        precision != GBS_FF && precision != GBS_AUTO)
+        precision != GBS_FF && precision != GBS_AUTO && precision != GBS_FX192)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: unknown precision %d", precision);
     if (order == 0 && precision == GBS_FF)
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: float-float serves the approximation (order > 0) only");
+    if (order > 0 && precision == GBS_FX192)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_prob: 192-bit fixed point serves the exact sum (order 0) only");
     if (n_pat == 0) return GBS_OK;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     if (order == 0 && precision == GBS_AUTO)

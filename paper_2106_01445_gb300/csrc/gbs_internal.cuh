@@ -28,10 +28,10 @@ struct gbs_ctx {
     void *aux = nullptr;
     size_t aux_bytes = 0;
     // persistent-grid sizes of the sweep kernels (CTAs per SM), by precision
-    int sweep_blocks_per_sm[4] = {0, 0, 0, 0};
+    int sweep_blocks_per_sm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // prefix levels looped inside one sweep unit, by precision (-1: the default);
     // set by gbs_autotune
-    int sweep_split[4] = {-1, -1, -1, -1};
+    int sweep_split[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // optional event timing of the sweep kernel launches
     static const int kTimingRing = 4096;
     bool timing = false;

@@ -23,8 +23,11 @@
 // double with TwoSum, stored per unit, and summed per pattern in unit order.
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "dd.cuh"
 #include "fx.cuh"
+#include "fx6.cuh"
 #include "gbs_internal.cuh"
 #include "zc.cuh"
 
@@ -86,8 +89,25 @@ template <> struct Prec<fx> {
     using Node = fxe;  // prefactors m 2^e
     static constexpr bool fixed = true;
     static constexpr int wrow = 3;  // offset rows (u'0, u'1, t) of U = B R^{-T}
+    using Piv = fx_piv;
     static constexpr double u = 7.888609052210118e-31, u_sum = 1.2325951644078309e-32;
 };
+// Q16.176 fixed point (fx6.cuh): the same sweep 64 bits wider, per-term relative error far
+// below 2^-164; prefactors, sub-unit and unit sums as m 2^e with 192-bit mantissas (fxe6)
+// and the unit partials summed exactly per pattern, for sums that cancel beyond ~1e20.
+template <> struct Prec<fx6> {
+    static constexpr int B = 2, idx = GBS_FX192;
+    using Tau = fxe6;
+    using Abs = float;
+    using Node = fxe6;
+    static constexpr bool fixed = true;
+    static constexpr int wrow = 3;
+    using Piv = fx6_piv;
+    static constexpr double u = 4.2351647362715017e-50, u_sum = 6.617444900424222e-52;  // 2^-164, 2^-170
+};
+// doubles per unit partial: (hi, lo, sum |terms|), or the 192-bit fxe6 sum (mantissa in three
+// words, exponent) and sum |terms| for fx6
+template <typename T> constexpr int partial_words() { return std::is_same<T, fx6>::value ? 5 : 3; }
 
 // Complex FP64 (the sector-resolved binned sweep at a complex generating variable t):
 // the matrices I - t O_Z are accretive for |t| <= 1, so the unpivoted recursion is safe and
@@ -118,6 +138,7 @@ template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ dd rsq<dd>(dd x) { return dd_rsqrt(x); }
 template <> __device__ __forceinline__ fx rsq<fx>(fx x) { return fx_rsqrt(x); }
+template <> __device__ __forceinline__ fx6 rsq<fx6>(fx6 x) { return fx6_rsqrt(x); }
 
 // 1/sqrt(det) as a prefix factor, in the Tau type of the precision, given rs = rsq(det)
 // (FP32 prefactors are taken in FP64)
@@ -125,12 +146,14 @@ __device__ __forceinline__ double tau_of(float det, float) { return rsqrt((doubl
 __device__ __forceinline__ double tau_of(double, double rs) { return rs; }
 __device__ __forceinline__ dd tau_of(dd, dd rs) { return rs; }
 __device__ __forceinline__ dd tau_of(fx, fx rs) { return fx_to_dd(rs); }
+__device__ __forceinline__ fxe6 tau_of(fx6, fx6 rs) { return fxe6_from(rs); }
 __device__ __forceinline__ zc tau_of(zc, zc rs) { return rs; }
 __device__ __forceinline__ zf tau_of(zf, zf rs) { return rs; }
 
 // constants and conversions of the working type
 template <typename T> __device__ __forceinline__ T konst(double v) { return T(v); }
 template <> __device__ __forceinline__ fx konst<fx>(double v) { return fx_from_double(v); }
+template <> __device__ __forceinline__ fx6 konst<fx6>(double v) { return fx6_from_double(v); }
 __device__ __forceinline__ float to_node(float x) { return x; }
 __device__ __forceinline__ double to_node(double x) { return x; }
 __device__ __forceinline__ dd to_node(dd x) { return x; }
@@ -141,12 +164,16 @@ template <typename N, typename T> __device__ __forceinline__ N node_times(const 
 template <> __device__ __forceinline__ fxe node_times<fxe, fx>(const fxe &p, const fx &rs) { return fxe_mul(p, rs); }
 template <typename N> __device__ __forceinline__ N node_one() { return N(1.0); }
 template <> __device__ __forceinline__ fxe node_one<fxe>() { return fxe_one(); }
+template <> __device__ __forceinline__ fxe6 node_one<fxe6>() { return fxe6(1.0); }
+template <> __device__ __forceinline__ fxe6 node_times<fxe6, fx6>(const fxe6 &p, const fx6 &rs) { return fxe_mul(p, rs); }
 // product of two non-negative factors
 template <typename T> __device__ __forceinline__ T mul_pos(T a, T b) { return a * b; }
 template <> __device__ __forceinline__ fx mul_pos<fx>(fx a, fx b) { return fx_mul_uu(a, b); }
+template <> __device__ __forceinline__ fx6 mul_pos<fx6>(fx6 a, fx6 b) { return fx_mul_uu(a, b); }
 // pivot check: 0 fine, 1 not positive (or NaN), 2 outside the fixed-point range
 template <typename T> __device__ __forceinline__ int pivot_bad(T det) { return det > T(0) ? 0 : 1; }
 template <> __device__ __forceinline__ int pivot_bad<fx>(fx det) { return fx_pivot_bad(det); }
+template <> __device__ __forceinline__ int pivot_bad<fx6>(fx6 det) { return fx_pivot_bad(det); }
 // complex pivots: their determinants may have any argument in (-pi, pi); only zero or NaN is bad
 template <> __device__ __forceinline__ int pivot_bad<zc>(zc det) {
     return fabs(det.re) + fabs(det.im) > 0.0 ? 0 : 1;
@@ -162,12 +189,16 @@ template <typename T> __device__ __forceinline__ T fms2(T c, T a0, T b0, T a1, T
 template <> __device__ __forceinline__ dd fms2<dd>(dd c, dd a0, dd b0, dd a1, dd b1) { return dd_fms2(c, a0, b0, a1, b1); }
 template <typename T> __device__ __forceinline__ T det2(T p00, T p01, T p11) { return dot2(p00, p11, -p01, p01); }
 template <> __device__ __forceinline__ fx det2<fx>(fx p00, fx p01, fx p11) { return fx_det2(p00, p01, p11); }
+template <> __device__ __forceinline__ fx6 det2<fx6>(fx6 p00, fx6 p01, fx6 p11) { return fx_det2(p00, p01, p11); }
 
 // an entry of A = I - O from its FP64 data (exact in double-double)
 template <typename T> __device__ __forceinline__ T a_entry(double delta, double o) { return (T)(delta - o); }
 template <> __device__ __forceinline__ dd a_entry<dd>(double delta, double o) { return dd_two_sum(delta, -o); }
 template <> __device__ __forceinline__ fx a_entry<fx>(double delta, double o) {
     return fx_from_double(delta) - fx_from_double(o);
+}
+template <> __device__ __forceinline__ fx6 a_entry<fx6>(double delta, double o) {
+    return fx6_from_double(delta) - fx6_from_double(o);
 }
 
 // the same with the generating variable t of the complex binned sweep: I - t O
@@ -188,11 +219,13 @@ __device__ __forceinline__ float abs_part(float x) { return x; }
 __device__ __forceinline__ double abs_part(double x) { return x; }
 __device__ __forceinline__ double abs_part(dd x) { return x.hi; }
 __device__ __forceinline__ float abs_part(fx x) { return (float)(int32_t)x.w[3] * (1.0f / 65536.0f); }
+__device__ __forceinline__ float abs_part(fx6 x) { return (float)(int32_t)x.w[5] * (1.0f / 65536.0f); }
 __device__ __forceinline__ bool is_nan(float x) { return x != x; }
 __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 __device__ __forceinline__ bool is_nan(zc x) { return zc_nan(x); }
 __device__ __forceinline__ bool is_nan(zf x) { return zf_nan(x); }
+__device__ __forceinline__ bool is_nan(const fxe6 &) { return false; }
 // a thread's subtree sum as (hi, lo) doubles
 __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
@@ -273,6 +306,7 @@ template <typename T> __device__ __forceinline__ void acc_add(Acc<T> &a, T x) {
 // double-double sums need no further compensation; fixed-point sums are exact
 template <> __device__ __forceinline__ void acc_add<dd>(Acc<dd> &a, dd x) { a.hi += x; }
 template <> __device__ __forceinline__ void acc_add<fx>(Acc<fx> &a, fx x) { a.hi += x; }
+template <> __device__ __forceinline__ void acc_add<fx6>(Acc<fx6> &a, fx6 x) { a.hi += x; }
 
 // (hi, lo) += sc * (x_hi + x_lo) for one thread's subtree sum
 __device__ __forceinline__ void unit_add(double &h, double &l, double sc, double xh, double xl) {
@@ -288,6 +322,7 @@ __device__ __forceinline__ void unit_add(double &h, double &l, dd sc, double xh,
     l = u.lo;
 }
 __device__ __forceinline__ double tau_abs(double x) { return fabs(x); }
+__device__ __forceinline__ double tau_abs(const fxe6 &x) { return fabs(fxe6_to_double(x)); }
 __device__ __forceinline__ double tau_abs(dd x) { return fabs(x.hi); }
 // (hi, lo) * prefix factor
 __device__ __forceinline__ void unit_scale(double &h, double &l, double tp) {
@@ -349,9 +384,9 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
     } else if constexpr (Prec<T>::fixed) {
         // symmetric form C - U U^T, U = B R^{-T} (offset rows)
         constexpr int d = 2 * (m - 1);
-        const fx_piv v = fx_pivot(p00, p01, p11);
+        const typename Prec<T>::Piv v = fx_pivot(p00, p01, p11);
         acc.bad |= fx_chol_bad(p00, v.det);
-        fx u0[d], u1[d], tt[d];
+        T u0[d], u1[d], tt[d];
 #pragma unroll
         for (int i = 0; i < d; ++i) fx_urow(v, A(o, o + 2 + i), A(o + 1, o + 2 + i), u0[i], u1[i], tt[i]);
         RegMat<T, m - 1> C;
@@ -597,7 +632,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     __shared__ int s_n, s_k, s_flag;
     __shared__ int s_base[kThreads];        // binned mode: modes included above each bottom node
     __shared__ typename BinOf<T>::type s_ubin[kMaxN + 1];  // binned mode: the unit's size bins
-    __shared__ fx s_vred[kThreads / 32];    // fixed point: per-warp aligned sums
+    __shared__ __align__(16) unsigned char s_vred_raw[sizeof(fx6) * (kThreads / 32)];  // fixed point: per-warp
+    T *s_vred = (T *)s_vred_raw;                                                          // aligned sums
     __shared__ float s_ared[kThreads / 32];
     __shared__ int s_ered[kThreads / 32];
     T *Ub = (T *)(smem + Lay::off_U);
@@ -707,6 +743,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         }
         __syncthreads();
         double u_hi = 0.0, u_lo = 0.0, u_abs = 0.0;
+        fxe6 uacc6(fx6_zero(), -(1 << 20));  // fx6: the unit's sum (thread 0)
         if constexpr (BIN) {
             for (int z = t; z <= n; z += kThreads) s_ubin[z] = typename BinOf<T>::type(0.0);
         }
@@ -754,12 +791,12 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     if (t < ((2 * np + 31) & ~31)) {
                         const int cp = min(t >> 1, np - 1), odd = t & 1;
                         const T *P = src + cp * sstr;
-                        const fx p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
-                        const fx det = fx_det2(p00, p01, p11);
-                        const fx y = fx_rsqrt(odd ? det : p00);
-                        const fx yo = fx_shfl_xor(y, 1);
+                        const T p00 = P[pidx(d, 0, 0)], p01 = P[pidx(d, 0, 1)], p11 = P[pidx(d, 1, 1)];
+                        const T det = fx_det2(p00, p01, p11);
+                        const T y = rsq<T>(odd ? det : p00);
+                        const T yo = fx_shfl_xor(y, 1);
                         if (!odd && t < 2 * np) {
-                            const fx_piv v = fx_pivot_from(p00, p01, det, y, yo);
+                            const typename Prec<T>::Piv v = fx_pivot_from(p00, p01, det, y, yo);
                             Qb[3 * cp] = v.a;
                             Qb[3 * cp + 1] = v.c;
                             Qb[3 * cp + 2] = v.b;
@@ -790,7 +827,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const T *P = src + cp * sstr;
                     const T b0 = P[pidx(d, 0, i + 2)], b1 = P[pidx(d, 1, i + 2)];
                     if constexpr (Prec<T>::fixed) {
-                        const fx_piv v{Qb[3 * cp], Qb[3 * cp + 1], Qb[3 * cp + 2], fx_zero(), fx_zero()};
+                        const typename Prec<T>::Piv v{Qb[3 * cp], Qb[3 * cp + 1], Qb[3 * cp + 2], konst<T>(0.0),
+                                                      konst<T>(0.0)};
                         fx_urow(v, b0, b1, Wb[3 * f], Wb[3 * f + 1], Wb[3 * f + 2]);
                     } else {
                         const T q00 = Qb[3 * cp], q01 = Qb[3 * cp + 1], q11 = Qb[3 * cp + 2];
@@ -869,7 +907,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 // each thread's subtree sum relative to its prefactor m 2^e, then one
                 // exponent-aligned fixed-point sum over the CTA: a single conversion to
                 // double-double per sub-unit
-                fx v = fx_zero();
+                T v = konst<T>(0.0);
                 int e = -(1 << 20);
                 float ab = 0.0f;
                 if (t < (1 << L_eff)) {
@@ -882,7 +920,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     const int excl = (qs - k) + (ss - kk) + (L_eff - __popc(t));
                     v = fx_neg_if(fx_mul_su(acc.hi, tn.m), excl & 1);   // |v| < 2^11
                     e = tn.e;
-                    ab = acc.abs * ((float)(int32_t)tn.m.w[3] * (1.0f / 65536.0f));
+                    ab = acc.abs * abs_part(tn.m);
                     if (acc.bad) atomicOr(&s_flag, acc.bad);
                 }
                 int em = __reduce_max_sync(0xffffffffu, e);
@@ -905,16 +943,22 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 }
                 __syncthreads();
                 if (t == 0) {
-                    fx S = s_vred[0];
+                    T S = s_vred[0];
                     float AB = s_ared[0];
 #pragma unroll
                     for (int w = 1; w < kThreads / 32; ++w) {
                         S = S + s_vred[w];
                         AB += s_ared[w];
                     }
-                    const dd sv = fx_to_dd(S);
-                    const double sc = ldexp(1.0, em + 4);
-                    unit_add(u_hi, u_lo, tsub, sv.hi * sc, sv.lo * sc);
+                    if constexpr (std::is_same<T, fx6>::value) {
+                        // the sub-unit's sum S 2^(em + 4) times its prefix factor, added to the
+                        // unit's sum, all as m 2^e with 192-bit mantissas
+                        uacc6 = fxe6_add(uacc6, fxe6_norm(S, em + 4) * tsub);
+                    } else {
+                        const dd sv = fx_to_dd(S);
+                        const double sc = ldexp(1.0, em + 4);
+                        unit_add(u_hi, u_lo, tsub, sv.hi * sc, sv.lo * sc);
+                    }
                     u_abs += tau_abs(tsub) * ldexp((double)AB, em);
                 }
             } else if (t < (1 << L_eff)) {
@@ -941,6 +985,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 store2(out + 2 * z, tpre * s_ubin[z]);
             }
             if (t == 0 && (s_flag || is_nan(tpre))) atomicOr(pl.pflags + sp, 1);
+            __syncthreads();
+        } else if constexpr (std::is_same<T, fx6>::value) {
+            // thread 0 holds the unit's whole sum: times the prefix factor, stored as the
+            // 192-bit mantissa (three words), the exponent and the sum of |terms|
+            if (t == 0) {
+                const fxe6 r = uacc6 * tpre;
+                double *out = pl.partials + (size_t)partial_words<T>() * u;
+                uint32_t *mw = (uint32_t *)out;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) mw[k] = r.m.w[k];
+                out[3] = (double)r.e;
+                out[4] = u_abs * tau_abs(tpre);
+                if (s_flag) atomicOr(pl.pflags + sp, s_flag);
+            }
             __syncthreads();
         } else {
         double c_hi = u_hi, c_lo = u_lo, c_abs = u_abs;
@@ -1070,6 +1128,57 @@ __global__ void finalize_kernel(int n_pat, const double *__restrict__ logdet, Pl
     if (status) status[p] = st;
 }
 
+// fx6: the pattern's unit sums (m 2^e, 192-bit mantissas) added in unit order by one warp,
+// aligned to the larger exponent at each step (every addend loses at most its bits below
+// 2^-176 of the larger), then the same result and bound as every other precision
+__device__ __forceinline__ fxe6 fxe6_shfl_down(const fxe6 &a, int off) {
+    fxe6 r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r.m.w[k] = __shfl_down_sync(0xffffffffu, a.m.w[k], off);
+    r.e = __shfl_down_sync(0xffffffffu, a.e, off);
+    return r;
+}
+__global__ void finalize6_kernel(int n_pat, const double *__restrict__ logdet, Plan pl, double *__restrict__ logP,
+                                 double *__restrict__ kappa, double *__restrict__ err_bound,
+                                 int32_t *__restrict__ status) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_pat) return;
+    const int sp = warp;
+    const int p = pl.perm[sp];
+    const int n = pl.pat_n[p];
+    const bool batch_over = *pl.overflow != 0;
+    const long long u0 = pl.unit_off[sp], u1 = batch_over ? u0 : pl.unit_off[sp + 1];
+    constexpr int W = partial_words<fx6>();
+    fxe6 acc(fx6_zero(), -(1 << 20));
+    double a = 0.0;
+    for (long long u = u0 + lane; u < u1; u += 32) {
+        const double *q = pl.partials + (size_t)W * u;
+        const uint32_t *mw = (const uint32_t *)q;
+        fxe6 v;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v.m.w[k] = mw[k];
+        v.e = (int)q[3];
+        acc = fxe6_add(acc, v);
+        a += q[4];
+    }
+    for (int off = 1; off < 32; off <<= 1) {  // fixed pairing order: deterministic
+        const fxe6 o = fxe6_shfl_down(acc, off);
+        const double oa = __shfl_down_sync(0xffffffffu, a, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            acc = fxe6_add(acc, o);
+            a += oa;
+        }
+    }
+    if (lane) return;
+    double lp, kap, eb;
+    int st;
+    finish_pattern<fx6>(n, batch_over, pl.pflags[sp], fxe6_to_double(acc), 0.0, a, *logdet, lp, kap, eb, st);
+    logP[p] = lp;
+    if (kappa) kappa[p] = kap;
+    if (err_bound) err_bound[p] = eb;
+    if (status) status[p] = st;
+}
+
 // ---- one slice of a batch's work units (the batch split across GPUs) ------------------
 // After the plan: the sweep evaluates only units [total part / nparts, total (part + 1) /
 // nparts) (units of one precision and split carry equal numbers of subsets once n >= B + L
@@ -1147,7 +1256,7 @@ struct WsOffsets {
     size_t counter, total, overflow, range, perm, pat_n, unit_off, pflags, partials, end;
 };
 
-WsOffsets ws_offsets(int n_pat, long long units) {
+WsOffsets ws_offsets(int n_pat, long long units, int pw = 3) {
     WsOffsets o;
     o.counter = 0;
     o.total = 8;
@@ -1158,7 +1267,7 @@ WsOffsets ws_offsets(int n_pat, long long units) {
     o.unit_off = align256(o.pat_n + 4 * (size_t)n_pat);
     o.pflags = align256(o.unit_off + 8 * ((size_t)n_pat + 1));
     o.partials = align256(o.pflags + 4 * (size_t)n_pat);
-    o.end = o.partials + 24 * (size_t)units;
+    o.end = o.partials + 8 * (size_t)pw * (size_t)units;
     return o;
 }
 
@@ -1199,11 +1308,11 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
     }
     long long cap;
     if (ctx->reserved) {
-        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / (8 * partial_words<T>()));
     } else {
         int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, 0).end);
         if (st) return st;
-        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+        cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / (8 * partial_words<T>()));
     }
     Plan pl = plan_from(ctx->ws, n_pat);
     pl.split = sweep_split_of(ctx, pi);
@@ -1216,9 +1325,9 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
         GBS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         long long need = *(long long *)ctx->pinned;
         if (need > cap) {
-            int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, need).end);
+            int st = gbs_ws_ensure(ctx, ws_offsets(n_pat, need, partial_words<T>()).end);
             if (st) return st;
-            cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / 24);
+            cap = (long long)((ctx->ws_bytes - ws_offsets(n_pat, 0).partials) / (8 * partial_words<T>()));
             pl = plan_from(ctx->ws, n_pat);
             pl.split = sweep_split_of(ctx, pi);
             plan_kernel<T><<<1, kPlanThreads, 0, ctx->stream>>>(M, pats, n_pat, cap, pl);
@@ -1233,8 +1342,11 @@ int run_sweep(gbs_ctx *ctx, int M, const double *O, const double *logdet, const 
     st = gbs_timing_end(ctx);
     if (st) return st;
     const int fthreads = 256, fblocks = (n_pat * 32 + fthreads - 1) / fthreads;
-    finalize_kernel<T><<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa,
-                                                             err_bound, status);
+    if constexpr (std::is_same<T, fx6>::value)
+        finalize6_kernel<<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa, err_bound, status);
+    else
+        finalize_kernel<T><<<fblocks, fthreads, 0, ctx->stream>>>(n_pat, logdet, pl, logP, kappa,
+                                                                 err_bound, status);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }
@@ -1567,7 +1679,7 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
 size_t sweep_workspace_bytes(int n_pat, long long units) { return ws_offsets(n_pat, units).end; }
 
 int sweep_split_of(const gbs_ctx *ctx, int precision) {
-    const int v = ctx->sweep_split[precision & 3];
+    const int v = ctx->sweep_split[precision & 7];
     return v < 0 || v > kS ? kS : v;
 }
 
@@ -1576,6 +1688,7 @@ long long sweep_units_upper_bound(int n_pat, int n_max, int precision, int split
     if (precision == GBS_FP64) unit_shape<double>(n_max, n_eff, L_eff, q, ss, split);
     else if (precision == GBS_DD) unit_shape<dd>(n_max, n_eff, L_eff, q, ss, split);
     else if (precision == GBS_FX) unit_shape<fx>(n_max, n_eff, L_eff, q, ss, split);
+    else if (precision == GBS_FX192) unit_shape<fx6>(n_max, n_eff, L_eff, q, ss, split);
     else unit_shape<float>(n_max, n_eff, L_eff, q, ss, split);
     return (long long)n_pat << (q - ss);
 }
@@ -1589,6 +1702,8 @@ int sweep_exact(gbs_ctx *ctx, int M, const double *O, const double *logdet,
         return run_sweep<dd>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     if (precision == GBS_FX)
         return run_sweep<fx>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
+    if (precision == GBS_FX192)
+        return run_sweep<fx6>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
     return run_sweep<float>(ctx, M, O, logdet, patterns, n_pat, logP, kappa, err_bound, status);
 }
 
