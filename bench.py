@@ -36,7 +36,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": None, "dd": 222976.0, "fp64": None, "fx": 160256.0}
+DRAM_TRAFFIC = {"fp32": None, "dd": 222976.0, "fp64": 469248.0, "fx": 240896.0}
 UNIT = "subset logdets/s"
 # 32-bit multiply-adds of one fixed-point update entry: two 128 x 128-bit products
 # truncated to their top 128 bits, 23 IMAD each (3 + 5 + 7 + 8 over the four rows)
@@ -850,8 +850,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fx", choices=["fp32", "fp64", "dd", "fx", "ff"],
-                    help="ff (float-float minors) serves --profile approx only")
+    ap.add_argument("--precision", default="fx", choices=["fp32", "fp64", "dd", "fx", "ff", "fx192"],
+                    help="ff (float-float minors) serves --profile approx only, fx192 --profile sweep only")
     ap.add_argument("--dd-sample", type=int, default=24)
     ap.add_argument("--dd-sample-nmax", type=int, default=15)
     ap.add_argument("--workload", default="m24_exact")
@@ -876,6 +876,8 @@ def main():
         return run_m100(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision in ("ff", "fx192"):
+        ap.error("--precision %s serves --profile only (the benchmark times fx, dd, fp64 or fp32)" % args.precision)
     return run_gpu(args)
 
 

@@ -87,9 +87,14 @@ static __device__ __noinline__ cx<ff> operator*(cx<ff> a, cx<ff> b) {
 }
 // e - a b: one fused form per part for float-float (see ff_fms2)
 template <typename R> __device__ __forceinline__ cx<R> cfms(cx<R> e, cx<R> a, cx<R> b) { return e - a * b; }
-static __device__ GBS_FF_FMS_INLINE cx<ff> cfms(cx<ff> e, cx<ff> a, cx<ff> b) {
+__device__ __forceinline__ cx<ff> cfms_ff(cx<ff> e, cx<ff> a, cx<ff> b) {
     return {ff_fms2(e.re, a.re, b.re, -a.im, b.im), ff_fms2(e.im, a.re, b.im, a.im, b.re)};
 }
+// out of line in the group terms (their unrolled loops hold dozens of these: inlined, the
+// code overflows the instruction cache); inline in the inverse's one-line update loop
+static __device__ GBS_FF_FMS_INLINE cx<ff> cfms(cx<ff> e, cx<ff> a, cx<ff> b) { return cfms_ff(e, a, b); }
+template <typename R> __device__ __forceinline__ cx<R> cfms_inl(cx<R> e, cx<R> a, cx<R> b) { return e - a * b; }
+__device__ __forceinline__ cx<ff> cfms_inl(cx<ff> e, cx<ff> a, cx<ff> b) { return cfms_ff(e, a, b); }
 static __device__ __noinline__ cx<ff> cinv(cx<ff> a) { return cinv<ff>(a); }
 static __device__ __noinline__ cx<ff> crsqrt(cx<ff> p) { return crsqrt<ff>(p); }
 __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
@@ -390,7 +395,7 @@ __device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ 
             if (fq < N - fp) { i = fp; j = fp + fq; } else { i = N - 1 - fp; j = i + (fq - (N - fp)); }
             if (i != k && j != k) {
                 cx<R> &e = G[i * N - (i * (i - 1)) / 2 + (j - i)];
-                e = cfms(e, cb[i], cu[j]);
+                e = cfms_inl(e, cb[i], cu[j]);
             }
             fq += sq;
             fp += sp;
@@ -730,7 +735,7 @@ __device__ void sweep_inverse_pair(cg::cluster_group &cl, int rank, int M, const
             if (fq < N - a) { i = a; j = a + fq; } else { i = r_hi - 1 - fp; j = i + (fq - (N - a)); }
             if (i != k && j != k) {
                 cx<R> &e = Gl[lidx(i, j)];
-                e = cfms(e, cb[i], cu[j]);
+                e = cfms_inl(e, cb[i], cu[j]);
             }
             fq += sq;
             fp += sp;
@@ -740,7 +745,7 @@ __device__ void sweep_inverse_pair(cg::cluster_group &cl, int rank, int M, const
             for (int j = rmid + t; j < N; j += kMinorThreads)
                 if (rmid != k && j != k) {
                     cx<R> &e = Gl[lidx(rmid, j)];
-                    e = cfms(e, cb[rmid], cu[j]);
+                    e = cfms_inl(e, cb[rmid], cu[j]);
                 }
         __syncthreads();
         // scale pivot k's row and column (own entries), stage pivot k + 1's column into
