@@ -239,6 +239,15 @@ int gbs_prob_combine(gbs_ctx *ctx, const double *logdet_sigmaQ, const uint64_t *
                      int nparts, const double *partials, const int32_t *pflags, double *logP, double *kappa,
                      double *err_bound, int32_t *status);
 
+/* Approximation (order > 0) with FP64 or float-float minors: patterns of at least n_min
+ * clicks run on the CTA-pair kernel (a thread-block cluster of two CTAs holding half of the
+ * packed 2n x 2n inverse each) instead of one CTA.  Patterns above 79 clicks always do (their
+ * inverse exceeds one SM's shared memory); the default n_min is 80.  A lower n_min routes
+ * smaller patterns through the pair kernel too (the results are the same up to rounding);
+ * the tests use it to check that kernel against the oracle on small patterns.  Not in the
+ * paper.  n_min in [3, 80], else GBS_E_INVALID. */
+int gbs_set_pair_from(gbs_ctx *ctx, int n_min);
+
 /* Allocation-free variant of gbs_prob for the exact sum (order 0).  The paper
  * has no counterpart: this serves callers that cannot call cudaMalloc (code
  * running under another owner's stream capture, processes whose device memory

@@ -45,6 +45,7 @@ SIGNATURES = {
     "gbs_clements_unitary": (_i, [_vp, _i, _vp, _vp, _vp]),
     "gbs_clements_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gbs_peak_flops": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "gbs_set_pair_from": (_i, [_vp, _i]),
     "gbs_timing_enable": (_i, [_vp, _i]),
     "gbs_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
 }

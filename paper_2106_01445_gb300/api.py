@@ -296,6 +296,10 @@ class Context:
                                                _ptr(dth), _ptr(dph)))
         return dth, dph
 
+    def set_pair_from(self, n_min: int = 80):
+        """Approximation: patterns of at least n_min clicks take the CTA-pair minors kernel."""
+        self._check(self.lib.gbs_set_pair_from(self.h, int(n_min)))
+
     def peak_flops(self, kind: str = "fp32") -> float:
         """FLOP/s of the FP32 / FP64 FMA loops ("fp32", "fp64") or of the fused
         Schur-update loops in double-double / fixed point ("dd", "fx"); "imad": 32-bit

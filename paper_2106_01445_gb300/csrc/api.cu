@@ -460,6 +460,14 @@ int gbs_gen_patterns(gbs_ctx *ctx, uint64_t seed, uint32_t stream, int M, int n_
     return launch_gen_patterns(ctx, seed, stream, M, n_lo, n_hi, n_pat, out);
 }
 
+int gbs_set_pair_from(gbs_ctx *ctx, int n_min) {
+    if (!ctx) return GBS_E_INVALID;
+    if (n_min < 3 || n_min > 80)
+        return gbs_fail(ctx, GBS_E_INVALID, "gbs_set_pair_from: %d outside [3, 80]", n_min);
+    ctx->pair_from = n_min;
+    return GBS_OK;
+}
+
 int gbs_peak_flops(gbs_ctx *ctx, int kind, double *flops) {
     if (!ctx || !flops || kind < 0 || kind > 4) return GBS_E_INVALID;
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));

@@ -422,6 +422,21 @@ __device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ 
     __syncthreads();
 }
 
+// shared-memory entries of the one-CTA minors kernel for patterns of up to n clicks: the
+// packed inverse, then max(the staged pivot columns, the pair phases' items); the items
+// number at least n - 2 and up to 8 n as long as the CTAs per SM of the bare inverse stay
+__host__ __device__ inline int minor_smem_entries(int n, int esz, int min_blocks) {
+    constexpr long long kSM = 228 * 1024, kCTA = 227 * 1024, kPerCTA = 4 * 1024;  // 1 KB reserved + static
+    const long long inv = (long long)n * (2 * n + 1), base = inv + 8LL * n;
+    long long per = kSM / (min_blocks > 1 ? 2 : 1) - kPerCTA;
+    if (base * esz > per) per = kCTA - kPerCTA;            // the inverse alone takes the SM
+    long long items = (per / esz - inv) / 15;
+    if (items > 8LL * n) items = 8LL * n;
+    if (items < n - 2) items = n - 2;
+    const long long ent = inv + (15 * items > 8LL * n ? 15 * items : 8LL * n);
+    return (int)ent;
+}
+
 // Read-only view of the swept matrix -G, G = (I - t O_S)^{-1}, packed upper triangle of
 // N x N: rows [0, rsplit) at b0, rows [rsplit, N) at b1 (whose first entry is packed
 // entry off1).  One CTA: rsplit = N.  A CTA pair (cluster): each half in one CTA's shared
@@ -440,10 +455,25 @@ template <typename R> struct GView {
     }
 };
 
-// The group terms det(G_WW)^{-1/2} of every W with |W| <= order, summed per |W| into
-// acc; worker `tid` of `nthr` takes every nthr-th group of each size.
+// The group terms det(G_WW)^{-1/2} of every W with |W| <= order, summed per |W| into acc.
+// Groups of one and two detectors: worker `tid` of `nthr` takes every nthr-th.  Groups of
+// three and four detectors go through each pair P = {a, b} (a < b) and the Schur
+// complement of G_PP in G, G^(P) = G - G_.P G_PP^-1 G_P.: with H_e = G^(P)_ee (2 x 2),
+//   det G_{P+e} = det G_PP det H_e,
+//   det G_{P+c+d} = det G_PP det H_c det(H_d - K^T H_c^-1 K),  K = G^(P)_cd,
+// and G^(P)_cd = G_cd - w_c^T w_d with w_e = D_P^-1/2 L_P^-1 G_Pe (G_PP = L_P D_P L_P^T).
+// The pairs of one `a` are taken in groups of consecutive b: phase 1 stores w_e, H_e, H_e^-1
+// and det(G_{P+e})^{-1/2} for every (b, e > b) of the group in `scratch` (cap items of 15
+// complex entries; every CTA computes all of them with its own threads), phase 2 forms the
+// four-detector terms of every (b, c, d), b < c < d (workers t2 of n2).  That is ~34 complex
+// products per four-detector group, against ~60 through a 6 x 6 factorisation per triple.
+// All pivots are accretive (Re > 0), so each determinant's principal root is the product of
+// its factors' principal roots.  Every thread of the CTA must call this (it synchronises the
+// CTA); s_off holds 2 (n + 1) ints of shared memory; add3: this CTA adds the three-detector
+// terms (of a CTA pair, one computes them for its phase 2 only).
 template <typename R>
-__device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order, int tid, int nthr,
+__device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order, int tid, int nthr, int t2,
+                                            int n2, cx<R> *scratch, int cap, int *s_off, bool add3,
                                             GroupAcc<R> &acc, bool &bad) {
     // w = 1: det of the 2x2 block, one root
     if (order >= 1)
@@ -465,92 +495,250 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                 for (int j = i; j < 4; ++j) m[pidx(4, i, j)] = V.g(rr[i], rr[j]);
             acc.add(2, ldl_rsqrt_prod<R, 4>(m, bad));
         }
-    // w = 3, and w = 4 from each triple's factorisation.  Triples in order of their
-    // largest detector c (then b, a), so the lanes of a warp share c and with it the
-    // number n - 1 - c of fourth detectors d > c.
-    if (order >= 3) {
-        const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
-        for (long long idx = tid; idx < ntri; idx += nthr) {
-            // c: the largest with C(c, 3) <= idx; then b: the largest with C(b, 2) <= rem
-            // (FP32 estimates on the MUFU pipe, corrected exactly in integers)
-            int c = (int)cbrtf(6.0f * (float)idx);
-            while ((long long)(c + 1) * c * (c - 1) / 6 <= idx) ++c;
-            while ((long long)c * (c - 1) * (c - 2) / 6 > idx) --c;
-            const long long rem = idx - (long long)c * (c - 1) * (c - 2) / 6;
-            int b = (int)sqrtf(2.0f * (float)rem);
-            while ((long long)(b + 1) * b / 2 <= rem) ++b;
-            while ((long long)b * (b - 1) / 2 > rem) --b;
-            const int a = (int)(rem - (long long)b * (b - 1) / 2);
-            const int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
-            // rows of the triple: entry (rr[i], col) with rr[i] <= col at rp[i][col]
-            const cx<R> *rp[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) rp[i] = V.row(rr[i]);
-            auto gr = [&](int i, int col) -> cx<R> { const cx<R> v = rp[i][col]; return mk<R>(-v.re, -v.im); };
-            cx<R> w6[21];
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = gr(i, rr[j]);
-            // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
-            cx<R> Lf[15], Dinv[6];
-            cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                cx<R> d = w6[pidx(6, k, k)];
-                if (!(d.re > R(0))) bad = true;
-                if (k & 1) f3 = f3 * crsqrt(prev * d);
-                prev = d;
-                cx<R> inv = cinv(d);
-                Dinv[k] = inv;
-#pragma unroll
-                for (int i = k + 1; i < 6; ++i) {
-                    cx<R> li = w6[pidx(6, k, i)] * inv;
-                    Lf[pidx(5, k, i - 1)] = li;
-#pragma unroll
-                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = cfms(w6[pidx(6, i, j)], li, w6[pidx(6, k, j)]);
+    // order 4 in FP64 and float-float: the pair phases below; order 3, and every order in
+    // FP32 (whose arithmetic is cheap next to the phases' barriers): a 6 x 6 factorisation
+    // per triple, each serving its fourth detectors through a 2 x 2 Schur block
+    constexpr bool kPairPhases = !std::is_same<R, float>::value;
+    if (order >= 3 && !(kPairPhases && order >= 4)) {
+        // w = 3, and w = 4 from each triple's factorisation.  Triples in order of their
+        // largest detector c (then b, a), so the lanes of a warp share c and with it the
+        // number n - 1 - c of fourth detectors d > c.
+        if (order >= 3) {
+            const long long ntri = (long long)n * (n - 1) * (n - 2) / 6;
+            for (long long idx = tid; idx < ntri; idx += nthr) {
+                // c: the largest with C(c, 3) <= idx; then b: the largest with C(b, 2) <= rem
+                // (FP32 estimates on the MUFU pipe, corrected exactly in integers)
+                int c = (int)cbrtf(6.0f * (float)idx);
+                while ((long long)(c + 1) * c * (c - 1) / 6 <= idx) ++c;
+                while ((long long)c * (c - 1) * (c - 2) / 6 > idx) --c;
+                const long long rem = idx - (long long)c * (c - 1) * (c - 2) / 6;
+                int b = (int)sqrtf(2.0f * (float)rem);
+                while ((long long)(b + 1) * b / 2 <= rem) ++b;
+                while ((long long)b * (b - 1) / 2 > rem) --b;
+                const int a = (int)(rem - (long long)b * (b - 1) / 2);
+                const int rr[6] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1, 2 * c, 2 * c + 1};
+                // rows of the triple: entry (rr[i], col) with rr[i] <= col at rp[i][col]
+                const cx<R> *rp[6];
+    #pragma unroll
+                for (int i = 0; i < 6; ++i) rp[i] = V.row(rr[i]);
+                auto gr = [&](int i, int col) -> cx<R> { const cx<R> v = rp[i][col]; return mk<R>(-v.re, -v.im); };
+                cx<R> w6[21];
+    #pragma unroll
+                for (int i = 0; i < 6; ++i)
+    #pragma unroll
+                    for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = gr(i, rr[j]);
+                // LDL^T kept: unit lower L (Lf[k][i], k < i), inverse pivots Dinv
+                cx<R> Lf[15], Dinv[6];
+                cx<R> f3 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
+    #pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    cx<R> d = w6[pidx(6, k, k)];
+                    if (!(d.re > R(0))) bad = true;
+                    if (k & 1) f3 = f3 * crsqrt(prev * d);
+                    prev = d;
+                    cx<R> inv = cinv(d);
+                    Dinv[k] = inv;
+    #pragma unroll
+                    for (int i = k + 1; i < 6; ++i) {
+                        cx<R> li = w6[pidx(6, k, i)] * inv;
+                        Lf[pidx(5, k, i - 1)] = li;
+    #pragma unroll
+                        for (int j = i; j < 6; ++j) w6[pidx(6, i, j)] = cfms(w6[pidx(6, i, j)], li, w6[pidx(6, k, j)]);
+                    }
                 }
-            }
-            acc.add(3, f3);
-            // float-float: this triple's quads summed in float-float first, then one FP64
-            // addition (keeps the FP64 pipe, 1/64 of FP32 here, out of the quad loop)
-            constexpr bool kTriplePartial = std::is_same<R, ff>::value;
-            cx<R> q4 = mk<R>(R(0), R(0));
-            if (order >= 4)
-                for (int d4 = c + 1; d4 < n; ++d4) {
-                    // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2); det S^{-1/2}
-                    cx<R> y0[6], y1[6];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        cx<R> v0 = gr(i, 2 * d4), v1 = gr(i, 2 * d4 + 1);
-#pragma unroll
-                        for (int k = 0; k < i; ++k) {
-                            v0 = cfms(v0, Lf[pidx(5, k, i - 1)], y0[k]);
-                            v1 = cfms(v1, Lf[pidx(5, k, i - 1)], y1[k]);
+                acc.add(3, f3);
+                // float-float: this triple's quads summed in float-float first, then one FP64
+                // addition (keeps the FP64 pipe, 1/64 of FP32 here, out of the quad loop)
+                constexpr bool kTriplePartial = std::is_same<R, ff>::value;
+                cx<R> q4 = mk<R>(R(0), R(0));
+                if (order >= 4)
+                    for (int d4 = c + 1; d4 < n; ++d4) {
+                        // y = L^{-1} G_{abc, d}; S = G_dd - y^T D^{-1} y (2 x 2); det S^{-1/2}
+                        cx<R> y0[6], y1[6];
+    #pragma unroll
+                        for (int i = 0; i < 6; ++i) {
+                            cx<R> v0 = gr(i, 2 * d4), v1 = gr(i, 2 * d4 + 1);
+    #pragma unroll
+                            for (int k = 0; k < i; ++k) {
+                                v0 = cfms(v0, Lf[pidx(5, k, i - 1)], y0[k]);
+                                v1 = cfms(v1, Lf[pidx(5, k, i - 1)], y1[k]);
+                            }
+                            y0[i] = v0;
+                            y1[i] = v1;
                         }
-                        y0[i] = v0;
-                        y1[i] = v1;
+                        const cx<R> *r0 = V.row(2 * d4), *r1 = V.row(2 * d4 + 1);
+                        const cx<R> e00 = r0[2 * d4], e01 = r0[2 * d4 + 1], e11 = r1[2 * d4 + 1];
+                        cx<R> s00 = mk<R>(-e00.re, -e00.im), s01 = mk<R>(-e01.re, -e01.im),
+                              s11 = mk<R>(-e11.re, -e11.im);
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
+                            s00 = cfms(s00, z0, y0[k]);
+                            s01 = cfms(s01, z0, y1[k]);
+                            s11 = cfms(s11, z1, y1[k]);
+                        }
+                        // pivots s00 and det / s00 of the accretive block: Re > 0 each
+                        const cx<R> det = cfms(s00 * s11, s01, s01);
+                        if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
+                        const cx<R> term = f3 * crsqrt(det);
+                        if constexpr (kTriplePartial) q4 = q4 + term;
+                        else acc.add(4, term);
                     }
-                    const cx<R> *r0 = V.row(2 * d4), *r1 = V.row(2 * d4 + 1);
-                    const cx<R> e00 = r0[2 * d4], e01 = r0[2 * d4 + 1], e11 = r1[2 * d4 + 1];
-                    cx<R> s00 = mk<R>(-e00.re, -e00.im), s01 = mk<R>(-e01.re, -e01.im),
-                          s11 = mk<R>(-e11.re, -e11.im);
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const cx<R> z0 = y0[k] * Dinv[k], z1 = y1[k] * Dinv[k];
-                        s00 = cfms(s00, z0, y0[k]);
-                        s01 = cfms(s01, z0, y1[k]);
-                        s11 = cfms(s11, z1, y1[k]);
-                    }
-                    // pivots s00 and det / s00 of the accretive block: Re > 0 each
-                    const cx<R> det = cfms(s00 * s11, s01, s01);
-                    if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
-                    const cx<R> term = f3 * crsqrt(det);
-                    if constexpr (kTriplePartial) q4 = q4 + term;
-                    else acc.add(4, term);
+                if constexpr (kTriplePartial)
+                    if (order >= 4) acc.add(4, q4);
+            }
+        }
+    } else if (order >= 3 && n >= 3) {
+        constexpr int IW = 15;  // per (b, e): w (4 x 2), H_e (3), H_e^-1 (3), det(G_{P+e})^{-1/2}
+        const int t1 = threadIdx.x, n1 = blockDim.x;
+        int *off1 = s_off, *off2 = s_off + (n + 1);
+        cx<R> q4 = mk<R>(R(0), R(0));
+        for (int a = 0; a + 2 < n; ++a) {
+            for (int b0 = a + 1; b0 + 1 < n;) {
+                // the group: b in [b0, b1) while its items fit (at least one b: cap >= n - 2)
+                int b1 = b0, items = 0;
+                while (b1 + 1 < n && (b1 == b0 || items + (n - b1 - 1) <= cap)) {
+                    items += n - b1 - 1;
+                    ++b1;
                 }
-            if constexpr (kTriplePartial)
-                if (order >= 4) acc.add(4, q4);
+                if (t1 == 0) {
+                    int s1 = 0, s2 = 0;
+                    for (int b = b0; b < b1; ++b) {
+                        off1[b - b0] = s1;
+                        off2[b - b0] = s2;
+                        s1 += n - b - 1;
+                        s2 += (n - b - 1) * (n - b - 2) / 2;
+                    }
+                    off1[b1 - b0] = s1;
+                    off2[b1 - b0] = s2;
+                }
+                __syncthreads();
+                const int nb = b1 - b0;
+                // phase 1: every (b, e), e > b
+                for (int it = t1; it < items; it += n1) {
+                    int lo = 0, hi = nb;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (off1[mid] <= it) lo = mid; else hi = mid;
+                    }
+                    const int b = b0 + lo, e = b + 1 + (it - off1[lo]);
+                    const int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
+                    // G_PP = L D L^T (unit lower L), pivots accretive
+                    cx<R> m4[10];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = V.g(rr[i], rr[j]);
+                    cx<R> L[6], dm[4], f2 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const cx<R> d = m4[pidx(4, k, k)];
+                        if (!(d.re > R(0))) bad = true;
+                        if (k & 1) f2 = f2 * crsqrt(prev * d);
+                        prev = d;
+                        dm[k] = crsqrt(d);
+                        const cx<R> inv = cinv(d);
+#pragma unroll
+                        for (int i = k + 1; i < 4; ++i) {
+                            const cx<R> li = m4[pidx(4, k, i)] * inv;
+                            L[pidx(3, k, i - 1)] = li;
+#pragma unroll
+                            for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = cfms(m4[pidx(4, i, j)], li, m4[pidx(4, k, j)]);
+                        }
+                    }
+                    // y = L^-1 G_{P,e} (two columns), w = D^-1/2 y
+                    cx<R> w[4][2];
+#pragma unroll
+                    for (int col = 0; col < 2; ++col) {
+                        cx<R> y[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            cx<R> v = V.g(rr[i], 2 * e + col);
+#pragma unroll
+                            for (int k = 0; k < i; ++k) v = cfms(v, L[pidx(3, k, i - 1)], y[k]);
+                            y[i] = v;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) w[i][col] = y[i] * dm[i];
+                    }
+                    // H_e = G_ee - w^T w; its pivots h00 and det / h00
+                    cx<R> h00 = V.g(2 * e, 2 * e), h01 = V.g(2 * e, 2 * e + 1), h11 = V.g(2 * e + 1, 2 * e + 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        h00 = cfms(h00, w[k][0], w[k][0]);
+                        h01 = cfms(h01, w[k][0], w[k][1]);
+                        h11 = cfms(h11, w[k][1], w[k][1]);
+                    }
+                    const cx<R> det = cfms(h00 * h11, h01, h01);
+                    if (!(h00.re > R(0)) || !(det.re * h00.re + det.im * h00.im > R(0))) bad = true;
+                    const cx<R> f3 = f2 * crsqrt(det);
+                    if (add3) acc.add(3, f3);
+                    const cx<R> id = cinv(det);
+                    cx<R> *o = scratch + (size_t)IW * it;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        o[2 * k] = w[k][0];
+                        o[2 * k + 1] = w[k][1];
+                    }
+                    o[8] = h00;
+                    o[9] = h01;
+                    o[10] = h11;
+                    o[11] = h11 * id;
+                    o[12] = mk<R>(R(0), R(0)) - h01 * id;
+                    o[13] = h00 * id;
+                    o[14] = f3;
+                }
+                __syncthreads();
+                // phase 2: every (b, c, d), b < c < d
+                if (order >= 4) {
+                    const int total = off2[nb];
+                    for (int it = t2; it < total; it += n2) {
+                        int lo = 0, hi = nb;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (off2[mid] <= it) lo = mid; else hi = mid;
+                        }
+                        const int b = b0 + lo, r = it - off2[lo];
+                        // (c', d') with c' < d' in colex order: r = d'(d' - 1)/2 + c'
+                        int dp = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)r)) * 0.5f);
+                        while (dp * (dp - 1) / 2 > r) --dp;
+                        while ((dp + 1) * dp / 2 <= r) ++dp;
+                        const int cp = r - dp * (dp - 1) / 2;
+                        const int c = b + 1 + cp, d = b + 1 + dp;
+                        const cx<R> *ic = scratch + (size_t)IW * (off1[lo] + cp);
+                        const cx<R> *jd = scratch + (size_t)IW * (off1[lo] + dp);
+                        // K = G^(P)_cd = G_cd - w_c^T w_d
+                        cx<R> K[2][2];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                cx<R> v = V.g(2 * c + i, 2 * d + j);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) v = cfms(v, ic[2 * k + i], jd[2 * k + j]);
+                                K[i][j] = v;
+                            }
+                        // X = H_c^-1 K; S = H_d - K^T X
+                        const cx<R> i00 = ic[11], i01 = ic[12], i11 = ic[13];
+                        cx<R> X[2][2];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            X[0][j] = i00 * K[0][j] + i01 * K[1][j];
+                            X[1][j] = i01 * K[0][j] + i11 * K[1][j];
+                        }
+                        const cx<R> s00 = cfms(cfms(jd[8], K[0][0], X[0][0]), K[1][0], X[1][0]);
+                        const cx<R> s01 = cfms(cfms(jd[9], K[0][0], X[0][1]), K[1][0], X[1][1]);
+                        const cx<R> s11 = cfms(cfms(jd[10], K[0][1], X[0][1]), K[1][1], X[1][1]);
+                        const cx<R> det = cfms(s00 * s11, s01, s01);
+                        if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
+                        q4 = q4 + ic[14] * crsqrt(det);
+                    }
+                }
+                acc.add(4, q4);     // this group's four-detector terms (zero if order 3)
+                q4 = mk<R>(R(0), R(0));
+                __syncthreads();    // the group's items are read: the next group may overwrite them
+                b0 = b1;
+            }
         }
     }
 }
@@ -607,11 +795,13 @@ template <typename R>
 __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) approx_minors_kernel(int M, const double *__restrict__ O,
                                                                     const uint64_t *__restrict__ pats,
                                                                     int n_pat, int order, int n_single,
+                                                                    int smem_entries,
                                                                     unsigned long long *counter,
                                                                     ApproxPlan pl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *G = (cx<R> *)smem_raw;
     __shared__ int modes[128];
+    __shared__ int s_off[2 * (kApproxMaxN + 1)];
     __shared__ long long s_u;
     __shared__ int s_bad;
     __shared__ double red[kMinorThreads / 32][2 * (kMaxOrder + 1)];
@@ -652,7 +842,11 @@ __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) appro
         acc.zero();
         bool bad = false;
         const GView<R> V{G, G, N, N, 0};
-        group_terms<R>(V, n, order, t, kMinorThreads, acc, bad);
+        // the staged columns and the rest of the allocation serve the pair phases
+        // items per group from this pattern's own n (not the batch's allocation): the work
+        // split, and with it every rounding, is the same in any batch
+        const int cap = (minor_smem_entries(n, (int)sizeof(cx<R>), MinorPrec<R>::min_blocks) - sym(N)) / 15;
+        group_terms<R>(V, n, order, t, kMinorThreads, t, kMinorThreads, G + sym(N), cap, s_off, true, acc, bad);
         if (bad) s_bad = 1;
         warp_group_sums<R>(acc, red[t >> 5]);
         __syncthreads();
@@ -773,9 +967,10 @@ __device__ void sweep_inverse_pair(cg::cluster_group &cl, int rank, int M, const
 template <typename R>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMinorThreads, 1)
 approx_minors_pair_kernel(int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int n_pat,
-                          int order, int n_single, unsigned long long *counter, ApproxPlan pl) {
+                          int order, int n_single, int smem_entries, unsigned long long *counter, ApproxPlan pl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int modes[128];
+    __shared__ int s_off[2 * (kApproxMaxN + 1)];
     __shared__ long long s_u;
     __shared__ int s_bad;
     __shared__ double red[2 * (kMinorThreads / 32)][2 * (kMaxOrder + 1)];
@@ -825,7 +1020,10 @@ approx_minors_pair_kernel(int M, const double *__restrict__ O, const uint64_t *_
         GroupAcc<R> acc;
         acc.zero();
         bool bad = false;
-        group_terms<R>(V, n, order, rank * kMinorThreads + t, 2 * kMinorThreads, acc, bad);
+        // each CTA computes every pair item in its own scratch (the staging area and beyond),
+        // rank 0 adds the three-detector terms, the four-detector ones are split over both
+        group_terms<R>(V, n, order, rank * kMinorThreads + t, 2 * kMinorThreads, rank * kMinorThreads + t,
+                       2 * kMinorThreads, stage, n - 2, s_off, rank == 0, acc, bad);
         if (bad) s_bad = 1;
         // warp sums: rank 1's into rank 0's table (rows 8..15), then rank 0 writes the unit
         double (*red0)[2 * (kMaxOrder + 1)] = rank == 0 ? red : cl.map_shared_rank(red, 0);
@@ -1658,7 +1856,8 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     // memory, or (FP64 and float-float) in a CTA pair's; a caller may lower it
     const int n_cap = MinorPrec<R>::pair ? kPairMaxN : MinorPrec<R>::nmax;
     const int nmax_smem = n_limit > 0 && n_limit < n_cap ? n_limit : n_cap;
-    const int n_single = MinorPrec<R>::nmax;
+    const int n_single = MinorPrec<R>::pair && ctx->pair_from - 1 < MinorPrec<R>::nmax ? ctx->pair_from - 1
+                                                                                       : MinorPrec<R>::nmax;
     static_assert(kMaxK + 1 <= 4096, "sector table");
     if (!ctx->ws || ctx->ws_bytes < approx_offsets(n_pat, 0).end) {
         int st = gbs_ws_ensure(ctx, approx_offsets(n_pat, 0).end);
@@ -1697,8 +1896,12 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     int st = gbs_timing_begin(ctx);
     if (st) return st;
     if (nsmall > 0) {
-        // the packed inverse and four staged pivot columns
-        const size_t minor_smem = sizeof(cx<R>) * ((size_t)sym(2 * nsmall) + 8 * (size_t)nsmall);
+        // the packed inverse and four staged pivot columns, or the pair phases' items
+        // (15 entries each, at least n - 2 of them, up to 8 n while the CTAs per SM stay)
+        const int ent = std::is_same<R, float>::value  // FP32: no pair phases
+                            ? sym(2 * nsmall) + 8 * nsmall
+                            : minor_smem_entries(nsmall, (int)sizeof(cx<R>), MinorPrec<R>::min_blocks);
+        const size_t minor_smem = sizeof(cx<R>) * (size_t)ent;
         GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)minor_smem));
         int nb = 0;
@@ -1706,16 +1909,17 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
                                                                     minor_smem));
         if (nb < 1) nb = 1;
         approx_minors_kernel<R><<<ctx->num_sms * nb, kMinorThreads, minor_smem, ctx->stream>>>(
-            M, O, pats, n_pat, order, n_single, (unsigned long long *)ctx->ws, pl);
+            M, O, pats, n_pat, order, n_single, ent, (unsigned long long *)ctx->ws, pl);
         GBS_CUDA(ctx, cudaGetLastError());
     }
     if constexpr (MinorPrec<R>::pair) if (nmax > n_single) {
-        // half of the packed inverse and three staged columns per CTA of a pair
-        const size_t pair_smem = sizeof(cx<R>) * ((size_t)pair_part_entries(2 * nmax) + 6 * (size_t)nmax);
+        // half of the packed inverse, and three staged columns or the pair phases' items
+        const int pent = pair_part_entries(2 * nmax) + (6 * nmax > 15 * (nmax - 2) ? 6 * nmax : 15 * (nmax - 2));
+        const size_t pair_smem = sizeof(cx<R>) * (size_t)pent;
         GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_pair_kernel<R>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
         approx_minors_pair_kernel<R><<<(ctx->num_sms / 2) * 2, kMinorThreads, pair_smem, ctx->stream>>>(
-            M, O, pats, n_pat, order, n_single,
+            M, O, pats, n_pat, order, n_single, pent,
             (unsigned long long *)((char *)ctx->ws + approx_offsets(n_pat, 0).counter2), pl);
         GBS_CUDA(ctx, cudaGetLastError());
     }

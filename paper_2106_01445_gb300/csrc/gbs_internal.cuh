@@ -32,6 +32,9 @@ struct gbs_ctx {
     // prefix levels looped inside one sweep unit, by precision (-1: the default);
     // set by gbs_autotune
     int sweep_split[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    // approximation: patterns of at least this many clicks take the CTA-pair minors kernel
+    // (FP64 and float-float; above 79 clicks they must)
+    int pair_from = 80;
     // optional event timing of the sweep kernel launches
     static const int kTimingRing = 4096;
     bool timing = false;

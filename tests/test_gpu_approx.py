@@ -237,6 +237,24 @@ def test_pair_kernel_in_mixed_batches(ctx):
     assert np.abs(ff["logP"][ok] - ref["logP"][ok]).max() < 1e-6
 
 
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
+def test_pair_kernel_on_small_patterns_matches_oracle(ctx, small_case, precision):
+    """The CTA-pair minors kernel (two CTAs, the inverse split over their shared memories,
+    distributed shared-memory reads) on the small device's patterns of 3..10 clicks, routed
+    there by gbs_set_pair_from, against the oracle at orders 2, 3 and 4 (1e-8)."""
+    M, U, r, eta, mode_sets, pats, st = small_case
+    ctx.set_pair_from(3)
+    try:
+        for order in (2, 3, 4):
+            res = run(ctx, U, r, eta, pats, order, precision)
+            for i, modes in enumerate(mode_sets):
+                ref, info = ap.approx_logprob(st.O, st.logdet, M, modes, order)
+                assert res["status"][i] in (0, 7), res["status"][i]
+                assert abs(res["logP"][i] - ref) < 1e-8, (order, len(modes), res["logP"][i] - ref)
+    finally:
+        ctx.set_pair_from(80)
+
+
 def test_ff_m50_sample_and_exact_only_rejects_ff(ctx):
     from paper_2106_01445_gb300 import GbsError
     c = g.CONFIGS["m50_approx"]
