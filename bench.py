@@ -867,7 +867,7 @@ def main():
     ap.add_argument("--npat", type=int, default=128)
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other three precisions of the exact sweep (short runs)")
-    ap.add_argument("--detail-out", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
+    ap.add_argument("--detail-out", default=os.path.join(ROOT, "bench_out", "bench_detail.json"),
                     help="side file for the per-workload study (the headline line stays short)")
     args = ap.parse_args()
     if args.profile:

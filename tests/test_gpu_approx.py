@@ -77,7 +77,7 @@ def _table_noise_sens(info, n, order, logdet, delta, seeds=4):
 
 @pytest.mark.parametrize("order", [2, 4])
 def test_fp32_split_matches_oracle(ctx, small_case, order):
-    # FP32 minors: moment tables with ~1e-5 relative rounding; the bound is the survey's 1e-4
+    # FP32 minors: moment tables with ~1e-5 relative rounding; the bound is the FP32 split's 1e-4 target
     # or three times the oracle's own change under that table noise, whichever is larger
     M, U, r, eta, mode_sets, pats, st = small_case
     res = run(ctx, U, r, eta, pats, order, "fp32")
