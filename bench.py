@@ -506,6 +506,31 @@ def run_workloads(dev, stream, meas, fp32_peak):
         return np.array([len(g.pattern_modes(p)) for p in pats])
 
     res = {}
+    # ---- the 24-mode batch split into N equal-cost slices (the multi-GPU strong-scaling
+    # partition), run one after another on this GPU: each slice's sweep time, the balance
+    # (slowest / mean: what N GPUs would wait for) and the combine, against the whole batch
+    c = g.CONFIGS["m24_exact"]
+    st = ctx.build_state(c.unitary(), c.squeezing(), c.eta)
+    pd = patterns_tensor(c.patterns(), dev)
+    ms_whole, kms_whole, whole = timed(lambda: ctx.prob(st["O"], st["logdet"], pd, precision="fx"))
+    split = {"whole_batch_sweep_ms": kms_whole}
+    for N in (2, 4, 8):
+        parts, flags, kms = [], [], []
+        for k in range(N):
+            _, kk, (pp, ff) = timed(lambda: ctx.prob_partial(st["O"], pd, k, N, precision="fx"))
+            parts.append(pp)
+            flags.append(ff)
+            kms.append(kk)
+        ms_c, _, comb = timed(lambda: ctx.prob_combine(st["logdet"], pd, torch.stack(parts), torch.stack(flags),
+                                                       precision="fx"))
+        a, b = host(comb), host(whole)
+        ok = b["status"] == 0
+        split["slices_%d" % N] = {"slice_sweep_ms": kms, "balance_max_over_mean": max(kms) / (sum(kms) / N),
+                                  "sum_of_slices_over_whole": sum(kms) / kms_whole, "combine_ms": ms_c,
+                                  "max_abs_dlogP_vs_whole": float(np.abs(a["logP"][ok] - b["logP"][ok]).max()),
+                                  "status_equal": bool((a["status"] == b["status"]).all())}
+    res["m24_split_slices"] = split
+
     # ---- 8 modes, all 256 patterns: latency of one call; sum of P; every pattern vs the oracle
     c = g.CONFIGS["m8_all"]
     U, r, pats = c.unitary(), c.squeezing(), c.patterns()
