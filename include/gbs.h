@@ -65,16 +65,17 @@ typedef enum {
                             eigenvalue of sigma_Q is below 16); else GBS_E_RANGE */
     GBS_FF = 4,          /* approximation only: float-float (~48-bit) complex minors on the FP32
                             pipes; FP64-class moments at a fraction of FP64's cost (n <= 79) */
-    GBS_AUTO = 5,        /* exact sum: GBS_FX, then GBS_DD for the patterns it reports GBS_E_RANGE
-                            (on the device, no host synchronisation; gbs_reserve covers it);
+    GBS_AUTO = 5,        /* exact sum: GBS_FX, then GBS_DD for the patterns it reports GBS_E_RANGE,
+                            then GBS_FX192 for the valid results whose err_bound exceeds 1e-10 (on
+                            the device, no host synchronisation; gbs_reserve covers it; a batch
+                            that needs neither rerun costs two sweeps over no units);
                             approximation: GBS_FF */
     GBS_FX192 = 6        /* exact sum only: 192-bit fixed point (Q16.176), prefactors and sums as
                             192-bit mantissas with exponents, unit sums added exactly per pattern:
                             per-term error ~2^-164 for signed sums that cancel beyond what
                             GBS_FX and GBS_DD resolve (kappa ~1e20 and more; err_bound says when
                             they do not suffice).  Same range condition as GBS_FX (GBS_E_RANGE).
-                            Not taken by gbs_prob_noalloc, gbs_prob_partial or gbs_reserve's
-                            no-allocation guarantee */
+                            Not taken by gbs_prob_noalloc or gbs_prob_partial */
 } gbs_precision;
 
 /* ---- context ------------------------------------------------------------ */

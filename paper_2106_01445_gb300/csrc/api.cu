@@ -168,11 +168,14 @@ int gbs_reserve(gbs_ctx *ctx, int n_pat, int n_max) {
         return gbs_fail(ctx, GBS_E_INVALID, "gbs_reserve: bad n_pat %d / n_max %d", n_pat, n_max);
     GBS_CUDA(ctx, cudaSetDevice(ctx->device));
     long long units = 0;
-    for (int prec = 0; prec < 4; ++prec) {
-        long long u = sweep_units_upper_bound(n_pat, n_max, prec, sweep_split_of(ctx, prec));
+    size_t bytes = 0;
+    for (int prec : {GBS_FP64, GBS_FP32_SPLIT, GBS_DD, GBS_FX, GBS_FX192}) {
+        const long long u = sweep_units_upper_bound(n_pat, n_max, prec, sweep_split_of(ctx, prec));
+        const size_t by = sweep_workspace_bytes_prec(n_pat, u, prec);
         if (u > units) units = u;
+        if (by > bytes) bytes = by;
     }
-    int st = gbs_ws_ensure(ctx, sweep_workspace_bytes(n_pat, units));
+    int st = gbs_ws_ensure(ctx, bytes);
     if (st) return st;
     // GBS_AUTO's rerun buffers
     const size_t aux = sweep_auto_bytes(n_pat);

@@ -77,6 +77,7 @@ int sweep_exact_on(gbs_ctx *ctx, void *ws, size_t ws_bytes, int M, const double 
                    const double *logdet, const uint64_t *patterns, int n_pat, int precision,
                    double *logP, double *kappa, double *err_bound, int32_t *status);
 size_t sweep_workspace_bytes(int n_pat, long long units);
+size_t sweep_workspace_bytes_prec(int n_pat, long long units, int precision);
 int sweep_slice(gbs_ctx *ctx, int M, const double *O, const uint64_t *patterns, int n_pat, int precision,
                 int part, int nparts, double *partial, int32_t *pflag);
 int sweep_combine(gbs_ctx *ctx, const double *logdet, const uint64_t *patterns, int n_pat, int precision,

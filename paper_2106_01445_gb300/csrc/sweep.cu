@@ -282,6 +282,9 @@ template <typename T> struct Layout {
     static constexpr size_t off_dec = off_decoff + sizeof(int) * (R + 2);
     static constexpr size_t bytes = (off_dec + sizeof(uint16_t) * dec_entries() + 15) / 16 * 16;
     static_assert(sizeof(T) * sym(2 * kMaxN) <= off_Q, "prefix matrix must fit in X, Y, Ub and W");
+    static_assert(off_Y % alignof(T) == 0 && off_tauX % alignof(Node) == 0 && off_tauY % alignof(Node) == 0 &&
+                      off_red % alignof(double) == 0,
+                  "shared-memory regions must be aligned for their types");
 };
 
 // ---- error-free accumulation ----------------------------------------------------
@@ -1617,11 +1620,40 @@ __global__ void auto_merge_kernel(int n_pat, const int32_t *__restrict__ st, con
     if (status) status[p] = st2[p];
 }
 
+// GBS_AUTO, last step: the patterns whose result is valid but whose bound exceeds tol (the
+// sum cancels beyond 128-bit fixed point and double-double) go to the 192-bit sweep ...
+__global__ void auto_mark_wide_kernel(int n_pat, const int32_t *__restrict__ st, const double *__restrict__ eb,
+                                      double tol, const uint64_t *__restrict__ pats, uint64_t *__restrict__ redo) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pat) return;
+    const bool again = st[p] == GBS_OK && !(eb[p] <= tol);
+    redo[2 * p] = again ? pats[2 * p] : ~0ull;
+    redo[2 * p + 1] = again ? pats[2 * p + 1] : ~0ull;
+}
+// ... and its results replace those where it succeeded
+__global__ void auto_merge_wide_kernel(int n_pat, double tol, const double *__restrict__ lp3,
+                                       const double *__restrict__ ka3, const double *__restrict__ er3,
+                                       const int32_t *__restrict__ st3, int32_t *__restrict__ st,
+                                       double *__restrict__ logP, double *__restrict__ kappa,
+                                       double *__restrict__ eb) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pat) return;
+    const bool again = st[p] == GBS_OK && !(eb[p] <= tol);
+    if (!again || st3[p] != GBS_OK) return;
+    logP[p] = lp3[p];
+    kappa[p] = ka3[p];
+    eb[p] = er3[p];
+}
+
 }  // namespace
 
 size_t sweep_auto_bytes(int n_pat) {
     const size_t n = (size_t)n_pat;
-    return align256(16 * n) + 3 * align256(8 * n) + 2 * align256(4 * n);
+    return align256(16 * n) + 5 * align256(8 * n) + 2 * align256(4 * n);
+}
+
+size_t sweep_workspace_bytes_prec(int n_pat, long long units, int precision) {
+    return ws_offsets(n_pat, units, precision == GBS_FX192 ? partial_words<fx6>() : 3).end;
 }
 
 int sweep_auto(gbs_ctx *ctx, int M, const double *O, const double *logdet, const uint64_t *patterns, int n_pat,
@@ -1646,16 +1678,28 @@ int sweep_auto(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     uint64_t *redo = (uint64_t *)b;
     double *lp2 = (double *)(b + align256(16 * n));
     double *ka2 = lp2 + align256(8 * n) / 8, *er2 = ka2 + align256(8 * n) / 8;
-    int32_t *st2 = (int32_t *)(er2 + align256(8 * n) / 8);
+    double *ka1 = kappa ? kappa : er2 + align256(8 * n) / 8;
+    double *eb1 = err_bound ? err_bound : er2 + 2 * (align256(8 * n) / 8);
+    int32_t *st2 = (int32_t *)(er2 + 3 * (align256(8 * n) / 8));
     int32_t *st1 = status ? status : st2 + align256(4 * n) / 4;
-    int r = sweep_exact(ctx, M, O, logdet, patterns, n_pat, GBS_FX, logP, kappa, err_bound, st1);
+    // 128-bit fixed point
+    int r = sweep_exact(ctx, M, O, logdet, patterns, n_pat, GBS_FX, logP, ka1, eb1, st1);
     if (r) return r;
+    // double-double for the patterns outside the fixed-point range
     const unsigned g = (unsigned)((n_pat + 255) / 256);
     auto_mark_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, patterns, redo);
     GBS_CUDA(ctx, cudaGetLastError());
     r = sweep_exact(ctx, M, O, logdet, redo, n_pat, GBS_DD, lp2, ka2, er2, st2);
     if (r) return r;
-    auto_merge_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, lp2, ka2, er2, st2, logP, kappa, err_bound, status);
+    auto_merge_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, lp2, ka2, er2, st2, logP, ka1, eb1, st1);
+    GBS_CUDA(ctx, cudaGetLastError());
+    // 192-bit fixed point for the valid results whose bound exceeds 1e-10
+    constexpr double kAutoTol = 1e-10;
+    auto_mark_wide_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, st1, eb1, kAutoTol, patterns, redo);
+    GBS_CUDA(ctx, cudaGetLastError());
+    r = sweep_exact(ctx, M, O, logdet, redo, n_pat, GBS_FX192, lp2, ka2, er2, st2);
+    if (r) return r;
+    auto_merge_wide_kernel<<<g, 256, 0, ctx->stream>>>(n_pat, kAutoTol, lp2, ka2, er2, st2, st1, logP, ka1, eb1);
     GBS_CUDA(ctx, cudaGetLastError());
     return GBS_OK;
 }

@@ -113,3 +113,25 @@ def test_range_status_and_anchor_bounds(ctx):
     assert (res["err_bound"] < 1e-10).all(), res["err_bound"]
     ok = fx["status"] == 0
     assert (np.abs(res["logP"][ok] - fx["logP"][ok]) <= fx["err_bound"][ok] + 1e-10).all()
+
+
+def test_auto_escalates_beyond_the_128_bit_bound(ctx):
+    """GBS_AUTO reruns in 192-bit fixed point exactly the valid results whose 128-bit bound
+    exceeds 1e-10: the strongly cancelling patterns then match the 60-digit values to 1e-10
+    with a bound below it; a pattern the 128-bit sweep resolves keeps its result bit for bit."""
+    cases = [e for e in CASES["single"] if e["name"] == "m12_k6"]
+    e = cases[0]
+    U, r = g.haar_unitary(e["M"], e["seed"]), g.squeezing(e["M"], e["K"], e["r"][0], e["r"][1], e["seed"])
+    pats = np.stack([g.modes_to_pattern(c["modes"]) for c in cases] + [g.modes_to_pattern([1, 4, 7])])
+    auto = gpu(ctx, U, r, e["eta"], pats, "auto")
+    fx = gpu(ctx, U, r, e["eta"], pats, "fx")
+    wide = gpu(ctx, U, r, e["eta"], pats, "fx192")
+    assert (auto["status"] == 0).all(), auto["status"]
+    assert (auto["err_bound"] < 1e-10).all(), auto["err_bound"]
+    for i, c in enumerate(cases):
+        assert abs(auto["logP"][i] - c["logP"]) < 1e-10, (i, auto["logP"][i] - c["logP"])
+    redo = (fx["status"] == 0) & (fx["err_bound"] > 1e-10)
+    assert redo[:len(cases)].any() and not redo[-1]
+    assert np.array_equal(auto["logP"][redo], wide["logP"][redo])
+    assert np.array_equal(auto["logP"][~redo], fx["logP"][~redo])
+    assert np.array_equal(auto["err_bound"][~redo], fx["err_bound"][~redo])
