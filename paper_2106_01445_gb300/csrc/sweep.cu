@@ -231,12 +231,56 @@ __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(dd h, dd l, double &oh, double &ol) { oh = h.hi; ol = h.lo + l.hi; }
 
+// ---- prefactor arrays --------------------------------------------------------------
+// The node prefactors are stored packed: a fixed-point m 2^e as its mantissa words and
+// exponent (20 or 28 bytes), every other type as itself.
+template <typename N> struct NodeIO {
+    static constexpr int bytes = sizeof(N), align = alignof(N);
+    static __device__ __forceinline__ N ld(const unsigned char *b, int i) { return ((const N *)b)[i]; }
+    static __device__ __forceinline__ void st(unsigned char *b, int i, const N &v) { ((N *)b)[i] = v; }
+};
+template <> struct NodeIO<fxe> {
+    static constexpr int bytes = 20, align = 4;
+    static __device__ __forceinline__ fxe ld(const unsigned char *b, int i) {
+        const uint32_t *q = (const uint32_t *)(b + bytes * i);
+        fxe r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r.m.w[k] = q[k];
+        r.e = (int)q[4];
+        return r;
+    }
+    static __device__ __forceinline__ void st(unsigned char *b, int i, const fxe &v) {
+        uint32_t *q = (uint32_t *)(b + bytes * i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = v.m.w[k];
+        q[4] = (uint32_t)v.e;
+    }
+};
+template <> struct NodeIO<fxe6> {
+    static constexpr int bytes = 28, align = 4;
+    static __device__ __forceinline__ fxe6 ld(const unsigned char *b, int i) {
+        const uint32_t *q = (const uint32_t *)(b + bytes * i);
+        fxe6 r;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r.m.w[k] = q[k];
+        r.e = (int)q[6];
+        return r;
+    }
+    static __device__ __forceinline__ void st(unsigned char *b, int i, const fxe6 &v) {
+        uint32_t *q = (uint32_t *)(b + bytes * i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) q[k] = v.m.w[k];
+        q[6] = (uint32_t)v.e;
+    }
+};
+
 // ---- shared-memory layout ----------------------------------------------------
 // X and Y alternate as source and destination of the breadth-first levels; the
 // unit's prefix-elimination matrix (up to 2 kMaxN rows) spans X, Y, Ub and W before
-// the levels start.  Ub holds the unit's trailing block, W the rows W = B P^{-1} of
-// the level being eliminated, Q the pivot quantities of a level's parents (and the W
-// rows of a prefix pivot).
+// the levels start.  Ub holds the unit's trailing block, Sl the sub-unit tree's stored
+// matrices, W the rows W = B P^{-1} of the level being eliminated; a level's pivot
+// quantities sit at the start of its destination buffer (read before the children are
+// written).  The prefactor arrays hold the W rows of a prefix pivot.
 template <typename T> struct Layout {
     static constexpr int B = Prec<T>::B;
     static constexpr int R = kL + B;  // modes of a unit's level-0 matrix
@@ -247,7 +291,7 @@ template <typename T> struct Layout {
         return m;
     }
     static constexpr int max_odd() {
-        int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots
+        int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots (binned mode)
         for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
         return m;
     }
@@ -259,7 +303,6 @@ template <typename T> struct Layout {
         }
         return m;
     }
-    static constexpr int q_entries() { return 3 * (kThreads / 2) > 4 * kMaxN ? 3 * (kThreads / 2) : 4 * kMaxN; }
     static constexpr int dec_entries() {
         int s = 0;
         for (int m = 1; m <= R; ++m) s += sym(2 * m);
@@ -271,19 +314,28 @@ template <typename T> struct Layout {
     static constexpr size_t off_Y = off_X + sizeof(T) * max_even();
     static constexpr int ublk() { return sym(2 * (kS + R)); }
     static constexpr size_t off_U = off_Y + sizeof(T) * max_odd();
-    static constexpr size_t off_W = off_U + sizeof(T) * ublk();
-    static constexpr size_t off_Q = off_W + sizeof(T) * w_entries();
-    static constexpr size_t off_tauX = off_Q + sizeof(T) * q_entries();
-    static constexpr size_t off_tauY = off_tauX + sizeof(Node) * kThreads;
-    static constexpr size_t off_red = off_tauY + sizeof(Node) * kThreads;      // 3 doubles per warp
+    // the sub-unit tree's stored matrices: after an include at depth d < kS - 1, the
+    // 2 (kS + R - d - 1) rows of the modes below it
+    static constexpr int slot_off(int d) {
+        int o = 0;
+        for (int e = 1; e < d; ++e) o += sym(2 * (kS + R - e));
+        return o;
+    }
+    static constexpr size_t off_Sl = off_U + sizeof(T) * ublk();
+    static constexpr size_t off_W = off_Sl + sizeof(T) * slot_off(kS);
+    // prefactors: even levels hold at most kThreads / 2 nodes, odd levels kThreads
+    static constexpr size_t off_tauX = off_W + sizeof(T) * w_entries();
+    static constexpr size_t off_tauY = off_tauX + NodeIO<Node>::bytes * (kThreads / 2);
+    static constexpr size_t off_red = (off_tauY + NodeIO<Node>::bytes * kThreads + 15) / 16 * 16;  // 3 doubles per warp
     static constexpr size_t off_modes = off_red + sizeof(double) * 3 * (kThreads / 32);
-    static constexpr size_t off_pos = off_modes + sizeof(int) * 128;
+    static constexpr size_t off_pos = off_modes + sizeof(int) * 64;
     static constexpr size_t off_decoff = off_pos + sizeof(int) * 2 * kMaxN;
     static constexpr size_t off_dec = off_decoff + sizeof(int) * (R + 2);
     static constexpr size_t bytes = (off_dec + sizeof(uint16_t) * dec_entries() + 15) / 16 * 16;
-    static_assert(sizeof(T) * sym(2 * kMaxN) <= off_Q, "prefix matrix must fit in X, Y, Ub and W");
-    static_assert(off_Y % alignof(T) == 0 && off_tauX % alignof(Node) == 0 && off_tauY % alignof(Node) == 0 &&
-                      off_red % alignof(double) == 0,
+    static_assert(sizeof(T) * sym(2 * kMaxN) <= off_tauX, "prefix matrix must fit in X, Y, Ub and W");
+    static_assert(sizeof(T) * 2 * (2 * kMaxN - 2) <= off_red - off_tauX, "prefix W rows must fit in the prefactors");
+    static_assert(off_Y % alignof(T) == 0 && off_tauX % alignof(T) == 0 && off_tauX % NodeIO<Node>::align == 0 &&
+                      off_tauY % NodeIO<Node>::align == 0 && off_red % alignof(double) == 0,
                   "shared-memory regions must be aligned for their types");
 };
 
@@ -547,6 +599,19 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(int M, const uint64_
     }
 }
 
+// entry f of the upper triangle of a D x D matrix (D even) in (D / 2) (D + 1) folded runs:
+// row p and row D - 1 - p share one run of D + 1 entries
+__device__ __forceinline__ void fold_ij(int f, int D, int &i, int &j) {
+    const int w = D + 1, p = f / w, k = f - p * w;
+    if (k < D - p) {
+        i = p;
+        j = p + k;
+    } else {
+        i = D - 1 - p;
+        j = i + (k - (D - p));
+    }
+}
+
 // ---- one 2x2 block pivot eliminated by the whole CTA ---------------------------------
 // Mx: packed D x D matrix (D even); the pivot block sits on rows c0, c0 + 1.  Rows and
 // columns >= c0 + 2 receive C - W B^T, W = B P^{-1} (its rows staged in Wb first).
@@ -565,28 +630,52 @@ __device__ __forceinline__ typename Prec<T>::Tau elim_pivot(T *Mx, int D, int c0
     if (t < Dt) {
         const T inv = rs * rs;
         const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
-        for (int i = t; i < Dt; i += kThreads) {
-            const T b0 = Mx[pidx(D, c0, c0 + 2 + i)], b1 = Mx[pidx(D, c0 + 1, c0 + 2 + i)];
-            Wb[2 * i] = dot2(q00, b0, q01, b1);
-            Wb[2 * i + 1] = dot2(q01, b0, q11, b1);
-        }
+        const T b0 = Mx[pidx(D, c0, c0 + 2 + t)], b1 = Mx[pidx(D, c0 + 1, c0 + 2 + t)];
+        Wb[2 * t] = dot2(q00, b0, q01, b1);
+        Wb[2 * t + 1] = dot2(q01, b0, q11, b1);
     }
     const typename Prec<T>::Tau rt = tau_of(det, rs);
     __syncthreads();
     // the trailing triangle, rows p and Dt - 1 - p folded into one run of Dt + 1 entries
-    const int w = Dt + 1, E = (Dt >> 1) * w;
+    const int E = (Dt >> 1) * (Dt + 1);
     for (int f = t; f < E; f += kThreads) {
-        const int p = f / w, k = f - p * w;
         int i, j;
-        if (k < Dt - p) {
-            i = p;
-            j = p + k;
-        } else {
-            i = Dt - 1 - p;
-            j = i + (k - (Dt - p));
-        }
+        fold_ij(f, Dt, i, j);
         T &c = Mx[pidx(D, c0 + 2 + i, c0 + 2 + j)];
         c = fms2(c, Wb[2 * i], Mx[pidx(D, c0, c0 + 2 + j)], Wb[2 * i + 1], Mx[pidx(D, c0 + 1, c0 + 2 + j)]);
+    }
+    __syncthreads();
+    return rt;
+}
+// The same pivot with the source kept: Dst (packed, D - c0 - 2 rows) receives the
+// trailing block's Schur complement, Mx is only read (the same operations in the same
+// order as elim_pivot, so the values are those it would leave in place).
+template <typename T>
+__device__ __forceinline__ typename Prec<T>::Tau elim_into(const T *Mx, int D, int c0, T *Dst, T *Wb, int *flag) {
+    const int t = threadIdx.x;
+    const T p00 = Mx[pidx(D, c0, c0)], p01 = Mx[pidx(D, c0, c0 + 1)], p11 = Mx[pidx(D, c0 + 1, c0 + 1)];
+    const T det = det2(p00, p01, p11);
+    if (t == 0) {
+        const int bad = pivot_bad(det);
+        if (bad) atomicOr(flag, bad);
+    }
+    const int Dt = D - c0 - 2;
+    const T rs = rsq<T>(det);
+    if (t < Dt) {
+        const T inv = rs * rs;
+        const T q00 = p11 * inv, q01 = -p01 * inv, q11 = p00 * inv;
+        const T b0 = Mx[pidx(D, c0, c0 + 2 + t)], b1 = Mx[pidx(D, c0 + 1, c0 + 2 + t)];
+        Wb[2 * t] = dot2(q00, b0, q01, b1);
+        Wb[2 * t + 1] = dot2(q01, b0, q11, b1);
+    }
+    const typename Prec<T>::Tau rt = tau_of(det, rs);
+    __syncthreads();
+    const int E = (Dt >> 1) * (Dt + 1);
+    for (int f = t; f < E; f += kThreads) {
+        int i, j;
+        fold_ij(f, Dt, i, j);
+        Dst[pidx(Dt, i, j)] = fms2(Mx[pidx(D, c0 + 2 + i, c0 + 2 + j)], Wb[2 * i], Mx[pidx(D, c0, c0 + 2 + j)],
+                                   Wb[2 * i + 1], Mx[pidx(D, c0 + 1, c0 + 2 + j)]);
     }
     __syncthreads();
     return rt;
@@ -616,16 +705,16 @@ __device__ __forceinline__ void store2(double *o, zf v) { o[0] = ff_to_double(v.
 // terms are summed unsigned into bins by subset size instead of into the signed sum
 template <typename T, bool BIN = false>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__restrict__ O,
-                                                        const uint64_t *__restrict__ pats,
-                                                        int n_pat, Plan pl) {
+                                                        const uint64_t *__restrict__ pats, int n_pat, Plan pl) {
     using Lay = Layout<T>;
     constexpr int B = Prec<T>::B;
     extern __shared__ __align__(16) unsigned char smem[];
     T *X = (T *)(smem + Lay::off_X);
     T *Y = (T *)(smem + Lay::off_Y);
     using Node = typename Prec<T>::Node;
-    Node *tauX = (Node *)(smem + Lay::off_tauX);
-    Node *tauY = (Node *)(smem + Lay::off_tauY);
+    using NIO = NodeIO<Node>;
+    unsigned char *tauX = smem + Lay::off_tauX;
+    unsigned char *tauY = smem + Lay::off_tauY;
     double *red = (double *)(smem + Lay::off_red);
     int *modes = (int *)(smem + Lay::off_modes);
     int *pos = (int *)(smem + Lay::off_pos);
@@ -641,7 +730,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
     __shared__ int s_ered[kThreads / 32];
     T *Ub = (T *)(smem + Lay::off_U);
     T *Wb = (T *)(smem + Lay::off_W);
-    T *Qb = (T *)(smem + Lay::off_Q);
+    T *Wpre = (T *)(smem + Lay::off_tauX);  // W rows of a prefix pivot (the prefactors are free then)
+    T *Sl = (T *)(smem + Lay::off_Sl);       // the sub-unit tree's stored matrices
     using Tau = typename Prec<T>::Tau;
     __shared__ Tau s_tpre;
 
@@ -706,10 +796,10 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         const int k = s_k;
         const int D0 = 2 * (k + rp);
         // gather G = (I - O) on those rows into X (packed; the prefix matrix spans X and Y),
-        // padding modes as identity; every thread takes entries of the whole matrix
-        for (int f = t; f < D0 * D0; f += kThreads) {
-            const int i = f / D0, j = f - i * D0;
-            if (j < i) continue;
+        // padding modes as identity
+        for (int f = t; f < (D0 >> 1) * (D0 + 1); f += kThreads) {
+            int i, j;
+            fold_ij(f, D0, i, j);
             const int a = pos[i >> 1], b = pos[j >> 1];
             T v;
             if (a >= n || b >= n) {
@@ -725,7 +815,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         __syncthreads();
         // eliminate the included prefix modes (2x2 block pivots)
         Tau tpre = Tau(1.0);
-        for (int e = 0; e < k; ++e) tpre = tpre * elim_pivot<T>(X, D0, 2 * e, Qb, &s_flag);
+        for (int e = 0; e < k; ++e) tpre = tpre * elim_pivot<T>(X, D0, 2 * e, Wpre, &s_flag);
         // the unit's trailing 2rp x 2rp block -> Ublk, through registers: the prefix
         // matrix may extend over Ublk
         {
@@ -745,45 +835,95 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
             }
         }
         __syncthreads();
+        const int nsub = 1 << ss;
         double u_hi = 0.0, u_lo = 0.0, u_abs = 0.0;
         fxe6 uacc6(fx6_zero(), -(1 << 20));  // fx6: the unit's sum (thread 0)
         if constexpr (BIN) {
             for (int z = t; z <= n; z += kThreads) s_ubin[z] = typename BinOf<T>::type(0.0);
         }
-        for (int sub = 0; sub < (1 << ss); ++sub) {
-            // sub-unit: include the set bits of `sub` among the next ss modes
-            const int kk = __popc(sub);
-            const int Ds = 2 * (kk + r), dU = 2 * rp;
-            // rows: included sub modes (in order), then the last r modes of Ublk
-            for (int f = t; f < Ds * Ds; f += kThreads) {
-                const int i = f / Ds, j = f - i * Ds;
-                if (j < i) continue;
-                int ai = i >> 1, bj = j >> 1;
-                // position of the ai-th row mode inside Ublk
-                const int ui = ai < kk ? (int)__fns((unsigned)sub, 0u, ai + 1) : ss + (ai - kk);
-                const int uj = bj < kk ? (int)__fns((unsigned)sub, 0u, bj + 1) : ss + (bj - kk);
-                Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
-            }
-            __syncthreads();
-            Tau tsub = Tau(1.0);
-            for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Qb, &s_flag);
-            // level 0 of the expansion: the trailing 2r x 2r block, packed into X
-            {
-                const int d = 2 * r, o = 2 * kk;
-                for (int f = t; f < d * d; f += kThreads) {
-                    const int i = f / d, j = f - i * d;
-                    if (j >= i) X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
+        // The sub-units: the include (1) / exclude (0) choices of the next ss modes of Ublk.
+        // Signed sweeps walk them as a tree, depth e choosing mode e: the matrix after an
+        // include at depth e is stored (in slot e + 1, or in X at the last depth), an
+        // exclude is a view of the same matrix one mode further on; leaf `leaf` takes the
+        // choices of its bits from the top (sub, the choice of mode e in bit e, is its bit
+        // reversal), so consecutive leaves share every choice above the one that turns
+        // include.  jv[e]: the slot of the matrix the node at depth e views (0: Ublk);
+        // tv[e]: the product of the includes' det^{-1/2} above depth e.
+        int jv[kS + 1];
+        Tau tv[kS + 1];
+        jv[0] = 0;
+        tv[0] = Tau(1.0);
+        for (int leaf = 0; leaf < nsub; ++leaf) {
+            int sub, kk;
+            Tau tsub;
+            if constexpr (BIN) {
+                sub = leaf;
+                kk = __popc(sub);
+                const int Ds = 2 * (kk + r), dU = 2 * rp;
+                // rows: included sub modes (in order), then the last r modes of Ublk
+                for (int f = t; f < (Ds >> 1) * (Ds + 1); f += kThreads) {
+                    int i, j;
+                    fold_ij(f, Ds, i, j);
+                    const int ai = i >> 1, bj = j >> 1;
+                    // position of the ai-th row mode inside Ublk
+                    const int ui = ai < kk ? (int)__fns((unsigned)sub, 0u, ai + 1) : ss + (ai - kk);
+                    const int uj = bj < kk ? (int)__fns((unsigned)sub, 0u, bj + 1) : ss + (bj - kk);
+                    Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
                 }
-                if (t == 0) tauX[0] = node_one<Node>();
+                __syncthreads();
+                tsub = Tau(1.0);
+                for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Wpre, &s_flag);
+                // level 0 of the expansion: the trailing 2r x 2r block, packed into X
+                const int d = 2 * r, o = 2 * kk;
+                for (int f = t; f < (d >> 1) * (d + 1); f += kThreads) {
+                    int i, j;
+                    fold_ij(f, d, i, j);
+                    X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
+                }
+            } else {
+                sub = ss ? (int)(__brev((unsigned)leaf) >> (32 - ss)) : 0;
+                kk = __popc(sub);
+                // the depth whose choice turns include (none at the first leaf); deeper
+                // choices are excludes
+                const int ds = leaf ? ss - 1 - (31 - __clz(leaf ^ (leaf - 1))) : ss;
+                if (ds < ss) {
+                    const int j0 = jv[ds], D = 2 * (rp - j0);
+                    const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
+                    T *dst = ds + 1 < ss ? Sl + Lay::slot_off(ds + 1) : X;
+                    const Tau rs = elim_into<T>(src, D, 2 * (ds - j0), dst, Wpre, &s_flag);
+                    for (int e = ds + 1; e <= ss; ++e) {
+                        jv[e] = ds + 1;
+                        tv[e] = tv[ds] * rs;
+                    }
+                } else {
+                    for (int e = 1; e <= ss; ++e) {
+                        jv[e] = 0;
+                        tv[e] = Tau(1.0);
+                    }
+                }
+                tsub = tv[ss];
+                // level 0 of the expansion: the leaf's matrix, packed into X (already there
+                // after an include at the last depth)
+                if (ds + 1 != ss) {
+                    const int j0 = jv[ss], D = 2 * (rp - j0), o = 2 * (ss - j0), d = 2 * r;
+                    const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
+                    for (int f = t; f < (d >> 1) * (d + 1); f += kThreads) {
+                        int i, j;
+                        fold_ij(f, d, i, j);
+                        X[pidx(d, i, j)] = src[pidx(D, o + i, o + j)];
+                    }
+                }
             }
+            if (t == 0) NIO::st(tauX, 0, node_one<Node>());
             __syncthreads();
             // breadth-first expansion of L_eff levels: node c at level l + 1 is child
             // c & 1 (0 exclude, 1 include) of parent c >> 1
             for (int l = 0; l < L_eff; ++l) {
                 const T *src = (l & 1) ? Y : X;
                 T *dst = (l & 1) ? X : Y;
-                const Node *tsrc = (l & 1) ? tauY : tauX;
-                Node *tdst = (l & 1) ? tauX : tauY;
+                const unsigned char *tsrc = (l & 1) ? tauY : tauX;
+                unsigned char *tdst = (l & 1) ? tauX : tauY;
+                T *Qb = dst;  // the parents' pivot quantities, read before the children are written
                 const int d = 2 * (r - l), dc = d - 2;
                 const int sstr = nstride(d), dstr = nstride(dc), Ec = sym(dc);
                 const int np = 1 << l;
@@ -803,8 +943,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                             Qb[3 * cp] = v.a;
                             Qb[3 * cp + 1] = v.c;
                             Qb[3 * cp + 2] = v.b;
-                            tdst[2 * cp] = tsrc[cp];
-                            tdst[2 * cp + 1] = node_times(tsrc[cp], v.rs);
+                            const Node tp = NIO::ld(tsrc, cp);
+                            NIO::st(tdst, 2 * cp, tp);
+                            NIO::st(tdst, 2 * cp + 1, node_times(tp, v.rs));
                             const int bad = fx_chol_bad(p00, det);
                             if (bad) atomicOr(&s_flag, bad);
                         }
@@ -819,8 +960,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                     Qb[3 * t + 1] = -p01 * inv;
                     Qb[3 * t + 2] = p00 * inv;
                     const int bad = pivot_bad(det);
-                    tdst[2 * t] = tsrc[t];
-                    tdst[2 * t + 1] = node_times(tsrc[t], rs);
+                    const Node tp = NIO::ld(tsrc, t);
+                    NIO::st(tdst, 2 * t, tp);
+                    NIO::st(tdst, 2 * t + 1, node_times(tp, rs));
                     if (bad) atomicOr(&s_flag, bad);
                 }
                 __syncthreads();
@@ -882,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 const bool has = t < (1 << L_eff);
                 if (has) {
                     const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
-                    const Node tn = ((L_eff & 1) ? tauY : tauX)[t];
+                    const Node tn = NIO::ld((L_eff & 1) ? tauY : tauX, t);
                     const int nreal = n - (n_eff - B);
                     SmemMat<T, B> A{node};
                     dfs<T, B, 0, false>(A, konst<T>(1.0), 0, nreal, acc, 0);
@@ -915,7 +1057,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 float ab = 0.0f;
                 if (t < (1 << L_eff)) {
                     const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
-                    const Node tn = ((L_eff & 1) ? tauY : tauX)[t];
+                    const Node tn = NIO::ld((L_eff & 1) ? tauY : tauX, t);
                     const int nreal = n - (n_eff - B);
                     Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
                     SmemMat<T, B> A{node};
@@ -966,7 +1108,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
                 }
             } else if (t < (1 << L_eff)) {
                 const T *node = ((L_eff & 1) ? Y : X) + t * nstride(2 * B);
-                const Node tau_node = ((L_eff & 1) ? tauY : tauX)[t];
+                const Node tau_node = NIO::ld((L_eff & 1) ? tauY : tauX, t);
                 const int nreal = n - (n_eff - B);
                 Acc<T> acc{konst<T>(0.0), konst<T>(0.0), 0, 0};
                 SmemMat<T, B> A{node};
