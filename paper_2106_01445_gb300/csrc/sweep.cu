@@ -425,7 +425,9 @@ __device__ __forceinline__ void leaf_pair(BinAcc<T, NB> &acc, T inc, T tau, bool
     if (real) acc.v[cnt] += tau;
 }
 
-template <typename T, int MD, int O, bool NEG, typename Src, typename AccT>
+// ONE: tau is exactly 1 (the subtree root and its exclude-only descendants), so products
+// with it are skipped
+template <typename T, int MD, int O, bool NEG, bool ONE = true, typename Src, typename AccT>
 __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, AccT &acc, int cnt) {
     constexpr int m = MD - O;
     constexpr int o = 2 * O;
@@ -435,7 +437,7 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
         const T det = det2(p00, p01, p11);
         if constexpr (Prec<T>::fixed) acc.bad |= pivot_bad(det);
         const T rs = rsq<T>(det);
-        leaf_pair<NEG>(acc, mul_pos(tau, rs), tau, real, cnt);
+        leaf_pair<NEG>(acc, ONE ? rs : mul_pos(tau, rs), tau, real, cnt);
     } else if constexpr (Prec<T>::fixed) {
         // symmetric form C - U U^T, U = B R^{-T} (offset rows)
         constexpr int d = 2 * (m - 1);
@@ -450,8 +452,8 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 #pragma unroll
             for (int j = i; j < d; ++j)
                 C.v[pidx(d, i, j)] = fx_sym_update(A(o + 2 + i, o + 2 + j), u0[i], u1[i], tt[i], u0[j], u1[j], tt[j]);
-        dfs<T, m - 1, 0, NEG>(C, fx_mul_uu(tau, v.rs), depth + 1, nreal, acc, cnt + 1);
-        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc, cnt);
+        dfs<T, m - 1, 0, NEG, false>(C, ONE ? v.rs : fx_mul_uu(tau, v.rs), depth + 1, nreal, acc, cnt + 1);
+        if (real) dfs<T, MD, O + 1, !NEG, ONE>(A, tau, depth + 1, nreal, acc, cnt);
     } else {
         constexpr int d = 2 * (m - 1);
         const T det = det2(p00, p01, p11);
@@ -472,8 +474,8 @@ __device__ __forceinline__ void dfs(const Src &A, T tau, int depth, int nreal, A
 #pragma unroll
             for (int j = i; j < d; ++j)
                 C.v[pidx(d, i, j)] = fms2(A(o + 2 + i, o + 2 + j), w0[i], b0[j], w1[i], b1[j]);
-        dfs<T, m - 1, 0, NEG>(C, tau * rs, depth + 1, nreal, acc, cnt + 1);
-        if (real) dfs<T, MD, O + 1, !NEG>(A, tau, depth + 1, nreal, acc, cnt);
+        dfs<T, m - 1, 0, NEG, false>(C, ONE ? rs : tau * rs, depth + 1, nreal, acc, cnt + 1);
+        if (real) dfs<T, MD, O + 1, !NEG, ONE>(A, tau, depth + 1, nreal, acc, cnt);
     }
 }
 
