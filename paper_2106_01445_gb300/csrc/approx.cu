@@ -98,6 +98,71 @@ __device__ __forceinline__ cx<ff> cfms_inl(cx<ff> e, cx<ff> a, cx<ff> b) { retur
 static __device__ __noinline__ cx<ff> cinv(cx<ff> a) { return cinv<ff>(a); }
 static __device__ __noinline__ cx<ff> crsqrt(cx<ff> p) { return crsqrt<ff>(p); }
 __device__ __forceinline__ cx<double> widen(cx<float> a) { return {(double)a.re, (double)a.im}; }
+
+// ---- the four-detector step of the pair phases ----------------------------------------
+// K entry: v - sum_k x_k y_k over the four rows of the pair's Schur factor (x = w_c, y = w_d)
+template <typename R>
+__device__ __forceinline__ cx<R> rank4_entry(cx<R> v, const cx<R> *x, const cx<R> *y, int i, int j) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v = cfms(v, x[2 * k + i], y[2 * k + j]);
+    return v;
+}
+// the term det(G_{P+c+d})^{-1/2} = f3_c det(S)^{-1/2}, S = H_d - K^T H_c^{-1} K, from K and the
+// stored items of c (ic) and d (jd); *bad: a pivot of S not accretive
+template <typename R> struct QuadTerm {
+    cx<R> term;
+    int bad;
+};
+template <typename R>
+__device__ __forceinline__ QuadTerm<R> quad_term(cx<R> k00, cx<R> k01, cx<R> k10, cx<R> k11, const cx<R> *ic,
+                                                 const cx<R> *jd) {
+    const cx<R> K[2][2] = {{k00, k01}, {k10, k11}};
+    const cx<R> i00 = ic[11], i01 = ic[12], i11 = ic[13];
+    cx<R> X[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        X[0][j] = i00 * K[0][j] + i01 * K[1][j];
+        X[1][j] = i01 * K[0][j] + i11 * K[1][j];
+    }
+    const cx<R> s00 = cfms(cfms(jd[8], K[0][0], X[0][0]), K[1][0], X[1][0]);
+    const cx<R> s01 = cfms(cfms(jd[9], K[0][0], X[0][1]), K[1][0], X[1][1]);
+    const cx<R> s11 = cfms(cfms(jd[10], K[0][1], X[0][1]), K[1][1], X[1][1]);
+    const cx<R> det = cfms(s00 * s11, s01, s01);
+    QuadTerm<R> q;
+    q.bad = !(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0));
+    q.term = ic[14] * crsqrt(det);
+    return q;
+}
+// float-float: each of these as one out-of-line call whose arithmetic is inline (the same
+// operations as the shared complex calls, a few calls per four-detector group instead of
+// ~30: their argument traffic cost more than the code they share)
+__device__ __forceinline__ cx<ff> cmul_ff(cx<ff> a, cx<ff> b) {
+    return {ff_dot2(a.re, b.re, -a.im, b.im), ff_dot2(a.re, b.im, a.im, b.re)};
+}
+static __device__ __noinline__ cx<ff> rank4_entry(cx<ff> v, const cx<ff> *x, const cx<ff> *y, int i, int j) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v = cfms_ff(v, x[2 * k + i], y[2 * k + j]);
+    return v;
+}
+static __device__ __noinline__ QuadTerm<ff> quad_term(cx<ff> k00, cx<ff> k01, cx<ff> k10, cx<ff> k11,
+                                                      const cx<ff> *ic, const cx<ff> *jd) {
+    const cx<ff> K[2][2] = {{k00, k01}, {k10, k11}};
+    const cx<ff> i00 = ic[11], i01 = ic[12], i11 = ic[13];
+    cx<ff> X[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        X[0][j] = cmul_ff(i00, K[0][j]) + cmul_ff(i01, K[1][j]);
+        X[1][j] = cmul_ff(i01, K[0][j]) + cmul_ff(i11, K[1][j]);
+    }
+    const cx<ff> s00 = cfms_ff(cfms_ff(jd[8], K[0][0], X[0][0]), K[1][0], X[1][0]);
+    const cx<ff> s01 = cfms_ff(cfms_ff(jd[9], K[0][0], X[0][1]), K[1][0], X[1][1]);
+    const cx<ff> s11 = cfms_ff(cfms_ff(jd[10], K[0][1], X[0][1]), K[1][1], X[1][1]);
+    const cx<ff> det = cfms_ff(cmul_ff(s00, s11), s01, s01);
+    QuadTerm<ff> q;
+    q.bad = !(s00.re > ff(0.0f, 0.0f)) || !(det.re * s00.re + det.im * s00.im > ff(0.0f, 0.0f));
+    q.term = cmul_ff(ic[14], crsqrt<ff>(det));
+    return q;
+}
 __device__ __forceinline__ cx<double> widen(cx<double> a) { return a; }
 __device__ __forceinline__ cx<double> widen(cx<ff> a) { return {ff_to_double(a.re), ff_to_double(a.im)}; }
 
@@ -455,6 +520,105 @@ template <typename R> struct GView {
     }
 };
 
+// ---- the pair phases' items ------------------------------------------------------------
+// Complex products, fused multiply-subtracts and roots: IN selects, for float-float, the
+// inline forms of the shared out-of-line calls (the same operations).
+template <typename R, bool IN> __device__ __forceinline__ cx<R> pmul(cx<R> a, cx<R> b) {
+    if constexpr (IN) return cmul_ff(a, b); else return a * b;
+}
+template <typename R, bool IN> __device__ __forceinline__ cx<R> pfms(cx<R> e, cx<R> a, cx<R> b) {
+    if constexpr (IN) return cfms_ff(e, a, b); else return cfms(e, a, b);
+}
+template <typename R, bool IN> __device__ __forceinline__ cx<R> prsqrt(cx<R> p) {
+    if constexpr (IN) return crsqrt<ff>(p); else return crsqrt(p);
+}
+template <typename R, bool IN> __device__ __forceinline__ cx<R> pinv(cx<R> p) {
+    if constexpr (IN) return cinv<ff>(p); else return cinv(p);
+}
+// item (b, e) of pair P = {a, b}: G_PP = L D L^T (unit lower L, accretive pivots), w = D^-1/2
+// L^-1 G_{P,e}, H_e = G_ee - w^T w; stores w (8), H_e (3), H_e^-1 (3) and
+// f3 = det(G_{P+e})^{-1/2} at o and returns f3 (bad: a pivot not accretive)
+template <typename R> struct PairItem {
+    cx<R> f3;
+    int bad;
+};
+template <typename R, bool IN>
+__device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, int b, int e, cx<R> *o) {
+    PairItem<R> out;
+    out.bad = 0;
+    const int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
+    cx<R> m4[10];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = V.g(rr[i], rr[j]);
+    cx<R> L[6], dm[4], f2 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const cx<R> d = m4[pidx(4, k, k)];
+        if (!(d.re > R(0))) out.bad = 1;
+        if (k & 1) f2 = pmul<R, IN>(f2, prsqrt<R, IN>(pmul<R, IN>(prev, d)));
+        prev = d;
+        dm[k] = prsqrt<R, IN>(d);
+        const cx<R> inv = pinv<R, IN>(d);
+#pragma unroll
+        for (int i = k + 1; i < 4; ++i) {
+            const cx<R> li = pmul<R, IN>(m4[pidx(4, k, i)], inv);
+            L[pidx(3, k, i - 1)] = li;
+#pragma unroll
+            for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = pfms<R, IN>(m4[pidx(4, i, j)], li, m4[pidx(4, k, j)]);
+        }
+    }
+    // y = L^-1 G_{P,e} (two columns), w = D^-1/2 y
+    cx<R> w[4][2];
+#pragma unroll
+    for (int col = 0; col < 2; ++col) {
+        cx<R> y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            cx<R> v = V.g(rr[i], 2 * e + col);
+#pragma unroll
+            for (int k = 0; k < i; ++k) v = pfms<R, IN>(v, L[pidx(3, k, i - 1)], y[k]);
+            y[i] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i][col] = pmul<R, IN>(y[i], dm[i]);
+    }
+    // H_e = G_ee - w^T w; its pivots h00 and det / h00
+    cx<R> h00 = V.g(2 * e, 2 * e), h01 = V.g(2 * e, 2 * e + 1), h11 = V.g(2 * e + 1, 2 * e + 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h00 = pfms<R, IN>(h00, w[k][0], w[k][0]);
+        h01 = pfms<R, IN>(h01, w[k][0], w[k][1]);
+        h11 = pfms<R, IN>(h11, w[k][1], w[k][1]);
+    }
+    const cx<R> det = pfms<R, IN>(pmul<R, IN>(h00, h11), h01, h01);
+    if (!(h00.re > R(0)) || !(det.re * h00.re + det.im * h00.im > R(0))) out.bad = 1;
+    out.f3 = pmul<R, IN>(f2, prsqrt<R, IN>(det));
+    const cx<R> id = pinv<R, IN>(det);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[2 * k] = w[k][0];
+        o[2 * k + 1] = w[k][1];
+    }
+    o[8] = h00;
+    o[9] = h01;
+    o[10] = h11;
+    o[11] = pmul<R, IN>(h11, id);
+    o[12] = mk<R>(R(0), R(0)) - pmul<R, IN>(h01, id);
+    o[13] = pmul<R, IN>(h00, id);
+    o[14] = out.f3;
+    return out;
+}
+template <typename R>
+__device__ __forceinline__ PairItem<R> pair_item(const GView<R> &V, int a, int b, int e, cx<R> *o) {
+    return pair_item_body<R, false>(V, a, b, e, o);
+}
+// float-float: one out-of-line call per item with its arithmetic inline
+static __device__ __noinline__ PairItem<ff> pair_item(const GView<ff> V, int a, int b, int e, cx<ff> *o) {
+    return pair_item_body<ff, true>(V, a, b, e, o);
+}
+
 // The group terms det(G_WW)^{-1/2} of every W with |W| <= order, summed per |W| into acc.
 // Groups of one and two detectors: worker `tid` of `nthr` takes every nthr-th.  Groups of
 // three and four detectors go through each pair P = {a, b} (a < b) and the Schur
@@ -622,71 +786,9 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                         if (off1[mid] <= it) lo = mid; else hi = mid;
                     }
                     const int b = b0 + lo, e = b + 1 + (it - off1[lo]);
-                    const int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
-                    // G_PP = L D L^T (unit lower L), pivots accretive
-                    cx<R> m4[10];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = V.g(rr[i], rr[j]);
-                    cx<R> L[6], dm[4], f2 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const cx<R> d = m4[pidx(4, k, k)];
-                        if (!(d.re > R(0))) bad = true;
-                        if (k & 1) f2 = f2 * crsqrt(prev * d);
-                        prev = d;
-                        dm[k] = crsqrt(d);
-                        const cx<R> inv = cinv(d);
-#pragma unroll
-                        for (int i = k + 1; i < 4; ++i) {
-                            const cx<R> li = m4[pidx(4, k, i)] * inv;
-                            L[pidx(3, k, i - 1)] = li;
-#pragma unroll
-                            for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = cfms(m4[pidx(4, i, j)], li, m4[pidx(4, k, j)]);
-                        }
-                    }
-                    // y = L^-1 G_{P,e} (two columns), w = D^-1/2 y
-                    cx<R> w[4][2];
-#pragma unroll
-                    for (int col = 0; col < 2; ++col) {
-                        cx<R> y[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            cx<R> v = V.g(rr[i], 2 * e + col);
-#pragma unroll
-                            for (int k = 0; k < i; ++k) v = cfms(v, L[pidx(3, k, i - 1)], y[k]);
-                            y[i] = v;
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) w[i][col] = y[i] * dm[i];
-                    }
-                    // H_e = G_ee - w^T w; its pivots h00 and det / h00
-                    cx<R> h00 = V.g(2 * e, 2 * e), h01 = V.g(2 * e, 2 * e + 1), h11 = V.g(2 * e + 1, 2 * e + 1);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        h00 = cfms(h00, w[k][0], w[k][0]);
-                        h01 = cfms(h01, w[k][0], w[k][1]);
-                        h11 = cfms(h11, w[k][1], w[k][1]);
-                    }
-                    const cx<R> det = cfms(h00 * h11, h01, h01);
-                    if (!(h00.re > R(0)) || !(det.re * h00.re + det.im * h00.im > R(0))) bad = true;
-                    const cx<R> f3 = f2 * crsqrt(det);
-                    if (add3) acc.add(3, f3);
-                    const cx<R> id = cinv(det);
-                    cx<R> *o = scratch + (size_t)IW * it;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        o[2 * k] = w[k][0];
-                        o[2 * k + 1] = w[k][1];
-                    }
-                    o[8] = h00;
-                    o[9] = h01;
-                    o[10] = h11;
-                    o[11] = h11 * id;
-                    o[12] = mk<R>(R(0), R(0)) - h01 * id;
-                    o[13] = h00 * id;
-                    o[14] = f3;
+                    const PairItem<R> pi = pair_item(V, a, b, e, scratch + (size_t)IW * it);
+                    if (pi.bad) bad = true;
+                    if (add3) acc.add(3, pi.f3);
                 }
                 __syncthreads();
                 // phase 2: every (b, c, d), b < c < d
@@ -707,31 +809,14 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                         const int c = b + 1 + cp, d = b + 1 + dp;
                         const cx<R> *ic = scratch + (size_t)IW * (off1[lo] + cp);
                         const cx<R> *jd = scratch + (size_t)IW * (off1[lo] + dp);
-                        // K = G^(P)_cd = G_cd - w_c^T w_d
-                        cx<R> K[2][2];
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-#pragma unroll
-                            for (int j = 0; j < 2; ++j) {
-                                cx<R> v = V.g(2 * c + i, 2 * d + j);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) v = cfms(v, ic[2 * k + i], jd[2 * k + j]);
-                                K[i][j] = v;
-                            }
-                        // X = H_c^-1 K; S = H_d - K^T X
-                        const cx<R> i00 = ic[11], i01 = ic[12], i11 = ic[13];
-                        cx<R> X[2][2];
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            X[0][j] = i00 * K[0][j] + i01 * K[1][j];
-                            X[1][j] = i01 * K[0][j] + i11 * K[1][j];
-                        }
-                        const cx<R> s00 = cfms(cfms(jd[8], K[0][0], X[0][0]), K[1][0], X[1][0]);
-                        const cx<R> s01 = cfms(cfms(jd[9], K[0][0], X[0][1]), K[1][0], X[1][1]);
-                        const cx<R> s11 = cfms(cfms(jd[10], K[0][1], X[0][1]), K[1][1], X[1][1]);
-                        const cx<R> det = cfms(s00 * s11, s01, s01);
-                        if (!(s00.re > R(0)) || !(det.re * s00.re + det.im * s00.im > R(0))) bad = true;
-                        q4 = q4 + ic[14] * crsqrt(det);
+                        // K = G^(P)_cd = G_cd - w_c^T w_d; X = H_c^-1 K; S = H_d - K^T X
+                        const cx<R> k00 = rank4_entry(V.g(2 * c, 2 * d), ic, jd, 0, 0);
+                        const cx<R> k01 = rank4_entry(V.g(2 * c, 2 * d + 1), ic, jd, 0, 1);
+                        const cx<R> k10 = rank4_entry(V.g(2 * c + 1, 2 * d), ic, jd, 1, 0);
+                        const cx<R> k11 = rank4_entry(V.g(2 * c + 1, 2 * d + 1), ic, jd, 1, 1);
+                        const QuadTerm<R> qt = quad_term(k00, k01, k10, k11, ic, jd);
+                        if (qt.bad) bad = true;
+                        q4 = q4 + qt.term;
                     }
                 }
                 acc.add(4, q4);     // this group's four-detector terms (zero if order 3)
