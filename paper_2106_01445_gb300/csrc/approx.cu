@@ -966,7 +966,7 @@ __host__ __device__ inline int pair_part_entries(int N) {  // the larger half
 
 template <typename R>
 __device__ void sweep_inverse_pair(cg::cluster_group &cl, int rank, int M, const double *__restrict__ O,
-                                   const int *modes, int n, double cs, double sn, cx<R> *Gl, cx<R> *stage,
+                                   const uint8_t *modes, int n, double cs, double sn, cx<R> *Gl, cx<R> *stage,
                                    cx<R> *stage_peer, int rsplit, int off1, int *s_bad, double *s_zs) {
     const int t = threadIdx.x;
     const int N = 2 * n, N2 = 2 * M;
@@ -1054,7 +1054,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMinorThreads, 1)
 approx_minors_pair_kernel(int M, const double *__restrict__ O, const uint64_t *__restrict__ pats, int n_pat,
                           int order, int n_single, int smem_entries, unsigned long long *counter, ApproxPlan pl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int modes[128];
+    __shared__ uint8_t modes[128];  // bytes: at 112 clicks the CTA needs all but ~0.2 KB of 227 KB
     __shared__ int s_off[2 * (kApproxMaxN + 1)];
     __shared__ long long s_u;
     __shared__ int s_bad;

@@ -237,6 +237,26 @@ def test_pair_kernel_in_mixed_batches(ctx):
     assert np.abs(ff["logP"][ok] - ref["logP"][ok]).max() < 1e-6
 
 
+def test_pair_kernel_at_the_click_limit(ctx):
+    """Patterns of 100, 111 and 112 clicks (the largest the approximation takes: at 112 the
+    CTA pair's packed inverse and pair items leave ~0.2 KB of the 227 KB a CTA may hold):
+    every pattern evaluated (no launch or workspace error).  The two minors precisions are
+    compared only as a sanity check, at 1e-4 in log P: parity at this size is not claimed
+    (no stored oracle values; on this strongly squeezed 120-mode device their difference,
+    a few 1e-6, is the tables' rounding amplified by the fit), and 1e-4 is far below the
+    order-2 approximation's own error on such patterns (tens of percent)."""
+    M = 120
+    U, r = g.haar_unitary(M, 31), g.squeezing(M, M, 1.2, 1.6, 31)
+    pats = np.stack([g.modes_to_pattern(list(range(m))) for m in (100, 111, 112)])
+    res = {p: run(ctx, U, r, 0.9, pats, 2, p) for p in ("fp64", "ff")}
+    for p in res:
+        assert np.isin(res[p]["status"], (0, 7)).all(), (p, res[p]["status"])
+        assert np.isfinite(res[p]["logP"]).all()
+    ok = (res["fp64"]["status"] == 0) & (res["ff"]["status"] == 0)
+    assert ok.any()
+    assert np.abs(res["ff"]["logP"][ok] - res["fp64"]["logP"][ok]).max() < 1e-4
+
+
 @pytest.mark.parametrize("precision", ["fp64", "ff"])
 def test_pair_kernel_on_small_patterns_matches_oracle(ctx, small_case, precision):
     """The CTA-pair minors kernel (two CTAs, the inverse split over their shared memories,
