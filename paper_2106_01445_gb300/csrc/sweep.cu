@@ -291,7 +291,7 @@ template <typename T> struct Layout {
         return m;
     }
     static constexpr int max_odd() {
-        int m = sym(2 * (kS + R));  // a sub-unit's matrix before its prefix pivots (binned mode)
+        int m = 0;
         for (int l = 1; l <= kL; l += 2) m = level_size(l) > m ? level_size(l) : m;
         return m;
     }
@@ -843,77 +843,49 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(int M, const double *__
         if constexpr (BIN) {
             for (int z = t; z <= n; z += kThreads) s_ubin[z] = typename BinOf<T>::type(0.0);
         }
-        // The sub-units: the include (1) / exclude (0) choices of the next ss modes of Ublk.
-        // Signed sweeps walk them as a tree, depth e choosing mode e: the matrix after an
-        // include at depth e is stored (in slot e + 1, or in X at the last depth), an
-        // exclude is a view of the same matrix one mode further on; leaf `leaf` takes the
-        // choices of its bits from the top (sub, the choice of mode e in bit e, is its bit
-        // reversal), so consecutive leaves share every choice above the one that turns
-        // include.  jv[e]: the slot of the matrix the node at depth e views (0: Ublk);
-        // tv[e]: the product of the includes' det^{-1/2} above depth e.
+        // The sub-units: the include (1) / exclude (0) choices of the next ss modes of Ublk,
+        // walked as a tree, depth e choosing mode e: the matrix after an include at depth e is
+        // stored (in slot e + 1, or in X at the last depth), an exclude is a view of the same
+        // matrix one mode further on; leaf `leaf` takes the choices of its bits from the top
+        // (sub, the choice of mode e in bit e, is its bit reversal), so consecutive leaves share
+        // every choice above the one that turns include.  jv[e]: the slot of the matrix the
+        // node at depth e views (0: Ublk); tv[e]: the product of the includes' det^{-1/2}
+        // above depth e.
         int jv[kS + 1];
         Tau tv[kS + 1];
         jv[0] = 0;
         tv[0] = Tau(1.0);
         for (int leaf = 0; leaf < nsub; ++leaf) {
-            int sub, kk;
-            Tau tsub;
-            if constexpr (BIN) {
-                sub = leaf;
-                kk = __popc(sub);
-                const int Ds = 2 * (kk + r), dU = 2 * rp;
-                // rows: included sub modes (in order), then the last r modes of Ublk
-                for (int f = t; f < (Ds >> 1) * (Ds + 1); f += kThreads) {
-                    int i, j;
-                    fold_ij(f, Ds, i, j);
-                    const int ai = i >> 1, bj = j >> 1;
-                    // position of the ai-th row mode inside Ublk
-                    const int ui = ai < kk ? (int)__fns((unsigned)sub, 0u, ai + 1) : ss + (ai - kk);
-                    const int uj = bj < kk ? (int)__fns((unsigned)sub, 0u, bj + 1) : ss + (bj - kk);
-                    Y[pidx(Ds, i, j)] = Ub[pidx(dU, 2 * ui + (i & 1), 2 * uj + (j & 1))];
+            const int sub = ss ? (int)(__brev((unsigned)leaf) >> (32 - ss)) : 0;
+            const int kk = __popc(sub);
+            // the depth whose choice turns include (none at the first leaf); deeper
+            // choices are excludes
+            const int ds = leaf ? ss - 1 - (31 - __clz(leaf ^ (leaf - 1))) : ss;
+            if (ds < ss) {
+                const int j0 = jv[ds], D = 2 * (rp - j0);
+                const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
+                T *dst = ds + 1 < ss ? Sl + Lay::slot_off(ds + 1) : X;
+                const Tau rs = elim_into<T>(src, D, 2 * (ds - j0), dst, Wpre, &s_flag);
+                for (int e = ds + 1; e <= ss; ++e) {
+                    jv[e] = ds + 1;
+                    tv[e] = tv[ds] * rs;
                 }
-                __syncthreads();
-                tsub = Tau(1.0);
-                for (int e = 0; e < kk; ++e) tsub = tsub * elim_pivot<T>(Y, Ds, 2 * e, Wpre, &s_flag);
-                // level 0 of the expansion: the trailing 2r x 2r block, packed into X
-                const int d = 2 * r, o = 2 * kk;
+            } else {
+                for (int e = 1; e <= ss; ++e) {
+                    jv[e] = 0;
+                    tv[e] = Tau(1.0);
+                }
+            }
+            const Tau tsub = tv[ss];
+            // level 0 of the expansion: the leaf's matrix, packed into X (already there
+            // after an include at the last depth)
+            if (ds + 1 != ss) {
+                const int j0 = jv[ss], D = 2 * (rp - j0), o = 2 * (ss - j0), d = 2 * r;
+                const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
                 for (int f = t; f < (d >> 1) * (d + 1); f += kThreads) {
                     int i, j;
                     fold_ij(f, d, i, j);
-                    X[pidx(d, i, j)] = Y[pidx(Ds, o + i, o + j)];
-                }
-            } else {
-                sub = ss ? (int)(__brev((unsigned)leaf) >> (32 - ss)) : 0;
-                kk = __popc(sub);
-                // the depth whose choice turns include (none at the first leaf); deeper
-                // choices are excludes
-                const int ds = leaf ? ss - 1 - (31 - __clz(leaf ^ (leaf - 1))) : ss;
-                if (ds < ss) {
-                    const int j0 = jv[ds], D = 2 * (rp - j0);
-                    const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
-                    T *dst = ds + 1 < ss ? Sl + Lay::slot_off(ds + 1) : X;
-                    const Tau rs = elim_into<T>(src, D, 2 * (ds - j0), dst, Wpre, &s_flag);
-                    for (int e = ds + 1; e <= ss; ++e) {
-                        jv[e] = ds + 1;
-                        tv[e] = tv[ds] * rs;
-                    }
-                } else {
-                    for (int e = 1; e <= ss; ++e) {
-                        jv[e] = 0;
-                        tv[e] = Tau(1.0);
-                    }
-                }
-                tsub = tv[ss];
-                // level 0 of the expansion: the leaf's matrix, packed into X (already there
-                // after an include at the last depth)
-                if (ds + 1 != ss) {
-                    const int j0 = jv[ss], D = 2 * (rp - j0), o = 2 * (ss - j0), d = 2 * r;
-                    const T *src = j0 ? Sl + Lay::slot_off(j0) : Ub;
-                    for (int f = t; f < (d >> 1) * (d + 1); f += kThreads) {
-                        int i, j;
-                        fold_ij(f, d, i, j);
-                        X[pidx(d, i, j)] = src[pidx(D, o + i, o + j)];
-                    }
+                    X[pidx(d, i, j)] = src[pidx(D, o + i, o + j)];
                 }
             }
             if (t == 0) NIO::st(tauX, 0, node_one<Node>());
