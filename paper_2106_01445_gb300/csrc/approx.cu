@@ -1983,9 +1983,14 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     if (nsmall > 0) {
         // the packed inverse and four staged pivot columns, or the pair phases' items
         // (15 entries each, at least n - 2 of them, up to 8 n while the CTAs per SM stay)
-        const int ent = std::is_same<R, float>::value  // FP32: no pair phases
-                            ? sym(2 * nsmall) + 8 * nsmall
-                            : minor_smem_entries(nsmall, (int)sizeof(cx<R>), MinorPrec<R>::min_blocks);
+        // (the largest over n <= nsmall: the kernel sizes each pattern's items from its own n,
+        // and the floor to whole items makes the entries fall by up to 14 between some n)
+        int ent = sym(2 * nsmall) + 8 * nsmall;  // FP32: no pair phases
+        if constexpr (!std::is_same<R, float>::value)
+            for (int m = 1; m <= nsmall; ++m) {
+                const int e = minor_smem_entries(m, (int)sizeof(cx<R>), MinorPrec<R>::min_blocks);
+                if (e > ent) ent = e;
+            }
         const size_t minor_smem = sizeof(cx<R>) * (size_t)ent;
         GBS_CUDA(ctx, cudaFuncSetAttribute(approx_minors_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)minor_smem));
