@@ -237,6 +237,21 @@ def test_pair_kernel_in_mixed_batches(ctx):
     assert np.abs(ff["logP"][ok] - ref["logP"][ok]).max() < 1e-6
 
 
+def test_one_cta_allocation_covers_smaller_patterns(ctx):
+    """Float-float minors, order 4: a 53-click pattern needs 10 more shared-memory entries for
+    its pair items than a 54-click one (whole items under two CTAs per SM), so a batch holding
+    both must be sized for the 53; every pattern's result is the one it gets alone."""
+    M = 60
+    U, r = g.haar_unitary(M, 41), g.squeezing(M, 30, 0.5, 0.8, 41)
+    pats = np.stack([g.modes_to_pattern(list(range(m))) for m in (53, 54)])
+    both = run(ctx, U, r, 0.7, pats, 4, "ff")
+    assert np.isin(both["status"], (0, 7)).all(), both["status"]
+    for i in range(2):
+        alone = run(ctx, U, r, 0.7, pats[i:i + 1], 4, "ff")
+        assert alone["status"][0] == both["status"][i]
+        assert alone["logP"][0] == both["logP"][i] or abs(alone["logP"][0] - both["logP"][i]) < 1e-12
+
+
 def test_pair_kernel_at_the_click_limit(ctx):
     """Patterns of 100, 111 and 112 clicks (the largest the approximation takes: at 112 the
     CTA pair's packed inverse and pair items leave ~0.2 KB of the 227 KB a CTA may hold):
