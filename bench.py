@@ -36,7 +36,7 @@ import gbs_inputs as g  # noqa: E402
 METRIC = "subset logdets/sec and click-pattern log P/sec at stated rel. error vs FP64 oracle"
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch on this workload
 # (ncu captures summarised under profiles/); None where no capture of the current kernel exists
-DRAM_TRAFFIC = {"fp32": 134400.0, "dd": 261888.0, "fp64": 129536.0, "fx": 175872.0}
+DRAM_TRAFFIC = {"fp32": 129536.0, "dd": 396800.0, "fp64": 130048.0, "fx": 182784.0}
 UNIT = "subset logdets/s"
 # 32-bit multiply-adds of one fixed-point update entry: two 128 x 128-bit products
 # truncated to their top 128 bits, 23 IMAD each (3 + 5 + 7 + 8 over the four rows)
