@@ -13,11 +13,14 @@
 // (2|Z|)^3/3 for a fresh Cholesky.
 //
 // Work decomposition (one persistent launch over every pattern):
-//   unit   = (pattern, include/exclude choice of the first q modes): a CTA gathers
-//            A on the unit's modes, eliminates the included prefix modes, and
-//   expands the next L levels breadth-first in shared memory (2^L nodes), then
-//   every thread runs the last B levels of its node as straight-line code with
-//            the Schur complements in registers.
+//   unit     = (pattern, include/exclude choice of the first q - s modes): a CTA gathers
+//              A on the unit's modes and eliminates the included prefix modes;
+//   sub-unit = a choice for the next s modes, the leaves of an s-level tree walked depth
+//              first over the unit's trailing block (an include's Schur complement
+//              stored per depth, an exclude a view of it); each sub-unit's matrix is
+//              expanded L levels breadth-first in shared memory (2^L nodes), then every
+//              thread runs the last B levels of its node as straight-line code with the
+//              Schur complements in registers.
 // Signed terms are accumulated per thread with the error-free TwoSum (float-float
 // in the FP32 path, double-double in the FP64 path), reduced across the CTA in
 // double with TwoSum, stored per unit, and summed per pattern in unit order.
