@@ -489,7 +489,7 @@ __device__ __forceinline__ void sweep_inverse(int M, const double *__restrict__ 
 
 // shared-memory entries of the one-CTA minors kernel for patterns of up to n clicks: the
 // packed inverse, then max(the staged pivot columns, the pair phases' items); the items
-// number at least n - 2 and up to 8 n as long as the CTAs per SM of the bare inverse stay
+// number at least n - 1 and up to 8 n as long as the CTAs per SM of the bare inverse stay
 __host__ __device__ inline int minor_smem_entries(int n, int esz, int min_blocks) {
     constexpr long long kSM = 228 * 1024, kCTA = 227 * 1024, kPerCTA = 4 * 1024;  // 1 KB reserved + static
     const long long inv = (long long)n * (2 * n + 1), base = inv + 8LL * n;
@@ -497,7 +497,7 @@ __host__ __device__ inline int minor_smem_entries(int n, int esz, int min_blocks
     if (base * esz > per) per = kCTA - kPerCTA;            // the inverse alone takes the SM
     long long items = (per / esz - inv) / 15;
     if (items > 8LL * n) items = 8LL * n;
-    if (items < n - 2) items = n - 2;
+    if (items < n - 1) items = n - 1;
     const long long ent = inv + (15 * items > 8LL * n ? 15 * items : 8LL * n);
     return (int)ent;
 }
@@ -542,33 +542,47 @@ template <typename R> struct PairItem {
     cx<R> f3;
     int bad;
 };
+// G_PP = L D L^T of pair P = {a, b} (unit lower L, accretive pivots): L (6), D^-1/2 (4) and
+// f2 = det(G_PP)^{-1/2} at pd[0..10]; returns 1 if a pivot is not accretive
+constexpr int kPairLdl = 11;
 template <typename R, bool IN>
-__device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, int b, int e, cx<R> *o) {
-    PairItem<R> out;
-    out.bad = 0;
+__device__ __forceinline__ int pair_ldl_body(const GView<R> &V, int a, int b, cx<R> *pd) {
+    int bad = 0;
     const int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
     cx<R> m4[10];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = V.g(rr[i], rr[j]);
-    cx<R> L[6], dm[4], f2 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
+    cx<R> f2 = mk<R>(R(1), R(0)), prev = mk<R>(R(1), R(0));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const cx<R> d = m4[pidx(4, k, k)];
-        if (!(d.re > R(0))) out.bad = 1;
+        if (!(d.re > R(0))) bad = 1;
         if (k & 1) f2 = pmul<R, IN>(f2, prsqrt<R, IN>(pmul<R, IN>(prev, d)));
         prev = d;
-        dm[k] = prsqrt<R, IN>(d);
+        pd[6 + k] = prsqrt<R, IN>(d);
         const cx<R> inv = pinv<R, IN>(d);
 #pragma unroll
         for (int i = k + 1; i < 4; ++i) {
             const cx<R> li = pmul<R, IN>(m4[pidx(4, k, i)], inv);
-            L[pidx(3, k, i - 1)] = li;
+            pd[pidx(3, k, i - 1)] = li;
 #pragma unroll
             for (int j = i; j < 4; ++j) m4[pidx(4, i, j)] = pfms<R, IN>(m4[pidx(4, i, j)], li, m4[pidx(4, k, j)]);
         }
     }
+    pd[10] = f2;
+    return bad;
+}
+// item (b, e) of pair P = {a, b} from the pair's factorisation pd: w = D^-1/2 L^-1 G_{P,e},
+// H_e = G_ee - w^T w; stores w (8), H_e (3), H_e^-1 (3) and f3 = det(G_{P+e})^{-1/2} at o and
+// returns f3 (bad: a pivot of H_e not accretive)
+template <typename R, bool IN>
+__device__ __forceinline__ PairItem<R> pair_item_from(const GView<R> &V, int a, int b, int e, const cx<R> *pd,
+                                                      cx<R> *o) {
+    PairItem<R> out;
+    out.bad = 0;
+    const int rr[4] = {2 * a, 2 * a + 1, 2 * b, 2 * b + 1};
     // y = L^-1 G_{P,e} (two columns), w = D^-1/2 y
     cx<R> w[4][2];
 #pragma unroll
@@ -578,11 +592,11 @@ __device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, 
         for (int i = 0; i < 4; ++i) {
             cx<R> v = V.g(rr[i], 2 * e + col);
 #pragma unroll
-            for (int k = 0; k < i; ++k) v = pfms<R, IN>(v, L[pidx(3, k, i - 1)], y[k]);
+            for (int k = 0; k < i; ++k) v = pfms<R, IN>(v, pd[pidx(3, k, i - 1)], y[k]);
             y[i] = v;
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) w[i][col] = pmul<R, IN>(y[i], dm[i]);
+        for (int i = 0; i < 4; ++i) w[i][col] = pmul<R, IN>(y[i], pd[6 + i]);
     }
     // H_e = G_ee - w^T w; its pivots h00 and det / h00
     cx<R> h00 = V.g(2 * e, 2 * e), h01 = V.g(2 * e, 2 * e + 1), h11 = V.g(2 * e + 1, 2 * e + 1);
@@ -594,7 +608,7 @@ __device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, 
     }
     const cx<R> det = pfms<R, IN>(pmul<R, IN>(h00, h11), h01, h01);
     if (!(h00.re > R(0)) || !(det.re * h00.re + det.im * h00.im > R(0))) out.bad = 1;
-    out.f3 = pmul<R, IN>(f2, prsqrt<R, IN>(det));
+    out.f3 = pmul<R, IN>(pd[10], prsqrt<R, IN>(det));
     const cx<R> id = pinv<R, IN>(det);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -610,13 +624,38 @@ __device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, 
     o[14] = out.f3;
     return out;
 }
+// item (b, e) with the pair's factorisation in registers (no table of them: the CTA pair)
+template <typename R, bool IN>
+__device__ __forceinline__ PairItem<R> pair_item_body(const GView<R> &V, int a, int b, int e, cx<R> *o) {
+    cx<R> pd[kPairLdl];
+    const int bad = pair_ldl_body<R, IN>(V, a, b, pd);
+    PairItem<R> out = pair_item_from<R, IN>(V, a, b, e, pd, o);
+    out.bad |= bad;
+    return out;
+}
 template <typename R>
 __device__ __forceinline__ PairItem<R> pair_item(const GView<R> &V, int a, int b, int e, cx<R> *o) {
     return pair_item_body<R, false>(V, a, b, e, o);
 }
-// float-float: one out-of-line call per item with its arithmetic inline
+template <typename R> __device__ __forceinline__ int pair_ldl(const GView<R> &V, int a, int b, cx<R> *pd) {
+    return pair_ldl_body<R, false>(V, a, b, pd);
+}
+template <typename R>
+__device__ __forceinline__ PairItem<R> pair_item_tab(const GView<R> &V, int a, int b, int e, const cx<R> *pd,
+                                                     cx<R> *o) {
+    return pair_item_from<R, false>(V, a, b, e, pd, o);
+}
+// float-float: one out-of-line call per item (and per pair factorisation) with its
+// arithmetic inline
 static __device__ __noinline__ PairItem<ff> pair_item(const GView<ff> V, int a, int b, int e, cx<ff> *o) {
     return pair_item_body<ff, true>(V, a, b, e, o);
+}
+static __device__ __noinline__ int pair_ldl(const GView<ff> V, int a, int b, cx<ff> *pd) {
+    return pair_ldl_body<ff, true>(V, a, b, pd);
+}
+static __device__ __noinline__ PairItem<ff> pair_item_tab(const GView<ff> V, int a, int b, int e, const cx<ff> *pd,
+                                                          cx<ff> *o) {
+    return pair_item_from<ff, true>(V, a, b, e, pd, o);
 }
 
 // The group terms det(G_WW)^{-1/2} of every W with |W| <= order, summed per |W| into acc.
@@ -634,10 +673,12 @@ static __device__ __noinline__ PairItem<ff> pair_item(const GView<ff> V, int a, 
 // All pivots are accretive (Re > 0), so each determinant's principal root is the product of
 // its factors' principal roots.  Every thread of the CTA must call this (it synchronises the
 // CTA); s_off holds 2 (n + 1) ints of shared memory; add3: this CTA adds the three-detector
-// terms (of a CTA pair, one computes them for its phase 2 only).
+// terms (of a CTA pair, one computes them for its phase 2 only).  table: the group's pair
+// factorisations G_PP = L D L^T are computed once per b into `scratch` ahead of the items
+// (cap >= n - 1 then), instead of once per item.
 template <typename R>
 __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order, int tid, int nthr, int t2,
-                                            int n2, cx<R> *scratch, int cap, int *s_off, bool add3,
+                                            int n2, cx<R> *scratch, int cap, int *s_off, bool add3, bool table,
                                             GroupAcc<R> &acc, bool &bad) {
     // w = 1: det of the 2x2 block, one root
     if (order >= 1)
@@ -759,9 +800,13 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
         cx<R> q4 = mk<R>(R(0), R(0));
         for (int a = 0; a + 2 < n; ++a) {
             for (int b0 = a + 1; b0 + 1 < n;) {
-                // the group: b in [b0, b1) while its items fit (at least one b: cap >= n - 2)
+                // the group: b in [b0, b1) while its items (and with `table` each pair's
+                // factorisation) fit in cap items' entries (at least one b: cap >= n - 2, and
+                // n - 1 with the table)
+                const int per_b = table ? kPairLdl : 0;
                 int b1 = b0, items = 0;
-                while (b1 + 1 < n && (b1 == b0 || items + (n - b1 - 1) <= cap)) {
+                while (b1 + 1 < n &&
+                       (b1 == b0 || IW * (items + (n - b1 - 1)) + per_b * (b1 - b0 + 1) <= IW * cap)) {
                     items += n - b1 - 1;
                     ++b1;
                 }
@@ -776,8 +821,13 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                     off1[b1 - b0] = s1;
                     off2[b1 - b0] = s2;
                 }
-                __syncthreads();
                 const int nb = b1 - b0;
+                // the group's pair factorisations (with `table`), then its items
+                cx<R> *const items_at = scratch + (size_t)per_b * nb;
+                if (table)
+                    for (int bb = t1; bb < nb; bb += n1)
+                        if (pair_ldl(V, a, b0 + bb, scratch + (size_t)kPairLdl * bb)) bad = true;
+                __syncthreads();
                 // phase 1: every (b, e), e > b
                 for (int it = t1; it < items; it += n1) {
                     int lo = 0, hi = nb;
@@ -786,7 +836,9 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                         if (off1[mid] <= it) lo = mid; else hi = mid;
                     }
                     const int b = b0 + lo, e = b + 1 + (it - off1[lo]);
-                    const PairItem<R> pi = pair_item(V, a, b, e, scratch + (size_t)IW * it);
+                    const PairItem<R> pi = table ? pair_item_tab(V, a, b, e, scratch + (size_t)kPairLdl * lo,
+                                                                 items_at + (size_t)IW * it)
+                                                 : pair_item(V, a, b, e, items_at + (size_t)IW * it);
                     if (pi.bad) bad = true;
                     if (add3) acc.add(3, pi.f3);
                 }
@@ -807,8 +859,8 @@ __device__ __forceinline__ void group_terms(const GView<R> &V, int n, int order,
                         while ((dp + 1) * dp / 2 <= r) ++dp;
                         const int cp = r - dp * (dp - 1) / 2;
                         const int c = b + 1 + cp, d = b + 1 + dp;
-                        const cx<R> *ic = scratch + (size_t)IW * (off1[lo] + cp);
-                        const cx<R> *jd = scratch + (size_t)IW * (off1[lo] + dp);
+                        const cx<R> *ic = items_at + (size_t)IW * (off1[lo] + cp);
+                        const cx<R> *jd = items_at + (size_t)IW * (off1[lo] + dp);
                         // K = G^(P)_cd = G_cd - w_c^T w_d; X = H_c^-1 K; S = H_d - K^T X
                         const cx<R> k00 = rank4_entry(V.g(2 * c, 2 * d), ic, jd, 0, 0);
                         const cx<R> k01 = rank4_entry(V.g(2 * c, 2 * d + 1), ic, jd, 0, 1);
@@ -931,7 +983,7 @@ __global__ void __launch_bounds__(kMinorThreads, MinorPrec<R>::min_blocks) appro
         // items per group from this pattern's own n (not the batch's allocation): the work
         // split, and with it every rounding, is the same in any batch
         const int cap = (minor_smem_entries(n, (int)sizeof(cx<R>), MinorPrec<R>::min_blocks) - sym(N)) / 15;
-        group_terms<R>(V, n, order, t, kMinorThreads, t, kMinorThreads, G + sym(N), cap, s_off, true, acc, bad);
+        group_terms<R>(V, n, order, t, kMinorThreads, t, kMinorThreads, G + sym(N), cap, s_off, true, true, acc, bad);
         if (bad) s_bad = 1;
         warp_group_sums<R>(acc, red[t >> 5]);
         __syncthreads();
@@ -1108,7 +1160,7 @@ approx_minors_pair_kernel(int M, const double *__restrict__ O, const uint64_t *_
         // each CTA computes every pair item in its own scratch (the staging area and beyond),
         // rank 0 adds the three-detector terms, the four-detector ones are split over both
         group_terms<R>(V, n, order, rank * kMinorThreads + t, 2 * kMinorThreads, rank * kMinorThreads + t,
-                       2 * kMinorThreads, stage, n - 2, s_off, rank == 0, acc, bad);
+                       2 * kMinorThreads, stage, n - 2, s_off, rank == 0, false, acc, bad);
         if (bad) s_bad = 1;
         // warp sums: rank 1's into rank 0's table (rows 8..15), then rank 0 writes the unit
         double (*red0)[2 * (kMaxOrder + 1)] = rank == 0 ? red : cl.map_shared_rank(red, 0);
@@ -1982,7 +2034,7 @@ int run_approx(gbs_ctx *ctx, int M, const double *O, const double *logdet, const
     if (st) return st;
     if (nsmall > 0) {
         // the packed inverse and four staged pivot columns, or the pair phases' items
-        // (15 entries each, at least n - 2 of them, up to 8 n while the CTAs per SM stay)
+        // (15 entries each, at least n - 1 of them, up to 8 n while the CTAs per SM stay)
         // (the largest over n <= nsmall: the kernel sizes each pattern's items from its own n,
         // and the floor to whole items makes the entries fall by up to 14 between some n)
         int ent = sym(2 * nsmall) + 8 * nsmall;  // FP32: no pair phases
