@@ -228,7 +228,6 @@ __device__ __forceinline__ bool is_nan(double x) { return x != x; }
 __device__ __forceinline__ bool is_nan(dd x) { return x.hi != x.hi; }
 __device__ __forceinline__ bool is_nan(zc x) { return zc_nan(x); }
 __device__ __forceinline__ bool is_nan(zf x) { return zf_nan(x); }
-__device__ __forceinline__ bool is_nan(const fxe6 &) { return false; }
 // a thread's subtree sum as (hi, lo) doubles
 __device__ __forceinline__ void sum_parts(float h, float l, double &oh, double &ol) { oh = h; ol = l; }
 __device__ __forceinline__ void sum_parts(double h, double l, double &oh, double &ol) { oh = h; ol = l; }
@@ -1727,10 +1726,11 @@ __global__ void auto_mark_kernel(int n_pat, const int32_t *__restrict__ st, cons
     redo[2 * p + 1] = again ? pats[2 * p + 1] : ~0ull;
 }
 // ... and the double-double results in their places
-__global__ void auto_merge_kernel(int n_pat, const int32_t *__restrict__ st, const double *__restrict__ lp2,
+// (st and status may be the same array: each thread reads its entry before it writes it)
+__global__ void auto_merge_kernel(int n_pat, const int32_t *st, const double *__restrict__ lp2,
                                   const double *__restrict__ ka2, const double *__restrict__ er2,
                                   const int32_t *__restrict__ st2, double *__restrict__ logP, double *__restrict__ kappa,
-                                  double *__restrict__ err_bound, int32_t *__restrict__ status) {
+                                  double *__restrict__ err_bound, int32_t *status) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pat || st[p] != GBS_E_RANGE) return;
     logP[p] = lp2[p];
